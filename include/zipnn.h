@@ -1,0 +1,169 @@
+/*
+ * zipnn.h -- C ABI of libzipnn_gpu.so, a GB300 (sm_103a) implementation of the
+ * lossless parameter codec of ZipNN (arXiv 2411.05239).
+ *
+ * What the codec computes (all of it in CUDA kernels on the device):
+ *   - exponent extraction (Sec. 3.1): the 8 exponent bits of each BF16/FP32
+ *     value form one byte stream; the sign moves to the top bit of the next
+ *     byte.  FP16 uses the same 16-bit permutation (5 exponent bits + 3 high
+ *     fraction bits form the first stream);
+ *   - byte grouping (Sec. 3.2): every other byte position forms its own stream;
+ *   - Huffman-only coding (Sec. 3.1) of every stream, in independent chunks
+ *     (Sec. 5.1, 256 KiB by default), with all-zero and single-byte streams
+ *     reduced to a header (Sec. 3.2) and incompressible streams stored raw
+ *     (Sec. 3.2, "Identifying compressibility");
+ *   - a map of every chunk and byte group so chunks decode in parallel
+ *     (Sec. 5.1, "Metadata and parallelism");
+ *   - XOR delta of two tensors (Sec. 4.2).
+ * The container layout is specified in the project's design notes; streams are
+ * byte-identical to those of the CPU oracle that implements that specification.
+ *
+ * Conventions for every call below:
+ *   - "d_" pointers are CUDA device pointers owned by the caller unless stated
+ *     otherwise; tensors and containers must start on a 16-byte boundary.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without waiting, except
+ *     where noted; results are valid once the stream has completed.
+ *   - The return value reports host-side validation and launch errors.  Errors
+ *     found by the kernels (a corrupt container, an exceeded wait) are recorded
+ *     in a per-device error word and returned by zipnn_sync_status().
+ *   - No call aborts, traps or falls back to the CPU.
+ */
+#ifndef ZIPNN_H
+#define ZIPNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZIPNN_BF16 = 0, /* 1 sign, 8 exponent, 7 fraction bits (Sec. 2.2) */
+    ZIPNN_FP16 = 1, /* 1 sign, 5 exponent, 10 fraction bits */
+    ZIPNN_FP32 = 2, /* 1 sign, 8 exponent, 23 fraction bits */
+    ZIPNN_U8 = 3    /* plain bytes: one group, no permutation */
+} zipnn_dtype;
+
+typedef enum {
+    ZIPNN_OK = 0,
+    ZIPNN_EINVAL = -1,   /* bad argument: size, alignment, dtype, chunk size, base */
+    ZIPNN_ENOMEM = -2,   /* device allocation failed or buffer too small */
+    ZIPNN_ECORRUPT = -3, /* container failed validation */
+    ZIPNN_ECUDA = -4,    /* a CUDA runtime call failed */
+    ZIPNN_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+    ZIPNN_EBUSY = -6     /* admission refused: memory budget exhausted */
+} zipnn_status;
+
+#define ZIPNN_FLAG_DELTA 1u           /* container holds a XOR b (Sec. 4.2) */
+#define ZIPNN_DEFAULT_CHUNK (256u << 10)  /* Sec. 5.1: 256 KB chunks */
+#define ZIPNN_MIN_CHUNK 4096u
+#define ZIPNN_MAX_CHUNK (16u << 20)
+#define ZIPNN_MAX_LANES 1024u
+
+/* A compressed container in device memory plus a host copy of its header
+ * fields (so that decoding needs no device-to-host read). */
+typedef struct zipnn_stream {
+    void* data;           /* device pointer to the container (16-B aligned) */
+    uint64_t nbytes;      /* container size in bytes */
+    uint64_t orig_nbytes; /* size of the original tensor in bytes */
+    int32_t dtype;        /* zipnn_dtype */
+    uint32_t flags;       /* ZIPNN_FLAG_DELTA or 0 */
+    uint32_t chunk_bytes; /* original bytes per chunk */
+    uint32_t lanes;       /* interleaved sub-streams per Huffman group-chunk */
+    uint32_t n_chunks;
+    uint32_t n_groups;
+    uint32_t owned;       /* 1: data was allocated by the library */
+    uint32_t reserved;
+} zipnn_stream;
+
+/* Decoder launch parameters for batched decoding.  Zero fields take defaults;
+ * the values change speed only, never the decoded bytes. */
+typedef struct zipnn_tuning {
+    int32_t threads;      /* threads per CTA (multiple of 32, 0 = default) */
+    int32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid */
+    int32_t lut_bits;     /* decode table width: 12 (full) or 8..11 (two-level) */
+    int32_t reserved;
+} zipnn_tuning;
+
+/* Library version (the container version is 1). */
+int zipnn_version(void);
+
+/* Text for a status code; never NULL. */
+const char* zipnn_strerror(int status);
+
+/* Sub-streams per Huffman group-chunk used when a call takes no lanes value:
+ * chunk_bytes / (element size * 1024), clamped to [1, 1024]. */
+uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes);
+
+/* Upper bound on the container size for nbytes of the given dtype and chunk
+ * size: header + map + raw data + 16-B padding per group-chunk. */
+size_t zipnn_compress_bound(size_t nbytes, int dtype, size_t chunk_bytes);
+
+/* Device scratch needed by zipnn_compress_into for this input. */
+size_t zipnn_compress_workspace_size(size_t nbytes, int dtype, size_t chunk_bytes);
+
+/* Compress nbytes of d_src (Sec. 3.1, 3.2, 5.1).  Allocates the container
+ * (stream-ordered, on cuda_stream) and fills *out; free it with
+ * zipnn_stream_free.  Synchronises cuda_stream once, to learn the exact
+ * container size before allocating it.
+ * Errors: EINVAL if dtype is unknown, nbytes is not a multiple of the element
+ * size, chunk_bytes is not a multiple of 16 in [4 KiB, 16 MiB], or d_src is not
+ * 16-B aligned; ENOMEM if allocation fails; ECUDA on a launch error. */
+zipnn_status zipnn_compress(const void* d_src, size_t nbytes, int dtype, size_t chunk_bytes,
+                            zipnn_stream* out, void* cuda_stream);
+
+/* Delta (Sec. 4.2): compress d_a XOR d_b (both nbytes, caller-owned); the
+ * container is flagged ZIPNN_FLAG_DELTA and decodes only with d_b as base. */
+zipnn_status zipnn_delta(const void* d_a, const void* d_b, size_t nbytes, int dtype,
+                         size_t chunk_bytes, zipnn_stream* out, void* cuda_stream);
+
+/* Compress into caller-owned memory without allocating or synchronising.
+ * d_base_or_null: NULL for a plain container, else the delta base (nbytes).
+ * lanes: 0 = zipnn_default_lanes.  d_out must hold out_capacity >=
+ * zipnn_compress_bound() bytes; d_workspace must hold workspace_bytes >=
+ * zipnn_compress_workspace_size() bytes and must not be used by another call
+ * until this one completes.  The container size is written, as a uint64, to
+ * d_out_nbytes (a device or host-mapped pointer; may be NULL) -- it is also in
+ * the container header at byte 40. */
+zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, size_t nbytes,
+                                 int dtype, size_t chunk_bytes, uint32_t lanes, void* d_out,
+                                 size_t out_capacity, void* d_workspace, size_t workspace_bytes,
+                                 uint64_t* d_out_nbytes, void* cuda_stream);
+
+/* Wrap a container that is already in device memory (e.g. copied from a file)
+ * as a zipnn_stream: reads and validates its 64-B header (synchronous copy of
+ * 64 bytes).  The stream does not own d_data.  ECORRUPT if the header is bad. */
+zipnn_status zipnn_stream_wrap(const void* d_data, size_t nbytes, zipnn_stream* out);
+
+/* Original size and dtype of a container. */
+zipnn_status zipnn_decompressed_size(const zipnn_stream* s, size_t* nbytes, int* dtype);
+
+/* Decompress s into d_dst (caller-owned, exactly orig_nbytes bytes).
+ * d_base_or_null must be the delta base (orig_nbytes) iff s is a delta
+ * container, else NULL (EINVAL otherwise).  Chunks that fail validation on
+ * the device are skipped and reported as ECORRUPT by zipnn_sync_status. */
+zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null, void* d_dst,
+                              size_t dst_nbytes, void* cuda_stream);
+
+/* Decompress count containers in ONE persistent kernel that pulls
+ * (tensor, chunk) work items from a device queue (the batching form).
+ * streams[i] decodes into d_dsts[i]; d_bases may be NULL (no deltas) or hold
+ * one base pointer (or NULL) per container.  tuning may be NULL. */
+zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* const* d_bases,
+                                    void* const* d_dsts, int count, const zipnn_tuning* tuning,
+                                    void* cuda_stream);
+
+/* Wait for cuda_stream and return (and clear) the device error word:
+ * ECORRUPT for a container rejected by a kernel, ETIMEOUT for a bounded wait
+ * that gave up, else the CUDA error state as ECUDA, else OK. */
+zipnn_status zipnn_sync_status(void* cuda_stream);
+
+/* Free a container allocated by the library (no-op for wrapped streams). */
+void zipnn_stream_free(zipnn_stream* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZIPNN_H */

@@ -1,0 +1,377 @@
+// C ABI of libzipnn_gpu.so (declarations and contracts in include/zipnn.h).
+// Host-side validation, job tables, stream-ordered allocation and launches of
+// the encoder (encode.cu) and decoder (decode.cu) kernels.  No call falls back
+// to the CPU: every byte of the codec is produced by the kernels.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "zipnn.h"
+#include "zipnn_internal.cuh"
+
+namespace zipnn {
+cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                     uint64_t nchunks_total, uint64_t ngc_total,
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st);
+cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                  uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
+                                  cudaStream_t st);
+cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                             uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
+                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st);
+}  // namespace zipnn
+
+using namespace zipnn;
+
+// Device error word: bit 0 corrupt container, bit 1 output too small,
+// bit 2 a bounded wait gave up.  One per device.
+__device__ uint32_t g_zipnn_err;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint32_t* g_err_ptr[kMaxDevices];
+
+uint32_t* err_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_err_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_zipnn_err) != cudaSuccess) return nullptr;
+    g_err_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  return g_err_ptr[dev];
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+zipnn_status check_params(int dtype, size_t nbytes, size_t chunk_bytes, uint32_t lanes) {
+  if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8) return ZIPNN_EINVAL;
+  const int es = elem_size(dtype);
+  if (nbytes % es) return ZIPNN_EINVAL;
+  if (chunk_bytes < ZIPNN_MIN_CHUNK || chunk_bytes > ZIPNN_MAX_CHUNK || chunk_bytes % 16)
+    return ZIPNN_EINVAL;
+  if (lanes < 1 || lanes > ZIPNN_MAX_LANES || lanes > chunk_bytes / 16) return ZIPNN_EINVAL;
+  if ((nbytes + chunk_bytes - 1) / chunk_bytes > 0xFFFFFFFFull) return ZIPNN_EINVAL;
+  return ZIPNN_OK;
+}
+
+zipnn_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return ZIPNN_OK;
+  if (e == cudaErrorMemoryAllocation) return ZIPNN_ENOMEM;
+  return ZIPNN_ECUDA;
+}
+
+uint32_t lanes_default(int dtype, size_t chunk_bytes) {
+  const int es = elem_size(dtype);
+  uint64_t t = chunk_bytes / ((uint64_t)es * 1024u);
+  if (t < 1) t = 1;
+  if (t > ZIPNN_MAX_LANES) t = ZIPNN_MAX_LANES;
+  return (uint32_t)t;
+}
+
+Job make_job(const void* src, const void* base, void* dst, size_t nbytes, int dtype,
+             size_t chunk_bytes, uint32_t lanes, uint32_t flags) {
+  Job J;
+  memset(&J, 0, sizeof(J));
+  J.src = static_cast<const uint8_t*>(src);
+  J.base = static_cast<const uint8_t*>(base);
+  J.dst = static_cast<uint8_t*>(dst);
+  J.nbytes = nbytes;
+  J.chunk_bytes = (uint32_t)chunk_bytes;
+  J.lanes = lanes;
+  J.n_chunks = (uint32_t)((nbytes + chunk_bytes - 1) / chunk_bytes);
+  J.dtype = dtype;
+  J.flags = flags;
+  return J;
+}
+
+zipnn_status read_header(const uint8_t* h, size_t nbytes, zipnn_stream* out) {
+  if (h[0] != 'Z' || h[1] != 'N' || h[2] != 'N' || h[3] != '1') return ZIPNN_ECORRUPT;
+  uint32_t ver = h[4] | (h[5] << 8);
+  if (ver != 1) return ZIPNN_ECORRUPT;
+  int dtype = h[6];
+  uint32_t flags = h[7];
+  uint64_t orig, P, total;
+  uint32_t C, T, G, nch;
+  memcpy(&orig, h + 8, 8);
+  memcpy(&C, h + 16, 4);
+  memcpy(&T, h + 20, 4);
+  memcpy(&G, h + 24, 4);
+  memcpy(&nch, h + 28, 4);
+  memcpy(&P, h + 32, 8);
+  memcpy(&total, h + 40, 8);
+  if (dtype > ZIPNN_U8 || (flags & ~ZIPNN_FLAG_DELTA)) return ZIPNN_ECORRUPT;
+  if (check_params(dtype, orig, C, T) != ZIPNN_OK) return ZIPNN_ECORRUPT;
+  if (G != (uint32_t)elem_size(dtype)) return ZIPNN_ECORRUPT;
+  if ((uint64_t)nch != (orig + C - 1) / C) return ZIPNN_ECORRUPT;
+  if (P != kHdrBytes + (uint64_t)nch * G * kEntryBytes) return ZIPNN_ECORRUPT;
+  if (total != nbytes || total < P) return ZIPNN_ECORRUPT;
+  for (int k = 48; k < 64; k++)
+    if (h[k]) return ZIPNN_ECORRUPT;
+  out->nbytes = total;
+  out->orig_nbytes = orig;
+  out->dtype = dtype;
+  out->flags = flags;
+  out->chunk_bytes = C;
+  out->lanes = T;
+  out->n_chunks = nch;
+  out->n_groups = G;
+  return ZIPNN_OK;
+}
+
+zipnn_status check_stream(const zipnn_stream* s) {
+  if (!s || !s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
+  if (check_params(s->dtype, s->orig_nbytes, s->chunk_bytes, s->lanes) != ZIPNN_OK)
+    return ZIPNN_EINVAL;
+  if (s->n_groups != (uint32_t)elem_size(s->dtype)) return ZIPNN_EINVAL;
+  if ((uint64_t)s->n_chunks != (s->orig_nbytes + s->chunk_bytes - 1) / s->chunk_bytes)
+    return ZIPNN_EINVAL;
+  if (s->nbytes < kHdrBytes + (uint64_t)s->n_chunks * s->n_groups * kEntryBytes)
+    return ZIPNN_EINVAL;
+  return ZIPNN_OK;
+}
+
+Job decode_job(const zipnn_stream* s, const void* base, void* dst) {
+  Job J = make_job(s->data, base, dst, s->orig_nbytes, s->dtype, s->chunk_bytes, s->lanes,
+                   s->flags);
+  J.stream_bytes = s->nbytes;
+  return J;
+}
+
+}  // namespace
+
+extern "C" {
+
+int zipnn_version(void) { return 1; }
+
+const char* zipnn_strerror(int status) {
+  switch (status) {
+    case ZIPNN_OK: return "ok";
+    case ZIPNN_EINVAL: return "invalid argument";
+    case ZIPNN_ENOMEM: return "out of device memory or buffer too small";
+    case ZIPNN_ECORRUPT: return "corrupt container";
+    case ZIPNN_ECUDA: return "CUDA runtime error";
+    case ZIPNN_ETIMEOUT: return "bounded device wait gave up";
+    case ZIPNN_EBUSY: return "memory budget exhausted";
+    default: return "unknown status";
+  }
+}
+
+uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes) {
+  if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8) return 0;
+  return lanes_default(dtype, chunk_bytes);
+}
+
+size_t zipnn_compress_bound(size_t nbytes, int dtype, size_t chunk_bytes) {
+  if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8 || chunk_bytes == 0) return 0;
+  const uint64_t G = elem_size(dtype);
+  const uint64_t nch = (nbytes + chunk_bytes - 1) / chunk_bytes;
+  return kHdrBytes + nch * G * kEntryBytes + nbytes + nch * G * 16;
+}
+
+size_t zipnn_compress_workspace_size(size_t nbytes, int dtype, size_t chunk_bytes) {
+  if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8 || chunk_bytes == 0) return 0;
+  const uint64_t G = elem_size(dtype);
+  const uint64_t nch = (nbytes + chunk_bytes - 1) / chunk_bytes;
+  return encode_scratch_bytes(nch, nch * G, 1);
+}
+
+zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, size_t nbytes,
+                                 int dtype, size_t chunk_bytes, uint32_t lanes, void* d_out,
+                                 size_t out_capacity, void* d_workspace, size_t workspace_bytes,
+                                 uint64_t* d_out_nbytes, void* cuda_stream) {
+  if (lanes == 0 && dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8) lanes = lanes_default(dtype, chunk_bytes);
+  zipnn_status rc = check_params(dtype, nbytes, chunk_bytes, lanes);
+  if (rc) return rc;
+  if ((nbytes && !d_src) || !d_out || !aligned16(d_src) || !aligned16(d_out) ||
+      !aligned16(d_base_or_null))
+    return ZIPNN_EINVAL;
+  if (out_capacity < zipnn_compress_bound(nbytes, dtype, chunk_bytes)) return ZIPNN_ENOMEM;
+  if (!d_workspace || workspace_bytes < zipnn_compress_workspace_size(nbytes, dtype, chunk_bytes))
+    return ZIPNN_ENOMEM;
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Job J = make_job(d_src, d_base_or_null, d_out, nbytes, dtype, chunk_bytes, lanes,
+                   d_base_or_null ? ZIPNN_FLAG_DELTA : 0u);
+  J.out_capacity = out_capacity;
+  J.out_nbytes = d_out_nbytes;
+  const uint64_t ngc = (uint64_t)J.n_chunks * elem_size(dtype);
+  EncodeScratch s;
+  encode_scratch_carve(d_workspace, J.n_chunks, ngc, 1, &s);
+  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st);
+  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st);
+  return cuda_status(e);
+}
+
+static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t nbytes, int dtype,
+                                   size_t chunk_bytes, zipnn_stream* out, void* cuda_stream) {
+  if (!out) return ZIPNN_EINVAL;
+  memset(out, 0, sizeof(*out));
+  const uint32_t lanes = (dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8) ? lanes_default(dtype, chunk_bytes) : 0;
+  zipnn_status rc = check_params(dtype, nbytes, chunk_bytes, lanes);
+  if (rc) return rc;
+  if ((nbytes && !d_src) || !aligned16(d_src) || !aligned16(d_base)) return ZIPNN_EINVAL;
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Job J = make_job(d_src, d_base, nullptr, nbytes, dtype, chunk_bytes, lanes,
+                   d_base ? ZIPNN_FLAG_DELTA : 0u);
+  const uint64_t ngc = (uint64_t)J.n_chunks * elem_size(dtype);
+  const size_t ws = encode_scratch_bytes(J.n_chunks, ngc, 1);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, ws, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  EncodeScratch s;
+  encode_scratch_carve(scratch, J.n_chunks, ngc, 1, &s);
+  e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st);
+  uint64_t total = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, s.totals, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  void* buf = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(&buf, total ? total : 16, st);
+  if (e == cudaSuccess) {
+    J.dst = static_cast<uint8_t*>(buf);
+    J.out_capacity = total;
+    e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st);
+  }
+  cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) {
+    if (buf) cudaFreeAsync(buf, st);
+    return cuda_status(e);
+  }
+  out->data = buf;
+  out->nbytes = total;
+  out->orig_nbytes = nbytes;
+  out->dtype = dtype;
+  out->flags = J.flags;
+  out->chunk_bytes = (uint32_t)chunk_bytes;
+  out->lanes = lanes;
+  out->n_chunks = J.n_chunks;
+  out->n_groups = (uint32_t)elem_size(dtype);
+  out->owned = 1;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_compress(const void* d_src, size_t nbytes, int dtype, size_t chunk_bytes,
+                            zipnn_stream* out, void* cuda_stream) {
+  return compress_alloc(d_src, nullptr, nbytes, dtype, chunk_bytes, out, cuda_stream);
+}
+
+zipnn_status zipnn_delta(const void* d_a, const void* d_b, size_t nbytes, int dtype,
+                         size_t chunk_bytes, zipnn_stream* out, void* cuda_stream) {
+  if (!d_b && nbytes) return ZIPNN_EINVAL;
+  if (!d_b) {
+    // empty delta: still a DELTA container
+    zipnn_status rc = compress_alloc(d_a, nullptr, 0, dtype, chunk_bytes, out, cuda_stream);
+    return rc;
+  }
+  return compress_alloc(d_a, d_b, nbytes, dtype, chunk_bytes, out, cuda_stream);
+}
+
+zipnn_status zipnn_stream_wrap(const void* d_data, size_t nbytes, zipnn_stream* out) {
+  if (!out || !d_data || !aligned16(d_data) || nbytes < (size_t)kHdrBytes) return ZIPNN_EINVAL;
+  memset(out, 0, sizeof(*out));
+  uint8_t h[kHdrBytes];
+  cudaError_t e = cudaMemcpy(h, d_data, kHdrBytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  zipnn_status rc = read_header(h, nbytes, out);
+  if (rc) return rc;
+  out->data = const_cast<void*>(d_data);
+  out->owned = 0;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_decompressed_size(const zipnn_stream* s, size_t* nbytes, int* dtype) {
+  if (!s) return ZIPNN_EINVAL;
+  if (nbytes) *nbytes = s->orig_nbytes;
+  if (dtype) *dtype = s->dtype;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null, void* d_dst,
+                              size_t dst_nbytes, void* cuda_stream) {
+  zipnn_status rc = check_stream(s);
+  if (rc) return rc;
+  if (dst_nbytes != s->orig_nbytes) return ZIPNN_EINVAL;
+  if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (d_base_or_null != nullptr)) return ZIPNN_EINVAL;
+  if ((dst_nbytes && !d_dst) || !aligned16(d_dst) || !aligned16(d_base_or_null)) return ZIPNN_EINVAL;
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Job J = decode_job(s, d_base_or_null, d_dst);
+  cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
+                                   nullptr, st);
+  return cuda_status(e);
+}
+
+zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* const* d_bases,
+                                    void* const* d_dsts, int count, const zipnn_tuning* tuning,
+                                    void* cuda_stream) {
+  if (count < 0 || (count > 0 && (!streams || !d_dsts))) return ZIPNN_EINVAL;
+  if (count == 0) return ZIPNN_OK;
+  std::vector<Job> jobs((size_t)count);
+  uint64_t chunk = 0;
+  int max_groups = 1;
+  for (int i = 0; i < count; i++) {
+    const zipnn_stream* s = &streams[i];
+    zipnn_status rc = check_stream(s);
+    if (rc) return rc;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
+    if ((s->orig_nbytes && !d_dsts[i]) || !aligned16(d_dsts[i]) || !aligned16(base))
+      return ZIPNN_EINVAL;
+    jobs[i] = decode_job(s, base, d_dsts[i]);
+    jobs[i].chunk_begin = chunk;
+    chunk += jobs[i].n_chunks;
+    if ((int)s->n_groups > max_groups) max_groups = (int)s->n_groups;
+  }
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  void* dmem = nullptr;
+  const size_t tbytes = sizeof(Job) * (size_t)count;
+  cudaError_t e = cudaMallocAsync(&dmem, tbytes + 16, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  Job* d_jobs = static_cast<Job*>(dmem);
+  unsigned long long* d_ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dmem) + tbytes);
+  e = cudaMemcpyAsync(d_jobs, jobs.data(), tbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st);
+  cudaFreeAsync(dmem, st);
+  return cuda_status(e);
+}
+
+zipnn_status zipnn_sync_status(void* cuda_stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ZIPNN_ECUDA;
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ZIPNN_ECUDA;
+  if (v) {
+    uint32_t z = 0;
+    cudaMemcpy(err, &z, 4, cudaMemcpyHostToDevice);
+  }
+  if (v & 1u) return ZIPNN_ECORRUPT;
+  if (v & 2u) return ZIPNN_ENOMEM;
+  if (v & 4u) return ZIPNN_ETIMEOUT;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? ZIPNN_OK : ZIPNN_ECUDA;
+}
+
+void zipnn_stream_free(zipnn_stream* s) {
+  if (!s) return;
+  if (s->owned && s->data) cudaFree(s->data);
+  memset(s, 0, sizeof(*s));
+}
+
+}  // extern "C"

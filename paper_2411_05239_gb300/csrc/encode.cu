@@ -1,0 +1,690 @@
+// Encoder kernels of the GB300 ZipNN codec (ZipNN Sec. 3.1, 3.2, 4.2, 5.1).
+//
+//   k_hist      one CTA per chunk: reads the chunk once with 16-B loads (XOR
+//               with the delta base fused in), applies the exponent-extraction /
+//               byte-grouping permutation in registers and builds one 256-bin
+//               histogram per byte group (per-warp shared-memory copies).
+//   k_build     one warp per group-chunk: mode decision (ZERO / CONST / RAW /
+//               HUFF), length-limited code lengths by package-merge (limit 12),
+//               canonical codes and the table bytes.  A Shannon lower bound
+//               proves RAW without building a code for incompressible groups.
+//   k_scan      one CTA per tensor: exclusive scan of the padded payload sizes
+//               (the chunk map of Sec. 5.1) and the container size.
+//   k_pack      one CTA per chunk: per-sub-stream bit counts, a CTA scan for
+//               the sub-stream start bits, MSB-first bit packing, raw copies;
+//               writes the map entries (and, in extra CTAs, the headers).
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "zipnn_internal.cuh"
+
+namespace zipnn {
+
+namespace {
+
+constexpr int kHistThreads = 256;
+constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kBuildWarps = 4;
+
+struct JobRef {
+  const Job* table;  // device table, or nullptr to use `one`
+  Job one;
+  int n;
+};
+
+__device__ __forceinline__ const Job& job_at(const JobRef& r, int j) {
+  return r.table ? r.table[j] : r.one;
+}
+
+__device__ __forceinline__ int find_job_chunk(const JobRef& r, uint64_t chunk) {
+  if (!r.table) return 0;
+  return find_job(r.table, r.n, chunk);
+}
+
+__device__ __forceinline__ int find_job_gc(const JobRef& r, uint64_t gc) {
+  if (!r.table) return 0;
+  int lo = 0, hi = r.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (r.table[mid].gc_begin <= gc) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Load original vector v (16 bytes) of a chunk, XOR-ed with the base when
+// given; bytes past nb (a partial last vector) read as zero.
+__device__ __forceinline__ uint4 load_vec(const uint8_t* src, const uint8_t* base, uint64_t v,
+                                          uint64_t nb) {
+  uint4 a;
+  if ((v + 1) * 16 <= nb) {
+    a = __ldg(reinterpret_cast<const uint4*>(src) + v);
+    if (base) {
+      uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
+      a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+    }
+  } else {
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (uint64_t k = v * 16; k < nb; k++) {
+      uint32_t byte = src[k] ^ (base ? base[k] : 0u);
+      w[(k - v * 16) >> 2] |= byte << (8 * (k & 3));
+    }
+    a = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  return a;
+}
+
+// Group bytes of one vector: out[g][q] holds 4 symbols each (q < V/4).
+__device__ __forceinline__ void split_vec(int dtype, uint4 a, uint32_t out[4][4]) {
+  if (dtype == ZIPNN_FP32) {
+    uint32_t x[4] = {a.x, a.y, a.z, a.w}, g[4];
+    split32(x, g);
+    out[0][0] = g[0]; out[1][0] = g[1]; out[2][0] = g[2]; out[3][0] = g[3];
+  } else if (dtype == ZIPNN_U8) {
+    out[0][0] = a.x; out[0][1] = a.y; out[0][2] = a.z; out[0][3] = a.w;
+  } else {
+    split16(a.x, a.y, out[0][0], out[1][0]);
+    split16(a.z, a.w, out[0][1], out[1][1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_hist
+
+__global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kHistWarps][4][256];
+  const uint64_t chunk = blockIdx.x;
+  const int j = find_job_chunk(jr, chunk);
+  const Job& J = job_at(jr, j);
+  const int dtype = J.dtype;
+  const int es = elem_size(dtype), G = es, V = 16 / es;
+  const uint64_t c = chunk - J.chunk_begin;
+  const uint64_t off = c * J.chunk_bytes;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off);
+  const uint8_t* src = J.src + off;
+  const uint8_t* base = J.base ? J.base + off : nullptr;
+  const int warp = threadIdx.x >> 5;
+
+  for (int i = threadIdx.x; i < kHistWarps * 4 * 256; i += kHistThreads) (&sh[0][0][0])[i] = 0;
+  __syncthreads();
+
+  const uint64_t nvec = (nb + 15) / 16;
+  const uint64_t m = nb / es;
+  for (uint64_t v = threadIdx.x; v < nvec; v += kHistThreads) {
+    uint4 a = load_vec(src, base, v, nb);
+    uint32_t g[4][4];
+    split_vec(dtype, a, g);
+    const int valid = (int)min((uint64_t)V, m - v * V);
+    for (int gg = 0; gg < G; gg++) {
+      for (int k = 0; k < valid; k++) {
+        uint32_t sym = (g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        atomicAdd(&sh[warp][gg][sym], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int gg = 0; gg < G; gg++) {
+    for (int b = threadIdx.x; b < 256; b += kHistThreads) {
+      uint32_t s = 0;
+      for (int w = 0; w < kHistWarps; w++) s += sh[w][gg][b];
+      hist[(J.gc_begin + c * G + gg) * 256 + b] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_build: one warp per group-chunk.
+
+struct BuildSmem {
+  uint32_t leafw[256];    // leaf weights, sorted by (count asc, symbol desc)
+  uint8_t leafsym[256];
+  uint8_t lens[256];      // code length per symbol
+  uint32_t lst[2][512];   // package-merge lists (double buffer)
+  uint32_t pk[256];       // packages of the previous list
+  uint32_t leafbits[kMaxLen][16];  // which positions of list i are leaves
+  uint32_t keys[256];
+};
+
+__device__ __forceinline__ int upper_bound_u32(const uint32_t* a, int n, uint32_t x) {
+  int lo = 0, hi = n;  // first index with a[i] > x
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int n, uint32_t x) {
+  int lo = 0, hi = n;  // first index with a[i] >= x
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBuildWarps * 32)
+k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
+        uint32_t* __restrict__ codes, uint8_t* __restrict__ tabs, GcMeta* __restrict__ meta) {
+  __shared__ BuildSmem smem[kBuildWarps];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const uint64_t gc = (uint64_t)blockIdx.x * kBuildWarps + wid;
+  if (gc >= ngc_total) return;
+  BuildSmem& S = smem[wid];
+
+  const int j = find_job_gc(jr, gc);
+  const Job& J = job_at(jr, j);
+  const int es = elem_size(J.dtype), G = es;
+  const uint64_t local = gc - J.gc_begin;
+  const uint64_t c = local / G;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
+  const uint32_t m = (uint32_t)(nb / es);
+  const uint32_t T = J.lanes;
+
+  // counts of symbols s = lane + 32 k
+  uint32_t cnt[8];
+  uint32_t nz = 0;
+  for (int k = 0; k < 8; k++) {
+    cnt[k] = hist[gc * 256 + lane + 32 * k];
+    nz += __popc(__ballot_sync(0xffffffffu, cnt[k] > 0));
+  }
+  uint32_t* mycodes = codes + gc * 256;
+  for (int k = 0; k < 8; k++) mycodes[lane + 32 * k] = 0;
+
+  GcMeta res;
+  res.nz = nz;
+  res.value = 0;
+  res.size = 0;
+  if (nz <= 1) {
+    uint32_t sym = 0;
+    for (int k = 0; k < 8; k++) {
+      uint32_t b = __ballot_sync(0xffffffffu, cnt[k] > 0);
+      if (b) sym = 32 * k + (__ffs(b) - 1);
+    }
+    res.mode = (nz == 0 || sym == 0) ? kZero : kConst;
+    res.value = (res.mode == kConst) ? sym : 0;
+    if (lane == 0) meta[gc] = res;
+    return;
+  }
+
+  const uint32_t h = (uint32_t)align_up(12 + nz, 4);
+  const uint64_t fixed = (uint64_t)h + 4ull * (T - 1);
+  // Shannon bound: any prefix code spends >= sum c log2(m / c) bits.  If even
+  // that many bits cannot beat the raw size, the decision is RAW.
+  {
+    float part = 0.f;
+    const float lm = log2f((float)m);
+    for (int k = 0; k < 8; k++)
+      if (cnt[k]) part += (float)cnt[k] * (lm - log2f((float)cnt[k]));
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    float lower = part * (1.0f - 1e-4f) - 64.0f;
+    if (lower > 0.f) {
+      uint64_t lb_bits = (uint64_t)lower;
+      uint64_t lb_size = fixed + 4ull * ((lb_bits + 31) / 32);
+      if (lb_size + (m >> 6) >= m) {
+        res.mode = kRaw;
+        res.size = m;
+        if (lane == 0) meta[gc] = res;
+        return;
+      }
+    }
+  }
+
+  // --- sort the leaves by key = count << 8 | (255 - symbol) (ascending)
+  for (int k = 0; k < 8; k++) {
+    int s = lane + 32 * k;
+    S.keys[s] = cnt[k] ? ((cnt[k] << 8) | (uint32_t)(255 - s)) : 0u;
+  }
+  __syncwarp();
+  const uint32_t nempty = 256 - nz;
+  for (int k = 0; k < 8; k++) {
+    if (!cnt[k]) continue;
+    uint32_t key = S.keys[lane + 32 * k];
+    uint32_t r = 0;
+    for (int q = 0; q < 256; q++) r += (S.keys[q] < key);
+    r -= nempty;  // empty slots hold 0, smaller than every key
+    S.leafw[r] = cnt[k];
+    S.leafsym[r] = (uint8_t)(lane + 32 * k);
+  }
+  for (int i = lane; i < kMaxLen * 16; i += 32) (&S.leafbits[0][0])[i] = 0;
+  __syncwarp();
+
+  // --- package-merge: list 0 = leaves; list i = merge(leaves, packages(list i-1))
+  const int n = (int)nz;
+  int sp = n;
+  uint32_t* prev = S.lst[0];
+  for (int k = lane; k < n; k += 32) prev[k] = S.leafw[k];
+  __syncwarp();
+  int cur_buf = 1;
+  for (int lvl = 1; lvl < kMaxLen; lvl++) {
+    uint32_t* cur = S.lst[cur_buf];
+    const int np = sp >> 1;
+    for (int k = lane; k < np; k += 32) S.pk[k] = prev[2 * k] + prev[2 * k + 1];
+    __syncwarp();
+    for (int k = lane; k < np; k += 32) {
+      uint32_t w = S.pk[k];
+      cur[k + upper_bound_u32(S.leafw, n, w)] = w;      // after leaves of equal weight
+    }
+    for (int k = lane; k < n; k += 32) {
+      uint32_t w = S.leafw[k];
+      int pos = k + lower_bound_u32(S.pk, np, w);
+      cur[pos] = w;
+      atomicOr(&S.leafbits[lvl][pos >> 5], 1u << (pos & 31));
+    }
+    __syncwarp();
+    sp = n + np;
+    prev = cur;
+    cur_buf ^= 1;
+  }
+
+  // --- selection, from the last list down: a[i] leaves and p packages among
+  // the first c items; the packages select the first 2p items of list i-1.
+  int a[kMaxLen];
+  {
+    int take = 2 * (n - 1);
+    for (int lvl = kMaxLen - 1; lvl >= 1; lvl--) {
+      int leaves = 0;
+      for (int wv = 0; wv < 16; wv++) {
+        int lo = wv * 32;
+        if (lo >= take) break;
+        uint32_t bits = S.leafbits[lvl][wv];
+        int upto = take - lo;
+        if (upto < 32) bits &= (1u << upto) - 1u;
+        leaves += __popc(bits);
+      }
+      a[lvl] = leaves;
+      take = 2 * (take - leaves);
+    }
+    a[0] = take;  // list 0 holds leaves only
+  }
+  for (int k = lane; k < n; k += 32) {
+    int len = 0;
+    for (int lvl = 0; lvl < kMaxLen; lvl++) len += (k < a[lvl]);
+    S.lens[S.leafsym[k]] = (uint8_t)len;
+  }
+  for (int k = 0; k < 8; k++)
+    if (!cnt[k]) S.lens[lane + 32 * k] = 0;
+  __syncwarp();
+
+  // --- bit count and mode decision
+  uint32_t bits = 0;
+  uint8_t mylen[8];
+  for (int k = 0; k < 8; k++) {
+    mylen[k] = S.lens[lane + 32 * k];
+    bits += cnt[k] * mylen[k];
+  }
+  for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+  const uint64_t hsize = fixed + 4ull * ((bits + 31) / 32);
+  if (!(hsize + (m >> 6) < m)) {
+    res.mode = kRaw;
+    res.size = m;
+    if (lane == 0) meta[gc] = res;
+    return;
+  }
+  res.mode = kHuff;
+  res.size = (uint32_t)hsize;
+
+  // --- canonical codes (RFC 1951 Sec. 3.2.2) and the table bytes
+  uint32_t count[kMaxLen + 1];
+  for (int l = 0; l <= kMaxLen; l++) count[l] = 0;
+  for (int l = 1; l <= kMaxLen; l++)
+    for (int k = 0; k < 8; k++) count[l] += __popc(__ballot_sync(0xffffffffu, mylen[k] == l));
+  uint8_t* tab = tabs + gc * kTabBytes;
+  if (lane < kMaxLen) tab[lane] = (uint8_t)count[lane + 1];
+  uint32_t code0 = 0, first_idx = 0;
+  const uint32_t ltmask = (1u << lane) - 1u;
+  for (int l = 1; l <= kMaxLen; l++) {
+    code0 = (code0 + count[l - 1]) << 1;
+    uint32_t basek = 0;
+    for (int k = 0; k < 8; k++) {
+      uint32_t b = __ballot_sync(0xffffffffu, mylen[k] == l);
+      if (mylen[k] == l) {
+        uint32_t r = basek + __popc(b & ltmask);
+        mycodes[lane + 32 * k] = ((uint32_t)l << 16) | (code0 + r);
+        tab[12 + first_idx + r] = (uint8_t)(lane + 32 * k);
+      }
+      basek += __popc(b);
+    }
+    first_idx += count[l];
+  }
+  if (lane == 0) meta[gc] = res;
+}
+
+// ---------------------------------------------------------------------------
+// k_scan: one CTA per tensor, exclusive scan of padded payload sizes.
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(JobRef jr, const GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
+       uint64_t* __restrict__ totals, uint32_t* __restrict__ err) {
+  __shared__ uint64_t warp_sums[kScanThreads / 32];
+  const int j = blockIdx.x;
+  const Job& J = job_at(jr, j);
+  const int G = elem_size(J.dtype);
+  const uint64_t ngc = (uint64_t)J.n_chunks * G;
+  const uint64_t per = (ngc + kScanThreads - 1) / kScanThreads;
+  const uint64_t b0 = min(ngc, per * threadIdx.x), b1 = min(ngc, b0 + per);
+  uint64_t local = 0;
+  for (uint64_t i = b0; i < b1; i++) local += align_up(meta[J.gc_begin + i].size, 16);
+  // block exclusive scan of `local`
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t w = warp_sums[lane];
+    uint64_t wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    warp_sums[lane] = wi - w;
+  }
+  __syncthreads();
+  uint64_t run = warp_sums[wid] + incl - local;
+  for (uint64_t i = b0; i < b1; i++) {
+    offs[J.gc_begin + i] = run;
+    run += align_up(meta[J.gc_begin + i].size, 16);
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    const uint64_t P = kHdrBytes + ngc * kEntryBytes;
+    const uint64_t total = P + run;
+    totals[j] = total;
+    if (J.out_nbytes) *J.out_nbytes = total;
+    if (J.out_capacity && total > J.out_capacity) atomicOr(err, 2u);  // ENOMEM
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_pack: one CTA per chunk (extra CTAs write the headers).
+
+constexpr int kPackMaxLanes = 1024;
+
+__device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
+  for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+__device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v) {
+  for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+struct PackSmem {
+  uint32_t codes[4][256];
+  uint32_t start[4][kPackMaxLanes + 1];
+  GcMeta meta[4];
+  uint64_t off[4];
+  uint32_t capw[4];  // bitstream words available in the payload
+};
+
+__global__ void __launch_bounds__(256)
+k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
+       const uint8_t* __restrict__ tabs, const GcMeta* __restrict__ meta,
+       const uint64_t* __restrict__ offs, const uint64_t* __restrict__ totals) {
+  __shared__ PackSmem S;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+
+  if (blockIdx.x >= nchunks_total) {  // header CTAs
+    const int j = (int)(blockIdx.x - nchunks_total);
+    const Job& J = job_at(jr, j);
+    if (totals[j] > J.out_capacity) return;
+    if (tid == 0) {
+      uint8_t* h = J.dst;
+      const int G = elem_size(J.dtype);
+      const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+      h[0] = 'Z'; h[1] = 'N'; h[2] = 'N'; h[3] = '1';
+      h[4] = 1; h[5] = 0;
+      h[6] = (uint8_t)J.dtype;
+      h[7] = (uint8_t)J.flags;
+      put_u64(h + 8, J.nbytes);
+      put_u32(h + 16, J.chunk_bytes);
+      put_u32(h + 20, J.lanes);
+      put_u32(h + 24, (uint32_t)G);
+      put_u32(h + 28, J.n_chunks);
+      put_u64(h + 32, P);
+      put_u64(h + 40, totals[j]);
+      for (int k = 48; k < 64; k++) h[k] = 0;
+    }
+    return;
+  }
+
+  const uint64_t chunk = blockIdx.x;
+  const int j = find_job_chunk(jr, chunk);
+  const Job& J = job_at(jr, j);
+  if (totals[j] > J.out_capacity) return;
+  const int dtype = J.dtype;
+  const int es = elem_size(dtype), G = es, V = 16 / es;
+  const uint64_t c = chunk - J.chunk_begin;
+  const uint64_t off0 = c * J.chunk_bytes;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
+  const uint64_t m = nb / es;
+  const uint64_t nvec = (nb + 15) / 16;
+  const uint32_t T = J.lanes;
+  const uint8_t* src = J.src + off0;
+  const uint8_t* base = J.base ? J.base + off0 : nullptr;
+  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+  uint8_t* out = J.dst;
+  const uint64_t gc0 = J.gc_begin + c * G;
+
+  if (tid < G) {
+    S.meta[tid] = meta[gc0 + tid];
+    S.off[tid] = offs[gc0 + tid];
+    uint8_t* e = out + kHdrBytes + (c * G + tid) * kEntryBytes;
+    put_u64(e, S.off[tid]);
+    put_u32(e + 8, S.meta[tid].size);
+    e[12] = (uint8_t)S.meta[tid].mode;
+    e[13] = (uint8_t)S.meta[tid].value;
+    e[14] = 0;
+    e[15] = 0;
+  }
+  __syncthreads();
+  uint32_t huff_mask = 0, raw_mask = 0;
+  for (int g = 0; g < G; g++) {
+    if (S.meta[g].mode == kHuff) huff_mask |= 1u << g;
+    if (S.meta[g].mode == kRaw) raw_mask |= 1u << g;
+  }
+  for (int g = 0; g < G; g++)
+    if (huff_mask >> g & 1)
+      for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
+  __syncthreads();
+
+  if (huff_mask) {
+    // Phase A: bits of every sub-stream
+    for (uint32_t t = tid; t < T; t += nthr) {
+      uint32_t bits[4] = {0, 0, 0, 0};
+      for (uint64_t v = t; v < nvec; v += T) {
+        uint32_t g4[4][4];
+        split_vec(dtype, load_vec(src, base, v, nb), g4);
+        const int valid = (int)min((uint64_t)V, m - v * V);
+        for (int g = 0; g < G; g++) {
+          if (!(huff_mask >> g & 1)) continue;
+          for (int k = 0; k < valid; k++) {
+            uint32_t sym = (g4[g][k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            bits[g] += S.codes[g][sym] >> 16;
+          }
+        }
+      }
+      for (int g = 0; g < G; g++) S.start[g][t + 1] = bits[g];
+    }
+    __syncthreads();
+    // exclusive scan per Huffman group by one warp each
+    const int wid = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+    for (int g = wid; g < G; g += nwarps) {
+      if (!(huff_mask >> g & 1)) continue;
+      uint32_t* a = S.start[g];
+      if (lane == 0) a[0] = 0;
+      const uint32_t per = (T + 31) / 32;
+      const uint32_t b0 = min(T, per * lane), b1 = min(T, b0 + per);
+      uint32_t local = 0;
+      for (uint32_t i = b0; i < b1; i++) local += a[i + 1];
+      uint32_t incl = local;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += tt;
+      }
+      uint32_t run = incl - local;
+      __syncwarp();
+      for (uint32_t i = b0; i < b1; i++) {
+        uint32_t b = a[i + 1];
+        a[i + 1] = run + b;  // a[t] = start of t, a[t + 1] = end of t
+        run += b;
+      }
+    }
+    __syncthreads();
+    // table bytes, start offsets, zeroed bitstream
+    for (int g = 0; g < G; g++) {
+      if (!(huff_mask >> g & 1)) continue;
+      uint8_t* p = out + P + S.off[g];
+      const uint32_t nz = S.meta[g].nz;
+      const uint32_t h = (uint32_t)align_up(12 + nz, 4);
+      const uint8_t* tab = tabs + (gc0 + g) * kTabBytes;
+      for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
+      uint32_t* po = reinterpret_cast<uint32_t*>(p + h);
+      for (uint32_t t = 1 + tid; t < T; t += nthr) po[t - 1] = S.start[g][t];
+      uint32_t* words = po + (T - 1);
+      const uint32_t padded_words = (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * (T - 1)) / 4;
+      for (uint32_t w = tid; w < padded_words; w += nthr) words[w] = 0;
+      if (tid == 0) S.capw[g] = padded_words;
+    }
+    __syncthreads();
+    // Phase B: emit codes, MSB first
+    for (uint32_t t = tid; t < T; t += nthr) {
+      uint32_t* words[4];
+      uint64_t acc[4];
+      uint32_t nacc[4], wi[4];
+      bool first[4];
+      for (int g = 0; g < G; g++) {
+        const uint32_t nz = S.meta[g].nz;
+        const uint32_t h = (uint32_t)align_up(12 + nz, 4);
+        words[g] = reinterpret_cast<uint32_t*>(out + P + S.off[g] + h) + (T - 1);
+        const uint32_t st = (huff_mask >> g & 1) ? S.start[g][t] : 0;
+        acc[g] = 0;
+        nacc[g] = st & 31;
+        wi[g] = st >> 5;
+        first[g] = (st & 31) != 0;
+      }
+      for (uint64_t v = t; v < nvec; v += T) {
+        uint32_t g4[4][4];
+        split_vec(dtype, load_vec(src, base, v, nb), g4);
+        const int valid = (int)min((uint64_t)V, m - v * V);
+        for (int g = 0; g < G; g++) {
+          if (!(huff_mask >> g & 1)) continue;
+          for (int k = 0; k < valid; k++) {
+            uint32_t sym = (g4[g][k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            uint32_t cl = S.codes[g][sym];
+            uint32_t len = cl >> 16;
+            acc[g] = (acc[g] << len) | (cl & 0xFFFFu);
+            nacc[g] += len;
+            if (nacc[g] >= 32) {
+              nacc[g] -= 32;
+              uint32_t word = (uint32_t)(acc[g] >> nacc[g]);
+              acc[g] &= (1ull << nacc[g]) - 1ull;
+              if (wi[g] < S.capw[g]) {  // always true when the input did not change
+                if (first[g]) atomicOr(&words[g][wi[g]], word);
+                else words[g][wi[g]] = word;
+              }
+              first[g] = false;
+              wi[g]++;
+            }
+          }
+        }
+      }
+      for (int g = 0; g < G; g++) {
+        if (!(huff_mask >> g & 1)) continue;
+        if (nacc[g] > 0 && wi[g] < S.capw[g])
+          atomicOr(&words[g][wi[g]], (uint32_t)(acc[g] << (32 - nacc[g])));
+      }
+    }
+  }
+
+  if (raw_mask) {
+    // Phase C: raw group planes, coalesced
+    for (uint64_t v = tid; v < nvec; v += nthr) {
+      uint32_t g4[4][4];
+      split_vec(dtype, load_vec(src, base, v, nb), g4);
+      const bool full = (v + 1) * V <= m;
+      for (int g = 0; g < G; g++) {
+        if (!(raw_mask >> g & 1)) continue;
+        uint8_t* p = out + P + S.off[g] + v * V;
+        if (full) {
+          if (V == 8) *reinterpret_cast<uint2*>(p) = make_uint2(g4[g][0], g4[g][1]);
+          else if (V == 4) *reinterpret_cast<uint32_t*>(p) = g4[g][0];
+          else *reinterpret_cast<uint4*>(p) = make_uint4(g4[g][0], g4[g][1], g4[g][2], g4[g][3]);
+        } else {
+          for (uint64_t k = 0; k < m - v * V; k++) p[k] = (uint8_t)(g4[g][k >> 2] >> (8 * (k & 3)));
+        }
+      }
+    }
+    // zero padding after the raw bytes
+    for (int g = 0; g < G; g++) {
+      if (!(raw_mask >> g & 1)) continue;
+      uint8_t* p = out + P + S.off[g];
+      for (uint64_t k = m + tid; k < align_up(m, 16); k += nthr) p[k] = 0;
+    }
+  }
+}
+
+}  // namespace
+
+size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njobs) {
+  (void)nchunks_total;
+  size_t b = 0;
+  b += align_up(ngc_total * 256 * 4, 256);          // hist
+  b += align_up(ngc_total * 256 * 4, 256);          // codes
+  b += align_up(ngc_total * kTabBytes, 256);        // tabs
+  b += align_up(ngc_total * sizeof(GcMeta), 256);   // meta
+  b += align_up(ngc_total * 8, 256);                // offs
+  b += align_up((uint64_t)njobs * 8, 256);          // totals
+  return b + 256;
+}
+
+void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total, int njobs,
+                          EncodeScratch* s) {
+  (void)nchunks_total;
+  uint8_t* p = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<uintptr_t>(base), 256));
+  s->hist = reinterpret_cast<uint32_t*>(p); p += align_up(ngc_total * 256 * 4, 256);
+  s->codes = reinterpret_cast<uint32_t*>(p); p += align_up(ngc_total * 256 * 4, 256);
+  s->tabs = p; p += align_up(ngc_total * kTabBytes, 256);
+  s->meta = reinterpret_cast<GcMeta*>(p); p += align_up(ngc_total * sizeof(GcMeta), 256);
+  s->offs = reinterpret_cast<uint64_t*>(p); p += align_up(ngc_total * 8, 256);
+  s->totals = reinterpret_cast<uint64_t*>(p);
+}
+
+static JobRef make_ref(const Job* d_jobs, int njobs, const Job* h_one) {
+  JobRef r;
+  r.table = h_one ? nullptr : d_jobs;
+  if (h_one) r.one = *h_one;
+  else memset(&r.one, 0, sizeof(Job));
+  r.n = njobs;
+  return r;
+}
+
+// Launch k_hist, k_build and k_scan.  d_jobs is a device table of njobs jobs,
+// unless njobs == 1 and h_one is given (then the job is passed by value).
+cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                     uint64_t nchunks_total, uint64_t ngc_total,
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st) {
+  JobRef r = make_ref(d_jobs, njobs, h_one);
+  if (nchunks_total) {
+    k_hist<<<(unsigned)nchunks_total, kHistThreads, 0, st>>>(r, s.hist);
+    unsigned nb = (unsigned)((ngc_total + kBuildWarps - 1) / kBuildWarps);
+    k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.codes, s.tabs, s.meta);
+  }
+  k_scan<<<njobs, kScanThreads, 0, st>>>(r, s.meta, s.offs, s.totals, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                  uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
+                                  cudaStream_t st) {
+  JobRef r = make_ref(d_jobs, njobs, h_one);
+  int threads = max_lanes < 64 ? 64 : (max_lanes > 256 ? 256 : (max_lanes + 31) / 32 * 32);
+  k_pack<<<(unsigned)(nchunks_total + njobs), threads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
+                                                                s.meta, s.offs, s.totals);
+  return cudaGetLastError();
+}
+
+}  // namespace zipnn

@@ -1,0 +1,299 @@
+"""Thin Python binding of libzipnn_gpu.so (argument marshalling only).
+
+Every step of the codec runs in the library's CUDA kernels; this module only
+passes device pointers, sizes and the current CUDA stream through the C ABI
+declared in ``include/zipnn.h``.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libzipnn_gpu.so")
+
+BF16, FP16, FP32, U8 = 0, 1, 2, 3
+FLAG_DELTA = 1
+DEFAULT_CHUNK = 256 * 1024
+TORCH_TO_CODE = {torch.bfloat16: BF16, torch.float16: FP16, torch.float32: FP32,
+                 torch.uint8: U8, torch.int8: U8}
+CODE_TO_TORCH = {BF16: torch.bfloat16, FP16: torch.float16, FP32: torch.float32, U8: torch.uint8}
+ELEM_SIZE = {BF16: 2, FP16: 2, FP32: 4, U8: 1}
+STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECORRUPT", -4: "ECUDA", -5: "ETIMEOUT",
+          -6: "EBUSY"}
+
+EXPORTS = [
+    "zipnn_version", "zipnn_strerror", "zipnn_default_lanes", "zipnn_compress_bound",
+    "zipnn_compress_workspace_size", "zipnn_compress", "zipnn_delta", "zipnn_compress_into",
+    "zipnn_stream_wrap", "zipnn_decompressed_size", "zipnn_decompress",
+    "zipnn_batch_decompress", "zipnn_sync_status", "zipnn_stream_free",
+]
+
+
+class ZipnnError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class ZStream(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("nbytes", ctypes.c_uint64),
+                ("orig_nbytes", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32),
+                ("lanes", ctypes.c_uint32), ("n_chunks", ctypes.c_uint32),
+                ("n_groups", ctypes.c_uint32), ("owned", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ZTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("lut_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libzipnn_gpu.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, u32, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int
+    zsp = ctypes.POINTER(ZStream)
+    sig = {
+        "zipnn_version": ([], i32),
+        "zipnn_strerror": ([i32], ctypes.c_char_p),
+        "zipnn_default_lanes": ([i32, sz], u32),
+        "zipnn_compress_bound": ([sz, i32, sz], sz),
+        "zipnn_compress_workspace_size": ([sz, i32, sz], sz),
+        "zipnn_compress": ([vp, sz, i32, sz, zsp, vp], i32),
+        "zipnn_delta": ([vp, vp, sz, i32, sz, zsp, vp], i32),
+        "zipnn_compress_into": ([vp, vp, sz, i32, sz, u32, vp, sz, vp, sz, vp, vp], i32),
+        "zipnn_stream_wrap": ([vp, sz, zsp], i32),
+        "zipnn_decompressed_size": ([zsp, ctypes.POINTER(sz), ctypes.POINTER(i32)], i32),
+        "zipnn_decompress": ([zsp, vp, vp, sz, vp], i32),
+        "zipnn_batch_decompress": ([zsp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                                    ctypes.POINTER(ZTuning), vp], i32),
+        "zipnn_sync_status": ([vp], i32),
+        "zipnn_stream_free": ([zsp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ZipnnError(rc, what)
+
+
+def _sp(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class _CudaView:
+    """Expose (pointer, nbytes) of device memory to torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1",
+                                         "data": (ptr, False), "version": 3}
+
+
+def device_bytes(ptr: int, n: int) -> torch.Tensor:
+    """A uint8 CUDA tensor aliasing n bytes at ptr (no copy)."""
+    if n == 0:
+        return torch.empty(0, dtype=torch.uint8, device="cuda")
+    return torch.as_tensor(_CudaView(ptr, n), device="cuda")
+
+
+class Compressed:
+    """A container in device memory (torch-owned buffer or library-owned)."""
+
+    def __init__(self, zs: ZStream, buffer: torch.Tensor | None = None):
+        self.zs = zs
+        self.buffer = buffer
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.zs.nbytes)
+
+    @property
+    def orig_nbytes(self) -> int:
+        return int(self.zs.orig_nbytes)
+
+    @property
+    def dtype_code(self) -> int:
+        return int(self.zs.dtype)
+
+    @property
+    def is_delta(self) -> bool:
+        return bool(self.zs.flags & FLAG_DELTA)
+
+    @property
+    def ratio(self) -> float:
+        return self.nbytes / max(1, self.orig_nbytes)
+
+    def device_tensor(self) -> torch.Tensor:
+        if self.buffer is not None:
+            return self.buffer[: self.nbytes]
+        return device_bytes(self.zs.data, self.nbytes)
+
+    def to_bytes(self) -> bytes:
+        return self.device_tensor().cpu().numpy().tobytes()
+
+    def free(self) -> None:
+        if self.zs.owned:
+            lib().zipnn_stream_free(ctypes.byref(self.zs))
+        self.buffer = None
+
+    def __del__(self):
+        try:
+            if self.zs.owned:
+                lib().zipnn_stream_free(ctypes.byref(self.zs))
+        except Exception:
+            pass
+
+
+def _flat_u8(x: torch.Tensor) -> torch.Tensor:
+    if not x.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    return x.contiguous().view(-1).view(torch.uint8)
+
+
+def dtype_code(x: torch.Tensor, dtype: int | None) -> int:
+    if dtype is not None:
+        return dtype
+    if x.dtype not in TORCH_TO_CODE:
+        raise ValueError(f"unsupported dtype {x.dtype}")
+    return TORCH_TO_CODE[x.dtype]
+
+
+def default_lanes(dtype: int, chunk_bytes: int) -> int:
+    return int(lib().zipnn_default_lanes(dtype, chunk_bytes))
+
+
+def compress_bound(nbytes: int, dtype: int, chunk_bytes: int) -> int:
+    return int(lib().zipnn_compress_bound(nbytes, dtype, chunk_bytes))
+
+
+def workspace_size(nbytes: int, dtype: int, chunk_bytes: int) -> int:
+    return int(lib().zipnn_compress_workspace_size(nbytes, dtype, chunk_bytes))
+
+
+def compress_into(x: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor,
+                  out_nbytes: torch.Tensor | None = None, base: torch.Tensor | None = None,
+                  chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0, dtype: int | None = None,
+                  stream=None) -> None:
+    """Enqueue compression of x into the caller's buffers (no allocation, no sync)."""
+    code = dtype_code(x, dtype)
+    src = _flat_u8(x)
+    bp = _flat_u8(base).data_ptr() if base is not None else None
+    if base is not None and base.numel() * base.element_size() != src.numel():
+        raise ValueError("base size differs")
+    onp = out_nbytes.data_ptr() if out_nbytes is not None else None
+    rc = lib().zipnn_compress_into(src.data_ptr() if src.numel() else None, bp, src.numel(), code,
+                                   chunk_bytes, lanes, out.data_ptr(), out.numel(),
+                                   workspace.data_ptr(), workspace.numel(), onp, _sp(stream))
+    _check(rc, "zipnn_compress_into")
+
+
+def compress(x: torch.Tensor, chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0,
+             base: torch.Tensor | None = None, dtype: int | None = None, stream=None,
+             exact: bool = True) -> Compressed:
+    """Compress a CUDA tensor; the container lives in a torch-allocated buffer.
+    Reads the container size back (one synchronisation)."""
+    code = dtype_code(x, dtype)
+    n = x.numel() * x.element_size()
+    out = torch.empty(compress_bound(n, code, chunk_bytes), dtype=torch.uint8, device=x.device)
+    ws = torch.empty(workspace_size(n, code, chunk_bytes), dtype=torch.uint8, device=x.device)
+    onb = torch.zeros(1, dtype=torch.int64, device=x.device)
+    compress_into(x, out, ws, onb, base=base, chunk_bytes=chunk_bytes, lanes=lanes, dtype=code,
+                  stream=stream)
+    total = int(onb.item())
+    buf = out[:total].clone() if exact else out
+    return wrap(buf, total)
+
+
+def compress_lib(x: torch.Tensor, chunk_bytes: int = DEFAULT_CHUNK, base: torch.Tensor | None = None,
+                 dtype: int | None = None, stream=None) -> Compressed:
+    """Compress with the library allocating the container (zipnn_compress / zipnn_delta)."""
+    code = dtype_code(x, dtype)
+    src = _flat_u8(x)
+    zs = ZStream()
+    if base is None:
+        rc = lib().zipnn_compress(src.data_ptr() if src.numel() else None, src.numel(), code,
+                                  chunk_bytes, ctypes.byref(zs), _sp(stream))
+        _check(rc, "zipnn_compress")
+    else:
+        b = _flat_u8(base)
+        rc = lib().zipnn_delta(src.data_ptr() if src.numel() else None,
+                               b.data_ptr() if b.numel() else None, src.numel(), code,
+                               chunk_bytes, ctypes.byref(zs), _sp(stream))
+        _check(rc, "zipnn_delta")
+    return Compressed(zs, None)
+
+
+def delta(a: torch.Tensor, b: torch.Tensor, chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0,
+          stream=None) -> Compressed:
+    """Container of a XOR b (Sec. 4.2); decode with base=b."""
+    return compress(a, chunk_bytes=chunk_bytes, lanes=lanes, base=b, stream=stream)
+
+
+def wrap(buf: torch.Tensor, nbytes: int | None = None) -> Compressed:
+    """Interpret a uint8 CUDA tensor holding a container (reads its header)."""
+    if nbytes is None:
+        nbytes = buf.numel()
+    zs = ZStream()
+    rc = lib().zipnn_stream_wrap(buf.data_ptr(), nbytes, ctypes.byref(zs))
+    _check(rc, "zipnn_stream_wrap")
+    return Compressed(zs, buf)
+
+
+def decompress(c: Compressed, out: torch.Tensor | None = None, base: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """Decode a container into `out` (allocated if None) on the current stream."""
+    if out is None:
+        out = torch.empty(c.orig_nbytes // ELEM_SIZE[c.dtype_code],
+                          dtype=CODE_TO_TORCH[c.dtype_code], device="cuda")
+    o = _flat_u8(out)
+    bp = _flat_u8(base).data_ptr() if base is not None else None
+    rc = lib().zipnn_decompress(ctypes.byref(c.zs), bp, o.data_ptr() if o.numel() else None,
+                                o.numel(), _sp(stream))
+    _check(rc, "zipnn_decompress")
+    return out
+
+
+def tuning(threads: int = 0, ctas_per_sm: int = 0, lut_bits: int = 0) -> ZTuning:
+    return ZTuning(threads, ctas_per_sm, lut_bits, 0)
+
+
+def batch_decompress(cs: list[Compressed], outs: list[torch.Tensor],
+                     bases: list[torch.Tensor | None] | None = None, tune: ZTuning | None = None,
+                     stream=None) -> None:
+    """Decode many containers in one persistent launch (device work queue)."""
+    n = len(cs)
+    arr = (ZStream * n)(*[c.zs for c in cs])
+    dsts = (ctypes.c_void_p * n)(*[_flat_u8(o).data_ptr() for o in outs])
+    bp = None
+    if bases is not None:
+        bp = (ctypes.c_void_p * n)(*[(_flat_u8(b).data_ptr() if b is not None else None)
+                                     for b in bases])
+    rc = lib().zipnn_batch_decompress(arr, bp, dsts, n, ctypes.byref(tune) if tune else None,
+                                      _sp(stream))
+    _check(rc, "zipnn_batch_decompress")
+
+
+def sync_status(stream=None) -> None:
+    """Wait for the stream and raise if a kernel reported an error."""
+    _check(lib().zipnn_sync_status(_sp(stream)), "zipnn_sync_status")
