@@ -132,6 +132,23 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
                                  size_t out_capacity, void* d_workspace, size_t workspace_bytes,
                                  uint64_t* d_out_nbytes, void* cuda_stream);
 
+/* Batched compression of `count` tensors in one set of launches (one
+ * histogram, one code-build, one scan and one pack kernel for all of them).
+ * d_srcs[i] holds nbytes[i] bytes of dtypes[i]; d_bases may be NULL or hold a
+ * delta base (or NULL) per tensor; d_outs[i] must hold out_capacities[i] >=
+ * zipnn_compress_bound() bytes; the container sizes are written to
+ * d_out_nbytes[i] (device or host-mapped array, may be NULL).  The workspace
+ * (>= zipnn_batch_compress_workspace_size) also holds the job table, copied
+ * from host memory during the call.  Same errors as zipnn_compress_into. */
+size_t zipnn_batch_compress_workspace_size(const size_t* nbytes, const int* dtypes, int count,
+                                           size_t chunk_bytes);
+zipnn_status zipnn_batch_compress_into(const void* const* d_srcs, const void* const* d_bases,
+                                       const size_t* nbytes, const int* dtypes, int count,
+                                       size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+                                       const size_t* out_capacities, void* d_workspace,
+                                       size_t workspace_bytes, uint64_t* d_out_nbytes,
+                                       void* cuda_stream);
+
 /* Wrap a container that is already in device memory (e.g. copied from a file)
  * as a zipnn_stream: reads and validates its 64-B header (synchronous copy of
  * 64 bytes).  The stream does not own d_data.  ECORRUPT if the header is bad. */

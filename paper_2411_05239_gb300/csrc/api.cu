@@ -210,6 +210,88 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
   return cuda_status(e);
 }
 
+namespace {
+struct BatchPlan {
+  std::vector<Job> jobs;
+  uint64_t nchunks = 0, ngc = 0;
+  int max_lanes = 1;
+};
+
+zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d_bases,
+                                 const size_t* nbytes, const int* dtypes, int count,
+                                 size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+                                 const size_t* caps, uint64_t* d_out_nbytes, BatchPlan* bp) {
+  if (count <= 0 || !nbytes || !dtypes) return ZIPNN_EINVAL;
+  bp->jobs.resize((size_t)count);
+  for (int i = 0; i < count; i++) {
+    const int dt = dtypes[i];
+    const uint32_t ln = (lanes == 0 && dt >= ZIPNN_BF16 && dt <= ZIPNN_U8) ? lanes_default(dt, chunk_bytes) : lanes;
+    zipnn_status rc = check_params(dt, nbytes[i], chunk_bytes, ln);
+    if (rc) return rc;
+    const void* src = d_srcs ? d_srcs[i] : nullptr;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    void* out = d_outs ? d_outs[i] : nullptr;
+    if ((nbytes[i] && !src) || !aligned16(src) || !aligned16(base) || !aligned16(out)) return ZIPNN_EINVAL;
+    if (d_outs) {
+      if (!out) return ZIPNN_EINVAL;
+      if (!caps || caps[i] < zipnn_compress_bound(nbytes[i], dt, chunk_bytes)) return ZIPNN_ENOMEM;
+    }
+    Job J = make_job(src, base, out, nbytes[i], dt, chunk_bytes, ln, base ? ZIPNN_FLAG_DELTA : 0u);
+    J.out_capacity = caps ? caps[i] : 0;
+    J.out_nbytes = d_out_nbytes ? d_out_nbytes + i : nullptr;
+    J.chunk_begin = bp->nchunks;
+    J.gc_begin = bp->ngc;
+    bp->nchunks += J.n_chunks;
+    bp->ngc += (uint64_t)J.n_chunks * elem_size(dt);
+    if ((int)ln > bp->max_lanes) bp->max_lanes = (int)ln;
+    bp->jobs[i] = J;
+  }
+  return ZIPNN_OK;
+}
+
+size_t batch_ws_bytes(const BatchPlan& bp) {
+  return align_up(sizeof(Job) * bp.jobs.size(), 256) +
+         encode_scratch_bytes(bp.nchunks, bp.ngc, (int)bp.jobs.size());
+}
+}  // namespace
+
+extern "C" size_t zipnn_batch_compress_workspace_size(const size_t* nbytes, const int* dtypes,
+                                                      int count, size_t chunk_bytes) {
+  BatchPlan bp;
+  if (plan_batch_compress(nullptr, nullptr, nbytes, dtypes, count, chunk_bytes, 0, nullptr,
+                          nullptr, nullptr, &bp) != ZIPNN_OK)
+    return 0;
+  return batch_ws_bytes(bp);
+}
+
+extern "C" zipnn_status zipnn_batch_compress_into(
+    const void* const* d_srcs, const void* const* d_bases, const size_t* nbytes,
+    const int* dtypes, int count, size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+    const size_t* out_capacities, void* d_workspace, size_t workspace_bytes,
+    uint64_t* d_out_nbytes, void* cuda_stream) {
+  if (!d_outs) return ZIPNN_EINVAL;
+  BatchPlan bp;
+  zipnn_status rc = plan_batch_compress(d_srcs, d_bases, nbytes, dtypes, count, chunk_bytes,
+                                        lanes, d_outs, out_capacities, d_out_nbytes, &bp);
+  if (rc) return rc;
+  if (!d_workspace || workspace_bytes < batch_ws_bytes(bp)) return ZIPNN_ENOMEM;
+  uint32_t* err = err_word();
+  if (!err) return ZIPNN_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+  Job* d_jobs = reinterpret_cast<Job*>(ws);
+  ws += align_up(sizeof(Job) * bp.jobs.size(), 256);
+  EncodeScratch s;
+  encode_scratch_carve(ws, bp.nchunks, bp.ngc, count, &s);
+  cudaError_t e = cudaMemcpyAsync(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_encode_analyse_ex(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st);
+  if (e == cudaSuccess)
+    e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st);
+  return cuda_status(e);
+}
+
 static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t nbytes, int dtype,
                                    size_t chunk_bytes, zipnn_stream* out, void* cuda_stream) {
   if (!out) return ZIPNN_EINVAL;
