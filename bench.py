@@ -1,0 +1,452 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 ZipNN codec hot path; prints ONE JSON line.
+
+Workload (default): a synthetic 8B-class decoder-only checkpoint in BF16
+(Llama-3.1-8B shapes, 290 tensors, 8,030,257,152 parameters = 16.06 GB), the
+stand-in for the paper's Llama-3.1 measurements (ZipNN Table 2, Table 3).
+One step = batched compression of all 290 tensors (histogram, code build, map
+scan, bit packing: one CUDA-graph launch) followed by batched persistent
+decompression of all of them (one CUDA-graph launch).  `value` is the
+decompression throughput in GB/s of ORIGINAL bytes (decode is the path timed
+first); compression throughput, ratio and latency percentiles ride along.
+Inputs (16 GB) are larger than L2 (129 MB), so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank runs its own checkpoint (weak scaling; no data-path
+collective); the timed region is bracketed by a barrier and device syncs and
+the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "decompress/compress GB/s (original bytes) on 1 GB300, % HBM peak; ratio; p99 ms"
+FALLBACK_HBM = 6800.0
+
+
+def peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, local: int):
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+
+
+def all_max(vals: list[float], world: int) -> list[float]:
+    if world == 1:
+        return vals
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("decode.cu", "zipnn_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2411_05239_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(units: float) -> float | None:
+    """DRAM bytes per decode launch from the committed ncu summary, if it was
+    taken on the current decoder source (else null)."""
+    p = os.path.join(ROOT, "profiles", "decode_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_sha") != kernel_hash():
+            return None
+        return float(d["dram_bytes_per_orig_byte"]) * units
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(ts: list[torch.Tensor], chunk: int, sample_bytes: int) -> np.ndarray:
+    """Evenly spaced chunks of the checkpoint, concatenated on the host."""
+    total_chunks = sum(-(-t.numel() * 2 // chunk) for t in ts)
+    want = max(1, sample_bytes // chunk)
+    stride = max(1, total_chunks // want)
+    pieces, k, got = [], 0, 0
+    for t in ts:
+        b = t.view(torch.uint8)
+        n = -(-b.numel() // chunk)
+        for c in range(n):
+            if k % stride == 0 and got < want and (c + 1) * chunk <= b.numel():
+                pieces.append(b[c * chunk:(c + 1) * chunk].cpu().numpy())
+                got += 1
+            k += 1
+    return np.concatenate(pieces)
+
+
+def time_oracle(sample: np.ndarray, chunk: int) -> dict:
+    import oracle as O
+    t0 = time.perf_counter()
+    s = O.compress(sample, O.BF16, chunk)
+    t1 = time.perf_counter()
+    y = O.decompress(s)
+    t2 = time.perf_counter()
+    assert np.array_equal(y, sample)
+    return {"compress_s": t1 - t0, "decompress_s": t2 - t1, "bytes": int(sample.size),
+            "ratio": len(s) / sample.size}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The oracle (plain single-threaded C, as it stands) on host cores."""
+    world, rank, local = dist_info()
+    if rank != 0:
+        return 0
+    from paper_2411_05239_gb300 import workloads as W
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    specs = W.llama8b_specs()
+    if dev == "cuda":
+        ts = W.checkpoint_bf16(specs, seed=2, device=dev)
+    else:  # draw only the first layers on the host: same recipe, bounded cost
+        ts = W.checkpoint_bf16(specs[:12], seed=2, device=dev)
+    per_step = args.ref_sample_mb << 20
+    sample = oracle_sample(ts, args.chunk, per_step * (args.steps + args.warmup))
+    del ts
+    steps = []
+    n = len(sample) // (args.steps + args.warmup) // args.chunk * args.chunk
+    for i in range(args.warmup + args.steps):
+        r = time_oracle(sample[i * n:(i + 1) * n], args.chunk)
+        if i >= args.warmup:
+            steps.append(r)
+    dec = sum(r["decompress_s"] for r in steps)
+    comp = sum(r["compress_s"] for r in steps)
+    nb = sum(r["bytes"] for r in steps)
+    value = nb / dec / 1e9
+    desc = (f"{args.steps} steps x {n >> 20} MiB: evenly spaced {args.chunk >> 10} KiB chunks of "
+            "the 8B BF16 checkpoint, oracle compress + decompress, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (dec + comp) / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded N(0, 0.02/sqrt(2l+1)) BF16 weights, Llama-3.1-8B shapes)",
+        "config": {"workload": "llama8b_bf16_checkpoint", "chunk_bytes": args.chunk,
+                   "sample": desc},
+        "compress_gbs": nb / comp / 1e9, "ratio": statistics.mean(r["ratio"] for r in steps),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gb300(args):
+    from paper_2411_05239_gb300 import workloads as W
+    from paper_2411_05239_gb300 import zipnn as Z
+
+    world, rank, local = dist_info()
+    dist_init(world, local)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_kind = peaks()
+
+    specs = W.llama8b_specs(n_layers=args.layers, vocab=args.vocab)
+    ts = W.checkpoint_bf16(specs, seed=2, device=dev)
+    orig = sum(t.numel() * 2 for t in ts)
+
+    # compression plan (batched, graph-captured) and a first pass for the sizes
+    bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk)
+    bc()
+    Z.sync_status()
+    cs = bc.containers()
+    comp_bytes = sum(c.nbytes for c in cs)
+    outs = [torch.empty_like(t) for t in ts]
+    tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+    comp_plan = Z.plan_compress(bc)
+    dec_plan = Z.plan_decompress(cs, outs, tune=tune)
+
+    # correctness gate before timing (bit-exact round trip on the device)
+    comp_plan.launch()
+    dec_plan.launch()
+    Z.sync_status()
+    for t, o in zip(ts, outs):
+        if not torch.equal(t.view(torch.int16), o.view(torch.int16)):
+            raise SystemExit("round trip mismatch: refusing to report a number")
+
+    stream = torch.cuda.current_stream()
+    K, Wm = args.steps, args.warmup
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+
+    def step(e=None):
+        if e:
+            e[0].record(stream)
+        comp_plan.launch(stream)
+        if e:
+            e[1].record(stream)
+        dec_plan.launch(stream)
+        if e:
+            e[2].record(stream)
+
+    for _ in range(Wm):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    for k in range(K):
+        step(evs[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    Z.sync_status()
+    comp_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
+    dec_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
+    span_ms = evs[0][0].elapsed_time(evs[K - 1][2])
+    mc, md, mspan, mwall = all_max([statistics.mean(comp_ms), statistics.mean(dec_ms),
+                                    span_ms, wall], world)
+
+    # plain form: one decompress launch per tensor (same buffers)
+    pt_ms = None
+    if args.per_tensor:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            for c, o in zip(cs, outs):
+                Z.decompress(c, out=o)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            for c, o in zip(cs, outs):
+                Z.decompress(c, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        Z.sync_status()
+        pt_ms = all_max([e0.elapsed_time(e1) / K], world)[0]
+
+    # end to end through host buffers: H2D of the containers (pinned), batched
+    # decode, D2H of the tensors (pinned), every step
+    e2e = None
+    if args.e2e_steps > 0:
+        h_cont = [torch.empty(c.nbytes, dtype=torch.uint8, pin_memory=True) for c in cs]
+        for h, c in zip(h_cont, cs):
+            h.copy_(c.device_tensor())
+        h_out = [torch.empty(t.numel(), dtype=torch.bfloat16, pin_memory=True) for t in ts]
+        d_cont = [c.device_tensor() for c in cs]
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            for d, h in zip(d_cont, h_cont):
+                d.copy_(h, non_blocking=True)
+            dec_plan.launch(stream)
+            for h, o in zip(h_out, outs):
+                h.copy_(o, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_s = all_max([(time.perf_counter() - t0) / args.e2e_steps], world)[0]
+        ok = all(torch.equal(h.view(torch.int16), t.view(torch.int16).cpu())
+                 for h, t in zip(h_out[:3], ts[:3]))
+        if not ok:
+            raise SystemExit("e2e round trip mismatch")
+        e2e = {"value": world * orig / e2e_s / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": comp_bytes, "d2h_bytes_per_step": orig,
+               "steps": args.e2e_steps, "ms_per_step": e2e_s * 1e3,
+               "path": "pinned host containers -> H2D -> batched decode plan -> D2H pinned"}
+        del h_cont, h_out
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample_mb > 0:
+        sample = oracle_sample(ts, args.chunk, args.cpu_sample_mb << 20)
+        r = time_oracle(sample, args.chunk)
+        cpu = {"value": r["bytes"] / r["decompress_s"] / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle",
+               "compress_gbs": r["bytes"] / r["compress_s"] / 1e9,
+               "sample": (f"{r['bytes'] >> 20} MiB: evenly spaced {args.chunk >> 10} KiB chunks "
+                          "of the checkpoint; oracle compress then decompress, 1 thread")}
+
+    dec_s, comp_s = md / 1e3, mc / 1e3
+    value = world * orig / dec_s / 1e9
+    alg_dec = comp_bytes + orig                 # compressed bytes read + original written
+    alg_comp = orig + comp_bytes                # original read + compressed written
+    traffic = traffic_from_profile(orig)
+    srt = sorted(dec_ms)
+    p = lambda q: srt[min(len(srt) - 1, int(math.ceil(q * len(srt))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": mspan / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded N(0, 0.02/sqrt(2l+1)) BF16 weights, Llama-3.1-8B shapes)",
+        "config": {"workload": ("llama8b_bf16_checkpoint" if (args.layers, args.vocab) == (32, 128256)
+                                else f"llama_bf16_checkpoint_{args.layers}l_{args.vocab}v"),
+                   "tensors": len(ts),
+                   "params": orig // 2, "bytes": orig, "chunk_bytes": args.chunk,
+                   "lanes": Z.default_lanes(Z.BF16, args.chunk),
+                   "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
+                   "form": "batched: 1 graph launch compress + 1 graph launch persistent decode"},
+        "decompress_gbs": value, "compress_gbs": world * orig / comp_s / 1e9,
+        "ratio": comp_bytes / orig,
+        "decompress_ms": {"mean": md, "p50": p(0.5), "p99": p(0.99)},
+        "compress_ms": {"mean": mc},
+        "p99_ms": p(0.99),
+        "per_tensor_decompress_gbs": (world * orig / (pt_ms / 1e3) / 1e9) if pt_ms else None,
+        "roofline": {"kernel": "k_decode (batched persistent decode + merge)", "bound": "hbm",
+                     "achieved": alg_dec / dec_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": alg_dec / dec_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes": alg_dec},
+        "roofline_compress": {"kernels": "k_hist+k_build+k_scan+k_pack", "bound": "hbm",
+                              "achieved": alg_comp / comp_s / 1e9, "peak": hbm_peak,
+                              "unit": "GB/s", "frac": alg_comp / comp_s / 1e9 / hbm_peak,
+                              "algorithmic_bytes": alg_comp},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 5 * K,
+        "clocks": clocks,
+        "wall_s_timed": mwall,
+        "impl": "gb300",
+        "paper_context": "ZipNN CPU: up to 80 GB/s decompression, 13 GB/s compression "
+                         "(Xeon Platinum 8480+, 224 cores, 16 workers)",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--chunk", type=int, default=256 * 1024)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--per-tensor", type=int, default=1)
+    ap.add_argument("--cpu-sample-mb", type=int, default=384)
+    ap.add_argument("--layers", type=int, default=32, help="decoder layers (32 = 8B class)")
+    ap.add_argument("--vocab", type=int, default=128256, help="embedding/head rows")
+    ap.add_argument("--ref-sample-mb", type=int, default=48)
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -172,6 +172,32 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
                                     void* const* d_dsts, int count, const zipnn_tuning* tuning,
                                     void* cuda_stream);
 
+/* Plans (batching form): a fixed set of tensors prepared once -- job table
+ * uploaded to the device, scratch allocated, and the launches captured in a
+ * CUDA graph -- so each later batched (de)compression of the same buffers is
+ * one zipnn_plan_launch (one cudaGraphLaunch).  The pointers given at plan
+ * creation must stay valid, and their contents may change between launches
+ * (new weights in the same buffers); creation synchronises the device once.
+ *
+ * zipnn_plan_decompress: the persistent decoder over all containers (work
+ *   items pulled from a device ticket), as zipnn_batch_decompress.
+ * zipnn_plan_compress: the four encoder kernels over all tensors, as
+ *   zipnn_batch_compress_into, with the scratch owned by the plan.
+ * Errors: EINVAL for bad arguments (as the corresponding direct calls),
+ * ENOMEM/ECUDA if allocation or capture fails.  zipnn_plan_launch returns
+ * EINVAL when called with another device current than at creation. */
+typedef struct zipnn_plan zipnn_plan;
+zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* const* d_bases,
+                                   void* const* d_dsts, int count, const zipnn_tuning* tuning,
+                                   zipnn_plan** out);
+zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d_bases,
+                                 const size_t* nbytes, const int* dtypes, int count,
+                                 size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+                                 const size_t* out_capacities, uint64_t* d_out_nbytes,
+                                 zipnn_plan** out);
+zipnn_status zipnn_plan_launch(zipnn_plan* plan, void* cuda_stream);
+void zipnn_plan_destroy(zipnn_plan* plan);
+
 /* Wait for cuda_stream and return (and clear) the device error word:
  * ECORRUPT for a container rejected by a kernel, ETIMEOUT for a bounded wait
  * that gave up, else the CUDA error state as ECUDA, else OK. */

@@ -146,6 +146,10 @@ Job decode_job(const zipnn_stream* s, const void* base, void* dst) {
 
 }  // namespace
 
+namespace zipnn {
+uint32_t* plan_err_word() { return err_word(); }
+}  // namespace zipnn
+
 extern "C" {
 
 int zipnn_version(void) { return 1; }

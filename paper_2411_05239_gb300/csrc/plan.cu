@@ -1,0 +1,224 @@
+// Plans: a batch of tensors prepared once (device job table, scratch, work
+// ticket) and captured as a CUDA graph, so that every later batched
+// compression or persistent-kernel decompression of the same tensors costs one
+// cudaGraphLaunch.  This is the batching form of the codec: many tensors of
+// uneven sizes in one launch per kernel (ZipNN Sec. 5.1: chunks and byte groups
+// are independent, so one grid serves them all).
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "zipnn.h"
+#include "zipnn_internal.cuh"
+
+namespace zipnn {
+cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                     uint64_t nchunks_total, uint64_t ngc_total,
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st);
+cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                                  uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
+                                  cudaStream_t st);
+cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
+                             uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
+                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st);
+uint32_t* plan_err_word();
+}  // namespace zipnn
+
+using namespace zipnn;
+
+struct zipnn_plan {
+  int kind = 0;                 // 1 = decompress, 2 = compress
+  int device = 0;
+  void* dmem = nullptr;         // job table + ticket + scratch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t nchunks = 0;
+  int count = 0;
+};
+
+namespace {
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+zipnn_status fail(zipnn_plan* p, cudaError_t e) {
+  if (p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dmem) cudaFree(p->dmem);
+    delete p;
+  }
+  return e == cudaErrorMemoryAllocation ? ZIPNN_ENOMEM : ZIPNN_ECUDA;
+}
+
+// Capture `body` on a private stream into p->graph / p->exec.
+template <class F>
+cudaError_t capture(zipnn_plan* p, F body) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t eb = body(cs);
+    e = cudaStreamEndCapture(cs, &p->graph);
+    if (eb != cudaSuccess) e = eb;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  cudaStreamDestroy(cs);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* const* d_bases,
+                                   void* const* d_dsts, int count, const zipnn_tuning* tuning,
+                                   zipnn_plan** out) {
+  if (!out || count <= 0 || !streams || !d_dsts) return ZIPNN_EINVAL;
+  *out = nullptr;
+  std::vector<Job> jobs((size_t)count);
+  uint64_t chunk = 0;
+  int max_groups = 1;
+  for (int i = 0; i < count; i++) {
+    const zipnn_stream* s = &streams[i];
+    if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
+    if ((s->orig_nbytes && !d_dsts[i]) || !aligned16(d_dsts[i]) || !aligned16(base))
+      return ZIPNN_EINVAL;
+    if (s->n_groups != (uint32_t)elem_size(s->dtype) || s->dtype < 0 || s->dtype > ZIPNN_U8 ||
+        s->lanes < 1 || s->lanes > ZIPNN_MAX_LANES || s->chunk_bytes < ZIPNN_MIN_CHUNK ||
+        (uint64_t)s->n_chunks != (s->orig_nbytes + s->chunk_bytes - 1) / s->chunk_bytes)
+      return ZIPNN_EINVAL;
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.src = static_cast<const uint8_t*>(s->data);
+    J.base = static_cast<const uint8_t*>(base);
+    J.dst = static_cast<uint8_t*>(d_dsts[i]);
+    J.nbytes = s->orig_nbytes;
+    J.chunk_bytes = s->chunk_bytes;
+    J.lanes = s->lanes;
+    J.n_chunks = s->n_chunks;
+    J.dtype = s->dtype;
+    J.flags = s->flags;
+    J.stream_bytes = s->nbytes;
+    J.chunk_begin = chunk;
+    chunk += J.n_chunks;
+    if ((int)s->n_groups > max_groups) max_groups = (int)s->n_groups;
+    jobs[i] = J;
+  }
+  uint32_t* err = plan_err_word();
+  if (!err) return ZIPNN_ECUDA;
+  zipnn_plan* p = new zipnn_plan();
+  p->kind = 1;
+  p->count = count;
+  p->nchunks = chunk;
+  cudaGetDevice(&p->device);
+  const size_t tbytes = align_up(sizeof(Job) * (size_t)count, 256);
+  cudaError_t e = cudaMalloc(&p->dmem, tbytes + 256);
+  if (e != cudaSuccess) return fail(p, e);
+  Job* d_jobs = static_cast<Job*>(p->dmem);
+  auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p->dmem) + tbytes);
+  e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(p, e);
+  zipnn_tuning tu;
+  memset(&tu, 0, sizeof(tu));
+  if (tuning) tu = *tuning;
+  e = capture(p, [&](cudaStream_t cs) {
+    return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs);
+  });
+  if (e != cudaSuccess) return fail(p, e);
+  *out = p;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d_bases,
+                                 const size_t* nbytes, const int* dtypes, int count,
+                                 size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+                                 const size_t* out_capacities, uint64_t* d_out_nbytes,
+                                 zipnn_plan** out) {
+  if (!out || count <= 0 || !nbytes || !dtypes || !d_outs || !out_capacities) return ZIPNN_EINVAL;
+  *out = nullptr;
+  std::vector<Job> jobs((size_t)count);
+  uint64_t nch = 0, ngc = 0;
+  int max_lanes = 1;
+  for (int i = 0; i < count; i++) {
+    const int dt = dtypes[i];
+    if (dt < ZIPNN_BF16 || dt > ZIPNN_U8) return ZIPNN_EINVAL;
+    const uint32_t ln = lanes ? lanes : zipnn_default_lanes(dt, chunk_bytes);
+    const int es = elem_size(dt);
+    if (nbytes[i] % es || chunk_bytes < ZIPNN_MIN_CHUNK || chunk_bytes > ZIPNN_MAX_CHUNK ||
+        chunk_bytes % 16 || ln < 1 || ln > ZIPNN_MAX_LANES || ln > chunk_bytes / 16)
+      return ZIPNN_EINVAL;
+    const void* src = d_srcs ? d_srcs[i] : nullptr;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    if ((nbytes[i] && !src) || !d_outs[i] || !aligned16(src) || !aligned16(base) ||
+        !aligned16(d_outs[i]))
+      return ZIPNN_EINVAL;
+    if (out_capacities[i] < zipnn_compress_bound(nbytes[i], dt, chunk_bytes)) return ZIPNN_ENOMEM;
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.src = static_cast<const uint8_t*>(src);
+    J.base = static_cast<const uint8_t*>(base);
+    J.dst = static_cast<uint8_t*>(d_outs[i]);
+    J.nbytes = nbytes[i];
+    J.chunk_bytes = (uint32_t)chunk_bytes;
+    J.lanes = ln;
+    J.n_chunks = (uint32_t)((nbytes[i] + chunk_bytes - 1) / chunk_bytes);
+    J.dtype = dt;
+    J.flags = base ? ZIPNN_FLAG_DELTA : 0u;
+    J.out_capacity = out_capacities[i];
+    J.out_nbytes = d_out_nbytes ? d_out_nbytes + i : nullptr;
+    J.chunk_begin = nch;
+    J.gc_begin = ngc;
+    nch += J.n_chunks;
+    ngc += (uint64_t)J.n_chunks * es;
+    if ((int)ln > max_lanes) max_lanes = (int)ln;
+    jobs[i] = J;
+  }
+  uint32_t* err = plan_err_word();
+  if (!err) return ZIPNN_ECUDA;
+  zipnn_plan* p = new zipnn_plan();
+  p->kind = 2;
+  p->count = count;
+  p->nchunks = nch;
+  cudaGetDevice(&p->device);
+  const size_t tbytes = align_up(sizeof(Job) * (size_t)count, 256);
+  const size_t sbytes = encode_scratch_bytes(nch, ngc, count);
+  cudaError_t e = cudaMalloc(&p->dmem, tbytes + sbytes);
+  if (e != cudaSuccess) return fail(p, e);
+  Job* d_jobs = static_cast<Job*>(p->dmem);
+  EncodeScratch s;
+  encode_scratch_carve(static_cast<uint8_t*>(p->dmem) + tbytes, nch, ngc, count, &s);
+  e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(p, e);
+  e = capture(p, [&](cudaStream_t cs) {
+    cudaError_t e2 = launch_encode_analyse_ex(d_jobs, nullptr, count, nch, ngc, s, err, cs);
+    if (e2 == cudaSuccess) e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs);
+    return e2;
+  });
+  if (e != cudaSuccess) return fail(p, e);
+  *out = p;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_plan_launch(zipnn_plan* p, void* cuda_stream) {
+  if (!p || !p->exec) return ZIPNN_EINVAL;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return ZIPNN_EINVAL;
+  cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? ZIPNN_OK : ZIPNN_ECUDA;
+}
+
+void zipnn_plan_destroy(zipnn_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->dmem) cudaFree(p->dmem);
+  delete p;
+}
+
+}  // extern "C"

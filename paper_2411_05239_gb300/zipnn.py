@@ -30,6 +30,8 @@ EXPORTS = [
     "zipnn_compress_workspace_size", "zipnn_compress", "zipnn_delta", "zipnn_compress_into",
     "zipnn_stream_wrap", "zipnn_decompressed_size", "zipnn_decompress",
     "zipnn_batch_decompress", "zipnn_sync_status", "zipnn_stream_free",
+    "zipnn_batch_compress_workspace_size", "zipnn_batch_compress_into",
+    "zipnn_plan_decompress", "zipnn_plan_compress", "zipnn_plan_launch", "zipnn_plan_destroy",
 ]
 
 
@@ -83,6 +85,19 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(ZTuning), vp], i32),
         "zipnn_sync_status": ([vp], i32),
         "zipnn_stream_free": ([zsp], None),
+        "zipnn_batch_compress_workspace_size": ([ctypes.POINTER(sz), ctypes.POINTER(i32), i32,
+                                                 sz], sz),
+        "zipnn_batch_compress_into": ([ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(sz), ctypes.POINTER(i32), i32, sz, u32,
+                                       ctypes.POINTER(vp), ctypes.POINTER(sz), vp, sz, vp, vp],
+                                      i32),
+        "zipnn_plan_decompress": ([zsp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                                   ctypes.POINTER(ZTuning), ctypes.POINTER(vp)], i32),
+        "zipnn_plan_compress": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz),
+                                 ctypes.POINTER(i32), i32, sz, u32, ctypes.POINTER(vp),
+                                 ctypes.POINTER(sz), vp, ctypes.POINTER(vp)], i32),
+        "zipnn_plan_launch": ([vp, vp], i32),
+        "zipnn_plan_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -297,3 +312,97 @@ def batch_decompress(cs: list[Compressed], outs: list[torch.Tensor],
 def sync_status(stream=None) -> None:
     """Wait for the stream and raise if a kernel reported an error."""
     _check(lib().zipnn_sync_status(_sp(stream)), "zipnn_sync_status")
+
+
+def _ptrs(ts, allow_none=False):
+    n = len(ts)
+    return (ctypes.c_void_p * n)(*[(_flat_u8(t).data_ptr() if t is not None else None)
+                                   for t in ts])
+
+
+class BatchCompressor:
+    """Batched compression of a fixed list of CUDA tensors into caller buffers.
+
+    Arguments are marshalled once; each call() enqueues the four encoder
+    kernels for all tensors (zipnn_batch_compress_into)."""
+
+    def __init__(self, xs: list[torch.Tensor], chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0,
+                 bases: list[torch.Tensor | None] | None = None):
+        n = len(xs)
+        self.xs = xs
+        self.chunk_bytes = chunk_bytes
+        self.codes = [dtype_code(x, None) for x in xs]
+        self.sizes = [x.numel() * x.element_size() for x in xs]
+        self.caps = [compress_bound(b, c, chunk_bytes) for b, c in zip(self.sizes, self.codes)]
+        dev = xs[0].device
+        self.outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in self.caps]
+        self._nb = (ctypes.c_size_t * n)(*self.sizes)
+        self._dt = (ctypes.c_int * n)(*self.codes)
+        self._caps = (ctypes.c_size_t * n)(*self.caps)
+        ws = lib().zipnn_batch_compress_workspace_size(self._nb, self._dt, n, chunk_bytes)
+        if ws == 0:
+            raise ZipnnError(-1, "zipnn_batch_compress_workspace_size")
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.out_nbytes = torch.zeros(n, dtype=torch.int64, device=dev)
+        self._srcs = _ptrs(xs)
+        self._bases = _ptrs(bases) if bases is not None else None
+        self._outs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        self.lanes = lanes
+        self.n = n
+
+    def __call__(self, stream=None) -> None:
+        rc = lib().zipnn_batch_compress_into(self._srcs, self._bases, self._nb, self._dt, self.n,
+                                             self.chunk_bytes, self.lanes, self._outs, self._caps,
+                                             self.ws.data_ptr(), self.ws.numel(),
+                                             self.out_nbytes.data_ptr(), _sp(stream))
+        _check(rc, "zipnn_batch_compress_into")
+
+    def containers(self) -> list[Compressed]:
+        """Wrap the containers written by the last call (synchronises)."""
+        sizes = self.out_nbytes.cpu().tolist()
+        return [wrap(o, int(s)) for o, s in zip(self.outs, sizes)]
+
+
+class Plan:
+    """A captured CUDA graph of a batched compression or decompression."""
+
+    def __init__(self, handle: int, keep: list):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None) -> None:
+        _check(lib().zipnn_plan_launch(self.handle, _sp(stream)), "zipnn_plan_launch")
+
+    def close(self) -> None:
+        if self.handle:
+            lib().zipnn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_decompress(cs: list[Compressed], outs: list[torch.Tensor],
+                    bases: list[torch.Tensor | None] | None = None,
+                    tune: ZTuning | None = None) -> Plan:
+    n = len(cs)
+    arr = (ZStream * n)(*[c.zs for c in cs])
+    dsts = _ptrs(outs)
+    bp = _ptrs(bases) if bases is not None else None
+    h = ctypes.c_void_p()
+    rc = lib().zipnn_plan_decompress(arr, bp, dsts, n, ctypes.byref(tune) if tune else None,
+                                     ctypes.byref(h))
+    _check(rc, "zipnn_plan_decompress")
+    return Plan(h.value, [cs, outs, bases])
+
+
+def plan_compress(bc: BatchCompressor) -> Plan:
+    h = ctypes.c_void_p()
+    rc = lib().zipnn_plan_compress(bc._srcs, bc._bases, bc._nb, bc._dt, bc.n, bc.chunk_bytes,
+                                   bc.lanes, bc._outs, bc._caps, bc.out_nbytes.data_ptr(),
+                                   ctypes.byref(h))
+    _check(rc, "zipnn_plan_compress")
+    return Plan(h.value, [bc])

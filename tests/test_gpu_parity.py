@@ -263,3 +263,49 @@ def test_checkpoint_8b_batched_full_size():
         c = cs[i]
         chunks = sorted({0, c.zs.n_chunks - 1, int(rng.integers(0, c.zs.n_chunks))})
         _check_sampled_chunks(c, ts[i], Z.BF16, chunks)
+
+
+def test_batch_compress_and_plans_match_oracle():
+    xs = [W.gaussian(n, 0.02, 90 + i) for i, n in enumerate([1, 4097, 131072, 250_001])]
+    xs.append(W.gaussian(30_000, 0.05, 95, torch.float32))
+    xs.append(W.gaussian(10_000, 0.02, 96, torch.float16))
+    xd = [x.cuda() for x in xs]
+    bc = Z.BatchCompressor(xd, chunk_bytes=16384)
+    bc()
+    Z.sync_status()
+    cs = bc.containers()
+    for x, c in zip(xs, cs):
+        assert c.to_bytes() == O.compress(u8(x), Z.dtype_code(x, None), 16384)
+    # graph-captured compression writes the same containers
+    for o in bc.outs:
+        o.zero_()
+    pc = Z.plan_compress(bc)
+    pc.launch()
+    Z.sync_status()
+    for x, c in zip(xs, bc.containers()):
+        assert c.to_bytes() == O.compress(u8(x), Z.dtype_code(x, None), 16384)
+    # graph-captured persistent decode, launched twice
+    outs = [torch.empty_like(x) for x in xd]
+    pd = Z.plan_decompress(cs, outs, tune=Z.tuning(ctas_per_sm=2))
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        pd.launch()
+        Z.sync_status()
+        for x, o in zip(xs, outs):
+            assert torch.equal(o.cpu().view(torch.uint8), x.view(torch.uint8))
+    pd.close()
+    pc.close()
+
+
+def test_batch_compress_deltas():
+    nxt, base = W.delta_pair(120_000, seed=21)
+    other = W.gaussian(7000, 0.02, 22)
+    bc = Z.BatchCompressor([nxt.cuda(), other.cuda()], chunk_bytes=8192,
+                           bases=[base.cuda(), None])
+    bc()
+    Z.sync_status()
+    c0, c1 = bc.containers()
+    assert c0.is_delta and not c1.is_delta
+    assert c0.to_bytes() == O.delta(u8(nxt), u8(base), Z.BF16, 8192)
+    assert c1.to_bytes() == O.compress(u8(other), Z.BF16, 8192)
