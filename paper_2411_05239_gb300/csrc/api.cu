@@ -235,7 +235,9 @@ zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d
     const void* src = d_srcs ? d_srcs[i] : nullptr;
     const void* base = d_bases ? d_bases[i] : nullptr;
     void* out = d_outs ? d_outs[i] : nullptr;
-    if ((nbytes[i] && !src) || !aligned16(src) || !aligned16(base) || !aligned16(out)) return ZIPNN_EINVAL;
+    const bool query = (d_srcs == nullptr && d_outs == nullptr);  // workspace-size query
+    if ((!query && nbytes[i] && !src) || !aligned16(src) || !aligned16(base) || !aligned16(out))
+      return ZIPNN_EINVAL;
     if (d_outs) {
       if (!out) return ZIPNN_EINVAL;
       if (!caps || caps[i] < zipnn_compress_bound(nbytes[i], dt, chunk_bytes)) return ZIPNN_ENOMEM;

@@ -85,3 +85,15 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     # output smaller than the bound
     assert lib.zipnn_compress_into(fake, None, 64, 0, 4096, 0, fake, 16, fake, 1 << 20, None,
                                    None) == -2
+
+
+def test_batch_workspace_query_needs_no_pointers(lib):
+    lib.zipnn_batch_compress_workspace_size.restype = ctypes.c_size_t
+    lib.zipnn_batch_compress_workspace_size.argtypes = [ctypes.POINTER(ctypes.c_size_t),
+                                                       ctypes.POINTER(ctypes.c_int),
+                                                       ctypes.c_int, ctypes.c_size_t]
+    nb = (ctypes.c_size_t * 3)(2, 8196, 0)
+    dt = (ctypes.c_int * 3)(0, 2, 3)
+    assert lib.zipnn_batch_compress_workspace_size(nb, dt, 3, 16384) > 0
+    bad = (ctypes.c_size_t * 1)(3)
+    assert lib.zipnn_batch_compress_workspace_size(bad, (ctypes.c_int * 1)(0), 1, 16384) == 0
