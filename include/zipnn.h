@@ -132,6 +132,25 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
                                  size_t out_capacity, void* d_workspace, size_t workspace_bytes,
                                  uint64_t* d_out_nbytes, void* cuda_stream);
 
+/* No-allocation compression (the paper has no counterpart; this serves
+ * callers that cannot allocate device memory when they compress: plugins that
+ * only receive device pointers from a host framework whose caching allocator
+ * they cannot reach, latency-critical loops where a cudaMalloc/cudaFree could
+ * synchronise the device, processes with a device-memory budget fixed at
+ * start-up).  Same arguments and output as zipnn_compress_into minus the
+ * workspace: the scratch is a fixed 8 MiB device array inside the library
+ * (held by every GPU that loads it until exit), so one call handles at most
+ * 3,578 (chunk, byte group) pairs -- 447 MiB of BF16/FP16 or 223 MiB of FP32 at
+ * 256 KiB chunks; larger inputs return ZIPNN_ENOMEM before any launch.  It
+ * calls no allocator.  All calls on a device share that array: calls whose
+ * kernels overlap on the GPU (e.g. unordered streams) race and corrupt each
+ * other's output, so order them.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress); make it before any stream capture. */
+zipnn_status zipnn_compress_into_static(const void* d_src, const void* d_base_or_null,
+                                        size_t nbytes, int dtype, size_t chunk_bytes,
+                                        uint32_t lanes, void* d_out, size_t out_capacity,
+                                        uint64_t* d_out_nbytes, void* cuda_stream);
+
 /* Batched compression of `count` tensors in one set of launches (one
  * histogram, one code-build, one scan and one pack kernel for all of them).
  * d_srcs[i] holds nbytes[i] bytes of dtypes[i]; d_bases may be NULL or hold a
