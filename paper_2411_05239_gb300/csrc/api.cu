@@ -15,13 +15,15 @@
 namespace zipnn {
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
-                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st);
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
+                                     int max_groups);
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
                                   cudaStream_t st);
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
-                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st);
+                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
+                             int uniform_dtype);
 }  // namespace zipnn
 
 using namespace zipnn;
@@ -209,7 +211,7 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
   const uint64_t ngc = (uint64_t)J.n_chunks * elem_size(dtype);
   EncodeScratch s;
   encode_scratch_carve(d_workspace, J.n_chunks, ngc, 1, &s);
-  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st);
+  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0);
   if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st);
   return cuda_status(e);
 }
@@ -219,6 +221,7 @@ struct BatchPlan {
   std::vector<Job> jobs;
   uint64_t nchunks = 0, ngc = 0;
   int max_lanes = 1;
+  int max_groups = 1;
 };
 
 zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d_bases,
@@ -250,6 +253,7 @@ zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d
     bp->nchunks += J.n_chunks;
     bp->ngc += (uint64_t)J.n_chunks * elem_size(dt);
     if ((int)ln > bp->max_lanes) bp->max_lanes = (int)ln;
+    if (elem_size(dt) > bp->max_groups) bp->max_groups = elem_size(dt);
     bp->jobs[i] = J;
   }
   return ZIPNN_OK;
@@ -292,7 +296,8 @@ extern "C" zipnn_status zipnn_batch_compress_into(
   cudaError_t e = cudaMemcpyAsync(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = launch_encode_analyse_ex(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st);
+    e = launch_encode_analyse_ex(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st,
+                                 bp.max_groups);
   if (e == cudaSuccess)
     e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st);
   return cuda_status(e);
@@ -318,7 +323,7 @@ static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t
   if (e != cudaSuccess) return cuda_status(e);
   EncodeScratch s;
   encode_scratch_carve(scratch, J.n_chunks, ngc, 1, &s);
-  e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st);
+  e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0);
   uint64_t total = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, s.totals, 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -395,7 +400,7 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   Job J = decode_job(s, d_base_or_null, d_dst);
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
-                                   nullptr, st);
+                                   nullptr, st, s->dtype);
   return cuda_status(e);
 }
 
@@ -407,8 +412,10 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   std::vector<Job> jobs((size_t)count);
   uint64_t chunk = 0;
   int max_groups = 1;
+  int uniform = streams[0].dtype;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
+    if (s->dtype != uniform) uniform = -1;
     zipnn_status rc = check_stream(s);
     if (rc) return rc;
     const void* base = d_bases ? d_bases[i] : nullptr;
@@ -431,7 +438,8 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   unsigned long long* d_ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dmem) + tbytes);
   e = cudaMemcpyAsync(d_jobs, jobs.data(), tbytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st);
+    e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
+                         uniform);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

@@ -89,47 +89,81 @@ __device__ __forceinline__ void split_vec(int dtype, uint4 a, uint32_t out[4][4]
 }
 
 // ---------------------------------------------------------------------------
-// k_hist
+// k_hist: shared-memory atomics into per-warp histograms.  The exponent group
+// is concentrated on a few values, so its atomics collide on the same address:
+// it gets 4 copies per warp (lanes 8q..8q+7 use copy q), spaced 257 words apart
+// so equal symbols of different copies fall in different banks.
 
-__global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[kHistWarps][4][256];
-  const uint64_t chunk = blockIdx.x;
-  const int j = find_job_chunk(jr, chunk);
-  const Job& J = job_at(jr, j);
-  const int dtype = J.dtype;
-  const int es = elem_size(dtype), G = es, V = 16 / es;
-  const uint64_t c = chunk - J.chunk_begin;
+constexpr int kECopies = 4;
+constexpr int kEStride = 257;
+
+template <int DT>
+__device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist) {
+  constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
+  constexpr int V = 16 / (DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2));
+  constexpr int ES = 16 / V;
+  constexpr int WARP_WORDS = kECopies * kEStride + (G - 1) * 256;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t off = c * J.chunk_bytes;
   const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off);
   const uint8_t* src = J.src + off;
   const uint8_t* base = J.base ? J.base + off : nullptr;
-  const int warp = threadIdx.x >> 5;
 
-  for (int i = threadIdx.x; i < kHistWarps * 4 * 256; i += kHistThreads) (&sh[0][0][0])[i] = 0;
+  for (int i = tid; i < kHistWarps * WARP_WORDS; i += kHistThreads) sh[i] = 0;
   __syncthreads();
-
+  uint32_t* he = sh + warp * WARP_WORDS + (lane >> 3) * kEStride;
+  uint32_t* hr = sh + warp * WARP_WORDS + kECopies * kEStride;
   const uint64_t nvec = (nb + 15) / 16;
-  const uint64_t m = nb / es;
-  for (uint64_t v = threadIdx.x; v < nvec; v += kHistThreads) {
-    uint4 a = load_vec(src, base, v, nb);
+  const uint64_t m = nb / ES;
+  for (uint64_t v = tid; v < nvec; v += kHistThreads) {
     uint32_t g[4][4];
-    split_vec(dtype, a, g);
-    const int valid = (int)min((uint64_t)V, m - v * V);
-    for (int gg = 0; gg < G; gg++) {
-      for (int k = 0; k < valid; k++) {
-        uint32_t sym = (g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu;
-        atomicAdd(&sh[warp][gg][sym], 1u);
-      }
+    split_vec(DT, load_vec(src, base, v, nb), g);
+    if ((v + 1) * V <= m) {
+#pragma unroll
+      for (int k = 0; k < V; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+#pragma unroll
+      for (int gg = 1; gg < G; gg++)
+#pragma unroll
+        for (int k = 0; k < V; k++)
+          atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+    } else {
+      const int valid = (int)(m - v * V);
+      for (int k = 0; k < valid; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+      for (int gg = 1; gg < G; gg++)
+        for (int k = 0; k < valid; k++)
+          atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
     }
   }
   __syncthreads();
-  for (int gg = 0; gg < G; gg++) {
-    for (int b = threadIdx.x; b < 256; b += kHistThreads) {
+  for (int b = tid; b < 256; b += kHistThreads) {
+    uint32_t s0 = 0;
+    for (int w = 0; w < kHistWarps; w++)
+      for (int q = 0; q < kECopies; q++) s0 += sh[w * WARP_WORDS + q * kEStride + b];
+    hist[(J.gc_begin + c * G) * 256 + b] = s0;
+    for (int gg = 1; gg < G; gg++) {
       uint32_t s = 0;
-      for (int w = 0; w < kHistWarps; w++) s += sh[w][gg][b];
+      for (int w = 0; w < kHistWarps; w++) s += sh[w * WARP_WORDS + kECopies * kEStride + (gg - 1) * 256 + b];
       hist[(J.gc_begin + c * G + gg) * 256 + b] = s;
     }
   }
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __restrict__ hist) {
+  extern __shared__ uint32_t hsm[];
+  const uint64_t chunk = blockIdx.x;
+  const int j = find_job_chunk(jr, chunk);
+  const Job& J = job_at(jr, j);
+  const uint64_t c = chunk - J.chunk_begin;
+  switch (J.dtype) {
+    case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, hist); break;
+    case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, hist); break;
+    case ZIPNN_FP32: hist_chunk<ZIPNN_FP32>(J, c, hsm, hist); break;
+    default: hist_chunk<ZIPNN_U8>(J, c, hsm, hist); break;
+  }
+}
+
+static int hist_smem_bytes(int max_groups) {
+  return kHistWarps * (kECopies * kEStride + (max_groups - 1) * 256) * 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -402,8 +436,22 @@ k_scan(JobRef jr, const GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
 
 // ---------------------------------------------------------------------------
 // k_pack: one CTA per chunk (extra CTAs write the headers).
+//
+// Each sub-stream t is split into R consecutive parts (R = threads / T), so a
+// 512-thread CTA covers a 128-lane chunk with 4 threads per sub-stream.  The
+// unit (t, k) of part k of sub-stream t runs on thread k*T + t: lanes of a warp
+// hold consecutive t and touch consecutive 16-B vectors (coalesced).
+//   pass A: bits of every unit for each Huffman group; raw groups are written
+//           to their payloads in the same pass;
+//   scan  : exclusive scan of the unit bits in (t, k) order -> bit offset of
+//           every unit (the offset of (t, 0) is the sub-stream start);
+//   pass B: codes emitted MSB-first from each unit's offset (the words a unit
+//           shares with its neighbours are merged with atomicOr).
+// With 2 CTAs per SM the chunks in flight (~78 MB) stay in L2 between the
+// passes, so the input is read from DRAM once here.
 
-constexpr int kPackMaxLanes = 1024;
+constexpr int kPackThreads = 512;
+constexpr int kPackMaxUnits = 1024;
 
 __device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
   for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
@@ -412,21 +460,233 @@ __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v) {
   for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
 }
 
+template <int DT> struct PTraits;
+template <> struct PTraits<ZIPNN_BF16> { static constexpr int G = 2, V = 8; };
+template <> struct PTraits<ZIPNN_FP16> { static constexpr int G = 2, V = 8; };
+template <> struct PTraits<ZIPNN_FP32> { static constexpr int G = 4, V = 4; };
+template <> struct PTraits<ZIPNN_U8> { static constexpr int G = 1, V = 16; };
+
 struct PackSmem {
   uint32_t codes[4][256];
-  uint32_t start[4][kPackMaxLanes + 1];
+  uint32_t part[4][kPackMaxUnits + 1];  // unit bits, then exclusive offsets
+  uint32_t wsum[kPackThreads / 32];
   GcMeta meta[4];
   uint64_t off[4];
-  uint32_t capw[4];  // bitstream words available in the payload
+  uint32_t capw[4];   // bitstream words available in the payload
+  uint32_t hsz[4];    // table + start-offset bytes before the bitstream
 };
 
-__global__ void __launch_bounds__(256)
+// Exclusive scan of a[0..n) in place (block-wide); n <= kPackMaxUnits.
+__device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* wsum) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t per = (n + nthr - 1) / nthr;
+  const uint32_t b0 = min(n, per * tid), b1 = min(n, b0 + per);
+  uint32_t local = 0;
+  for (uint32_t i = b0; i < b1; i++) local += a[i];
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = nthr >> 5;
+    uint32_t w = lane < nw ? wsum[lane] : 0u, wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  uint32_t run = wsum[wid] + incl - local;
+  for (uint32_t i = b0; i < b1; i++) {
+    const uint32_t b = a[i];
+    a[i] = run;
+    run += b;
+  }
+  __syncthreads();
+}
+
+template <int DT>
+__device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t* codes,
+                           const uint8_t* tabs, const GcMeta* meta, const uint64_t* offs) {
+  constexpr int G = PTraits<DT>::G, V = PTraits<DT>::V, ES = 16 / V;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint64_t off0 = c * J.chunk_bytes;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
+  const uint64_t m = nb / ES;
+  const uint64_t nvec = (nb + 15) / 16;
+  const uint32_t T = J.lanes;
+  const uint32_t R = T <= (uint32_t)nthr ? (uint32_t)nthr / T : 1u;  // parts per sub-stream
+  const uint32_t units = T * R;                                        // <= max(nthr, T)
+  const uint64_t nvt = (nvec + T - 1) / T;                             // vectors of sub-stream 0
+  const uint64_t per = (nvt + R - 1) / R;                              // vectors per part
+  const uint8_t* src = J.src + off0;
+  const uint8_t* base = J.base ? J.base + off0 : nullptr;
+  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+  uint8_t* out = J.dst;
+  const uint64_t gc0 = J.gc_begin + c * G;
+
+  if (tid < G) {
+    S.meta[tid] = meta[gc0 + tid];
+    S.off[tid] = offs[gc0 + tid];
+    uint8_t* e = out + kHdrBytes + (c * G + tid) * kEntryBytes;
+    put_u64(e, S.off[tid]);
+    put_u32(e + 8, S.meta[tid].size);
+    e[12] = (uint8_t)S.meta[tid].mode;
+    e[13] = (uint8_t)S.meta[tid].value;
+    e[14] = 0;
+    e[15] = 0;
+  }
+  __syncthreads();
+  uint32_t huff = 0, raw = 0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if (S.meta[g].mode == kHuff) huff |= 1u << g;
+    if (S.meta[g].mode == kRaw) raw |= 1u << g;
+  }
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if (huff >> g & 1)
+      for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
+  __syncthreads();
+
+  // pass A: unit bits (+ raw planes)
+  for (uint32_t u = tid; u < units; u += nthr) {
+    const uint32_t t = u % T, k = u / T;
+    uint32_t bits[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) bits[g] = 0;
+    const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
+    for (uint64_t i = (uint64_t)k * per; i < i1; i++) {
+      const uint64_t v = t + i * T;
+      if (v >= nvec) break;
+      uint32_t g4[4][4];
+      split_vec(DT, load_vec(src, base, v, nb), g4);
+      const bool full = (v + 1) * V <= m;
+      const int valid = full ? V : (int)(m - v * V);
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (huff >> g & 1) {
+          if (full) {
+#pragma unroll
+            for (int q = 0; q < V; q++) bits[g] += S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu] >> 16;
+          } else {
+            for (int q = 0; q < valid; q++) bits[g] += S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu] >> 16;
+          }
+        } else if (raw >> g & 1) {
+          uint8_t* p = out + P + S.off[g] + v * V;
+          if (full) {
+            if (V == 8) *reinterpret_cast<uint2*>(p) = make_uint2(g4[g][0], g4[g][1]);
+            else if (V == 4) *reinterpret_cast<uint32_t*>(p) = g4[g][0];
+            else *reinterpret_cast<uint4*>(p) = make_uint4(g4[g][0], g4[g][1], g4[g][2], g4[g][3]);
+          } else {
+            for (int q = 0; q < valid; q++) p[q] = (uint8_t)(g4[g][q >> 2] >> (8 * (q & 3)));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) S.part[g][t * R + k] = bits[g];
+  }
+  // raw padding
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if (!(raw >> g & 1)) continue;
+    uint8_t* p = out + P + S.off[g];
+    for (uint64_t q = m + tid; q < align_up(m, 16); q += nthr) p[q] = 0;
+  }
+  if (!huff) return;
+  __syncthreads();
+
+  // scan unit bits -> unit offsets; table bytes, sub-stream starts, zeroed words
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if (!(huff >> g & 1)) continue;
+    block_exclusive_scan(S.part[g], units, S.wsum);
+    uint8_t* p = out + P + S.off[g];
+    const uint32_t nz = S.meta[g].nz;
+    const uint32_t h = (uint32_t)align_up(12 + nz, 4);
+    const uint8_t* tab = tabs + (gc0 + g) * kTabBytes;
+    for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
+    uint32_t* po = reinterpret_cast<uint32_t*>(p + h);
+    for (uint32_t t = 1 + tid; t < T; t += nthr) po[t - 1] = S.part[g][t * R];
+    uint32_t* words = po + (T - 1);
+    const uint32_t capw = (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * (T - 1)) / 4;
+    for (uint32_t w = tid; w < capw; w += nthr) words[w] = 0;
+    if (tid == 0) {
+      S.capw[g] = capw;
+      S.hsz[g] = h + 4 * (T - 1);
+    }
+  }
+  __syncthreads();
+
+  // pass B: emit
+  for (uint32_t u = tid; u < units; u += nthr) {
+    const uint32_t t = u % T, k = u / T;
+    uint32_t* words[G];
+    uint64_t acc[G];
+    uint32_t nacc[G], wi[G], capw[G];
+    bool first[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      words[g] = reinterpret_cast<uint32_t*>(out + P + S.off[g] + S.hsz[g]);
+      const uint32_t st = (huff >> g & 1) ? S.part[g][t * R + k] : 0u;
+      acc[g] = 0;
+      nacc[g] = st & 31;
+      wi[g] = st >> 5;
+      first[g] = (st & 31) != 0;
+      capw[g] = S.capw[g];
+    }
+    const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
+    for (uint64_t i = (uint64_t)k * per; i < i1; i++) {
+      const uint64_t v = t + i * T;
+      if (v >= nvec) break;
+      uint32_t g4[4][4];
+      split_vec(DT, load_vec(src, base, v, nb), g4);
+      const int valid = (int)min((uint64_t)V, m - v * V);
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (!(huff >> g & 1)) continue;
+#pragma unroll
+        for (int q = 0; q < V; q++) {
+          if (q >= valid) break;
+          const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
+          const uint32_t len = cl >> 16;
+          acc[g] = (acc[g] << len) | (cl & 0xFFFFu);
+          nacc[g] += len;
+          if (nacc[g] >= 32) {
+            nacc[g] -= 32;
+            const uint32_t word = (uint32_t)(acc[g] >> nacc[g]);
+            if (wi[g] < capw[g]) {  // always true when the input did not change
+              if (first[g]) atomicOr(&words[g][wi[g]], word);
+              else words[g][wi[g]] = word;
+            }
+            first[g] = false;
+            wi[g]++;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      if (!(huff >> g & 1)) continue;
+      if (nacc[g] > 0 && wi[g] < capw[g])
+        atomicOr(&words[g][wi[g]], (uint32_t)(acc[g] << (32 - nacc[g])));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPackThreads)
 k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
        const uint8_t* __restrict__ tabs, const GcMeta* __restrict__ meta,
        const uint64_t* __restrict__ offs, const uint64_t* __restrict__ totals) {
   __shared__ PackSmem S;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-
+  const int tid = threadIdx.x;
   if (blockIdx.x >= nchunks_total) {  // header CTAs
     const int j = (int)(blockIdx.x - nchunks_total);
     const Job& J = job_at(jr, j);
@@ -450,180 +710,16 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
     }
     return;
   }
-
   const uint64_t chunk = blockIdx.x;
   const int j = find_job_chunk(jr, chunk);
   const Job& J = job_at(jr, j);
   if (totals[j] > J.out_capacity) return;
-  const int dtype = J.dtype;
-  const int es = elem_size(dtype), G = es, V = 16 / es;
   const uint64_t c = chunk - J.chunk_begin;
-  const uint64_t off0 = c * J.chunk_bytes;
-  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
-  const uint64_t m = nb / es;
-  const uint64_t nvec = (nb + 15) / 16;
-  const uint32_t T = J.lanes;
-  const uint8_t* src = J.src + off0;
-  const uint8_t* base = J.base ? J.base + off0 : nullptr;
-  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
-  uint8_t* out = J.dst;
-  const uint64_t gc0 = J.gc_begin + c * G;
-
-  if (tid < G) {
-    S.meta[tid] = meta[gc0 + tid];
-    S.off[tid] = offs[gc0 + tid];
-    uint8_t* e = out + kHdrBytes + (c * G + tid) * kEntryBytes;
-    put_u64(e, S.off[tid]);
-    put_u32(e + 8, S.meta[tid].size);
-    e[12] = (uint8_t)S.meta[tid].mode;
-    e[13] = (uint8_t)S.meta[tid].value;
-    e[14] = 0;
-    e[15] = 0;
-  }
-  __syncthreads();
-  uint32_t huff_mask = 0, raw_mask = 0;
-  for (int g = 0; g < G; g++) {
-    if (S.meta[g].mode == kHuff) huff_mask |= 1u << g;
-    if (S.meta[g].mode == kRaw) raw_mask |= 1u << g;
-  }
-  for (int g = 0; g < G; g++)
-    if (huff_mask >> g & 1)
-      for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
-  __syncthreads();
-
-  if (huff_mask) {
-    // Phase A: bits of every sub-stream
-    for (uint32_t t = tid; t < T; t += nthr) {
-      uint32_t bits[4] = {0, 0, 0, 0};
-      for (uint64_t v = t; v < nvec; v += T) {
-        uint32_t g4[4][4];
-        split_vec(dtype, load_vec(src, base, v, nb), g4);
-        const int valid = (int)min((uint64_t)V, m - v * V);
-        for (int g = 0; g < G; g++) {
-          if (!(huff_mask >> g & 1)) continue;
-          for (int k = 0; k < valid; k++) {
-            uint32_t sym = (g4[g][k >> 2] >> (8 * (k & 3))) & 0xFFu;
-            bits[g] += S.codes[g][sym] >> 16;
-          }
-        }
-      }
-      for (int g = 0; g < G; g++) S.start[g][t + 1] = bits[g];
-    }
-    __syncthreads();
-    // exclusive scan per Huffman group by one warp each
-    const int wid = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-    for (int g = wid; g < G; g += nwarps) {
-      if (!(huff_mask >> g & 1)) continue;
-      uint32_t* a = S.start[g];
-      if (lane == 0) a[0] = 0;
-      const uint32_t per = (T + 31) / 32;
-      const uint32_t b0 = min(T, per * lane), b1 = min(T, b0 + per);
-      uint32_t local = 0;
-      for (uint32_t i = b0; i < b1; i++) local += a[i + 1];
-      uint32_t incl = local;
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t tt = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += tt;
-      }
-      uint32_t run = incl - local;
-      __syncwarp();
-      for (uint32_t i = b0; i < b1; i++) {
-        uint32_t b = a[i + 1];
-        a[i + 1] = run + b;  // a[t] = start of t, a[t + 1] = end of t
-        run += b;
-      }
-    }
-    __syncthreads();
-    // table bytes, start offsets, zeroed bitstream
-    for (int g = 0; g < G; g++) {
-      if (!(huff_mask >> g & 1)) continue;
-      uint8_t* p = out + P + S.off[g];
-      const uint32_t nz = S.meta[g].nz;
-      const uint32_t h = (uint32_t)align_up(12 + nz, 4);
-      const uint8_t* tab = tabs + (gc0 + g) * kTabBytes;
-      for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
-      uint32_t* po = reinterpret_cast<uint32_t*>(p + h);
-      for (uint32_t t = 1 + tid; t < T; t += nthr) po[t - 1] = S.start[g][t];
-      uint32_t* words = po + (T - 1);
-      const uint32_t padded_words = (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * (T - 1)) / 4;
-      for (uint32_t w = tid; w < padded_words; w += nthr) words[w] = 0;
-      if (tid == 0) S.capw[g] = padded_words;
-    }
-    __syncthreads();
-    // Phase B: emit codes, MSB first
-    for (uint32_t t = tid; t < T; t += nthr) {
-      uint32_t* words[4];
-      uint64_t acc[4];
-      uint32_t nacc[4], wi[4];
-      bool first[4];
-      for (int g = 0; g < G; g++) {
-        const uint32_t nz = S.meta[g].nz;
-        const uint32_t h = (uint32_t)align_up(12 + nz, 4);
-        words[g] = reinterpret_cast<uint32_t*>(out + P + S.off[g] + h) + (T - 1);
-        const uint32_t st = (huff_mask >> g & 1) ? S.start[g][t] : 0;
-        acc[g] = 0;
-        nacc[g] = st & 31;
-        wi[g] = st >> 5;
-        first[g] = (st & 31) != 0;
-      }
-      for (uint64_t v = t; v < nvec; v += T) {
-        uint32_t g4[4][4];
-        split_vec(dtype, load_vec(src, base, v, nb), g4);
-        const int valid = (int)min((uint64_t)V, m - v * V);
-        for (int g = 0; g < G; g++) {
-          if (!(huff_mask >> g & 1)) continue;
-          for (int k = 0; k < valid; k++) {
-            uint32_t sym = (g4[g][k >> 2] >> (8 * (k & 3))) & 0xFFu;
-            uint32_t cl = S.codes[g][sym];
-            uint32_t len = cl >> 16;
-            acc[g] = (acc[g] << len) | (cl & 0xFFFFu);
-            nacc[g] += len;
-            if (nacc[g] >= 32) {
-              nacc[g] -= 32;
-              uint32_t word = (uint32_t)(acc[g] >> nacc[g]);
-              acc[g] &= (1ull << nacc[g]) - 1ull;
-              if (wi[g] < S.capw[g]) {  // always true when the input did not change
-                if (first[g]) atomicOr(&words[g][wi[g]], word);
-                else words[g][wi[g]] = word;
-              }
-              first[g] = false;
-              wi[g]++;
-            }
-          }
-        }
-      }
-      for (int g = 0; g < G; g++) {
-        if (!(huff_mask >> g & 1)) continue;
-        if (nacc[g] > 0 && wi[g] < S.capw[g])
-          atomicOr(&words[g][wi[g]], (uint32_t)(acc[g] << (32 - nacc[g])));
-      }
-    }
-  }
-
-  if (raw_mask) {
-    // Phase C: raw group planes, coalesced
-    for (uint64_t v = tid; v < nvec; v += nthr) {
-      uint32_t g4[4][4];
-      split_vec(dtype, load_vec(src, base, v, nb), g4);
-      const bool full = (v + 1) * V <= m;
-      for (int g = 0; g < G; g++) {
-        if (!(raw_mask >> g & 1)) continue;
-        uint8_t* p = out + P + S.off[g] + v * V;
-        if (full) {
-          if (V == 8) *reinterpret_cast<uint2*>(p) = make_uint2(g4[g][0], g4[g][1]);
-          else if (V == 4) *reinterpret_cast<uint32_t*>(p) = g4[g][0];
-          else *reinterpret_cast<uint4*>(p) = make_uint4(g4[g][0], g4[g][1], g4[g][2], g4[g][3]);
-        } else {
-          for (uint64_t k = 0; k < m - v * V; k++) p[k] = (uint8_t)(g4[g][k >> 2] >> (8 * (k & 3)));
-        }
-      }
-    }
-    // zero padding after the raw bytes
-    for (int g = 0; g < G; g++) {
-      if (!(raw_mask >> g & 1)) continue;
-      uint8_t* p = out + P + S.off[g];
-      for (uint64_t k = m + tid; k < align_up(m, 16); k += nthr) p[k] = 0;
-    }
+  switch (J.dtype) {
+    case ZIPNN_BF16: pack_chunk<ZIPNN_BF16>(J, c, S, codes, tabs, meta, offs); break;
+    case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, codes, tabs, meta, offs); break;
+    case ZIPNN_FP32: pack_chunk<ZIPNN_FP32>(J, c, S, codes, tabs, meta, offs); break;
+    default: pack_chunk<ZIPNN_U8>(J, c, S, codes, tabs, meta, offs); break;
   }
 }
 
@@ -666,10 +762,14 @@ static JobRef make_ref(const Job* d_jobs, int njobs, const Job* h_one) {
 // unless njobs == 1 and h_one is given (then the job is passed by value).
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
-                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st) {
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
+                                     int max_groups) {
   JobRef r = make_ref(d_jobs, njobs, h_one);
+  if (h_one) max_groups = elem_size(h_one->dtype);
   if (nchunks_total) {
-    k_hist<<<(unsigned)nchunks_total, kHistThreads, 0, st>>>(r, s.hist);
+    const int hs = hist_smem_bytes(max_groups < 1 ? 4 : (max_groups > 4 ? 4 : max_groups));
+    if (hs > 48 * 1024) cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, hs);
+    k_hist<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist);
     unsigned nb = (unsigned)((ngc_total + kBuildWarps - 1) / kBuildWarps);
     k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.codes, s.tabs, s.meta);
   }
@@ -681,8 +781,8 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
                                   cudaStream_t st) {
   JobRef r = make_ref(d_jobs, njobs, h_one);
-  int threads = max_lanes < 64 ? 64 : (max_lanes > 256 ? 256 : (max_lanes + 31) / 32 * 32);
-  k_pack<<<(unsigned)(nchunks_total + njobs), threads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
+  (void)max_lanes;
+  k_pack<<<(unsigned)(nchunks_total + njobs), kPackThreads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
                                                                 s.meta, s.offs, s.totals);
   return cudaGetLastError();
 }

@@ -16,13 +16,15 @@
 namespace zipnn {
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
-                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st);
+                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
+                                     int max_groups);
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
                                   cudaStream_t st);
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
-                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st);
+                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
+                             int uniform_dtype);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
@@ -81,8 +83,10 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   std::vector<Job> jobs((size_t)count);
   uint64_t chunk = 0;
   int max_groups = 1;
+  int uniform = streams[0].dtype;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
+    if (s->dtype != uniform) uniform = -1;
     if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
     const void* base = d_bases ? d_bases[i] : nullptr;
     if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
@@ -127,7 +131,8 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   memset(&tu, 0, sizeof(tu));
   if (tuning) tu = *tuning;
   e = capture(p, [&](cudaStream_t cs) {
-    return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs);
+    return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
+                            uniform);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
@@ -143,7 +148,7 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   *out = nullptr;
   std::vector<Job> jobs((size_t)count);
   uint64_t nch = 0, ngc = 0;
-  int max_lanes = 1;
+  int max_lanes = 1, max_groups = 1;
   for (int i = 0; i < count; i++) {
     const int dt = dtypes[i];
     if (dt < ZIPNN_BF16 || dt > ZIPNN_U8) return ZIPNN_EINVAL;
@@ -176,6 +181,7 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
     nch += J.n_chunks;
     ngc += (uint64_t)J.n_chunks * es;
     if ((int)ln > max_lanes) max_lanes = (int)ln;
+    if (es > max_groups) max_groups = es;
     jobs[i] = J;
   }
   uint32_t* err = plan_err_word();
@@ -195,7 +201,8 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(p, e);
   e = capture(p, [&](cudaStream_t cs) {
-    cudaError_t e2 = launch_encode_analyse_ex(d_jobs, nullptr, count, nch, ngc, s, err, cs);
+    cudaError_t e2 = launch_encode_analyse_ex(d_jobs, nullptr, count, nch, ngc, s, err, cs,
+                                              max_groups);
     if (e2 == cudaSuccess) e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs);
     return e2;
   });
