@@ -426,6 +426,111 @@ def run_gb300(args):
     return 0
 
 
+def run_serve(args):
+    """Served stream: 2,000 requests, Poisson arrivals at 200 req/s, compress /
+    decompress (70/30), BF16/FP16/FP32 (60/20/20), sizes log-uniform in
+    [64 KiB, 2 GiB], 15% deltas against a resident base; HBM budget 40 GB.
+    Served (continuous batching) and plain (serial, one stream, one launch per
+    request) paths replay the same trace; latency = completion - arrival."""
+    import threading as th
+    from paper_2411_05239_gb300 import workloads as W
+    from paper_2411_05239_gb300 import zipnn as Z
+
+    torch.cuda.set_device(0)
+    trace = W.request_trace(n=args.serve_requests, seed=4)
+    maxb = max(r.nbytes for r in trace)
+    pools = {}
+    for k, (dt, tdt) in enumerate(W.TORCH_DTYPE.items()):
+        es = torch.tensor([], dtype=tdt).element_size()
+        n = maxb // es + 1
+        nxt, base = W.delta_pair(n, seed=40 + k, device="cuda")
+        plain = W.gaussian(n, 0.02, seed=50 + k, dtype=tdt, device="cuda")
+        pools[dt] = (plain, nxt.to(tdt) if tdt != torch.bfloat16 else nxt,
+                     base.to(tdt) if tdt != torch.bfloat16 else base)
+    def inputs(r):
+        es = {"bf16": 2, "fp16": 2, "fp32": 4}[r.dtype]
+        n = r.nbytes // es
+        plain, nxt, base = pools[r.dtype]
+        return (nxt[:n], base[:n]) if r.delta else (plain[:n], None)
+    containers = {}
+    for r in trace:
+        if r.op == "decompress":
+            x, b = inputs(r)
+            containers[r.rid] = Z.compress(x, base=b)
+    torch.cuda.synchronize()
+
+    # served path
+    srv = Z.Server(args.serve_budget_gb << 30, slots=args.serve_slots)
+    lat, done_bytes, t_first, t_last = {}, 0, None, 0.0
+    t0 = time.perf_counter() + 0.5
+    def submitter():
+        for r in trace:
+            dt = t0 + r.t_arrival - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            x, b = inputs(r)
+            if r.op == "compress":
+                srv.submit_compress(x, base=b, tag=r.rid)
+            else:
+                srv.submit_decompress(containers[r.rid], base=b, tag=r.rid)
+    th_sub = th.Thread(target=submitter)
+    th_sub.start()
+    while len(lat) < len(trace):
+        for c in srv.poll():
+            if c.status != 0:
+                raise SystemExit(f"served request {c.tag} failed: {c.status}")
+            lat[c.tag] = (c.t_done - c.t_submit) * 1e3
+            done_bytes += trace[c.tag].nbytes
+            t_first = c.t_submit if t_first is None else min(t_first, c.t_submit)
+            t_last = max(t_last, c.t_done)
+            srv.release(c.id)
+        time.sleep(0.0002)
+    th_sub.join()
+    st = srv.stats()
+    srv.close()
+    served = sorted(lat.values())
+
+    # plain path: serial, one stream, one launch set per request
+    out_buf = torch.empty(Z.compress_bound(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
+                          device="cuda")   # FP32 has the largest bound and workspace
+    ws = torch.empty(Z.workspace_size(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
+                     device="cuda")
+    dec_out = torch.empty(maxb // 2 + 16, dtype=torch.int16, device="cuda")
+    plat = []
+    t0 = time.perf_counter() + 0.2
+    for r in trace:
+        dt = t0 + r.t_arrival - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        x, b = inputs(r)
+        if r.op == "compress":
+            Z.compress_into(x, out_buf, ws, base=b)
+        else:
+            c = containers[r.rid]
+            Z.decompress(c, out=dec_out.view(torch.uint8)[:c.orig_nbytes].view(x.dtype), base=b)
+        torch.cuda.synchronize()
+        plat.append((time.perf_counter() - (t0 + r.t_arrival)) * 1e3)
+    Z.sync_status()
+    plain = sorted(plat)
+    pct = lambda a, q: a[min(len(a) - 1, int(math.ceil(q * len(a))) - 1)]
+    total = sum(r.nbytes for r in trace)
+    line = {
+        "metric": METRIC, "value": done_bytes / (t_last - t_first) / 1e9, "unit": "GB/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "served_stream", "requests": len(trace), "rate_per_s": 200,
+                   "budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
+                   "offered_gb": total / 1e9},
+        "served": {"p50_ms": pct(served, 0.5), "p99_ms": pct(served, 0.99),
+                   "mean_ms": statistics.mean(served), "batches": st.batches,
+                   "max_batch": st.max_batch, "gbs": done_bytes / (t_last - t_first) / 1e9},
+        "plain": {"p50_ms": pct(plain, 0.5), "p99_ms": pct(plain, 0.99),
+                  "mean_ms": statistics.mean(plain)},
+        "impl": "gb300",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,11 +545,17 @@ def main(argv=None):
     ap.add_argument("--cpu-sample-mb", type=int, default=384)
     ap.add_argument("--layers", type=int, default=32, help="decoder layers (32 = 8B class)")
     ap.add_argument("--vocab", type=int, default=128256, help="embedding/head rows")
+    ap.add_argument("--workload", default="checkpoint", choices=["checkpoint", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--ref-sample-mb", type=int, default=48)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gb300(args)
 
 

@@ -83,8 +83,12 @@ typedef struct zipnn_stream {
 typedef struct zipnn_tuning {
     int32_t threads;      /* threads per CTA (multiple of 32, 0 = default) */
     int32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid */
-    int32_t lut_bits;     /* decode table width: 12 (full) or 8..11 (two-level) */
-    int32_t reserved;
+    int32_t lut_bits;     /* decode table width W in bits: 10, 11 or 12 (0 = 11);
+                             codes longer than W take a slow path */
+    int32_t debug_flags;  /* 0.  Bit 0 is fault injection for tests: the decoder
+                             waits for 16 bytes that are never copied, so its
+                             bounded wait gives up after 100 ms and the call
+                             reports ZIPNN_ETIMEOUT via zipnn_sync_status */
 } zipnn_tuning;
 
 /* Library version (the container version is 1). */
@@ -216,6 +220,60 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
                                  zipnn_plan** out);
 zipnn_status zipnn_plan_launch(zipnn_plan* plan, void* cuda_stream);
 void zipnn_plan_destroy(zipnn_plan* plan);
+
+/* Request server (serving form): continuous batching of compress and
+ * decompress requests with admission against a device-memory budget.
+ * zipnn_server_create allocates a device arena of budget_bytes (outputs and
+ * scratch live there) and `slots` CUDA streams, and starts a scheduler thread
+ * on the current device.  zipnn_server_submit (thread-safe, non-blocking)
+ * queues a request; the scheduler admits requests in arrival order while their
+ * input bytes (caller-owned, charged only), output and scratch fit the budget
+ * and a slot is free, and launches everything admitted in one pass as one
+ * batch (one batched compression + one persistent batched decode) on that
+ * slot's stream, so batches on different slots overlap on the device.
+ * zipnn_server_poll returns completions; each output stays in the arena (and
+ * charged) until zipnn_server_release.  A request whose footprint exceeds the
+ * whole budget is refused at submit with EBUSY.  The caller's inputs must stay
+ * valid until the request completes.  Times are seconds on a steady clock. */
+#define ZIPNN_OP_COMPRESS 0
+#define ZIPNN_OP_DECOMPRESS 1
+typedef struct zipnn_request {
+    int32_t op;            /* ZIPNN_OP_COMPRESS or ZIPNN_OP_DECOMPRESS */
+    int32_t dtype;         /* compress: zipnn_dtype of the input */
+    const void* d_input;   /* compress: the tensor (16-B aligned) */
+    uint64_t input_bytes;  /* compress: tensor bytes */
+    zipnn_stream container;/* decompress: the container to decode */
+    const void* d_base;    /* delta base (compress: makes a delta; decompress: required
+                              for delta containers), else NULL */
+    uint64_t chunk_bytes;  /* compress: 0 = 256 KiB */
+    uint64_t tag;          /* caller's value, echoed in the completion */
+} zipnn_request;
+typedef struct zipnn_completion {
+    uint64_t id;           /* server id returned by submit */
+    uint64_t tag;
+    int32_t status;        /* zipnn_status of the launch */
+    int32_t op;
+    void* d_output;        /* container (compress) or tensor (decompress) in the arena */
+    uint64_t output_bytes;
+    double t_submit, t_admit, t_done;
+} zipnn_completion;
+typedef struct zipnn_server_stats {
+    uint64_t submitted, completed, batches, max_batch, bytes_processed;
+    uint64_t arena_used, inputs_charged;
+} zipnn_server_stats;
+typedef struct zipnn_server zipnn_server;
+zipnn_status zipnn_server_create(uint64_t budget_bytes, int slots, zipnn_server** out);
+zipnn_status zipnn_server_submit(zipnn_server* s, const zipnn_request* r, uint64_t* id);
+int zipnn_server_poll(zipnn_server* s, zipnn_completion* out, int max);
+zipnn_status zipnn_server_release(zipnn_server* s, uint64_t id);
+/* Wait until nothing is queued or running (ETIMEOUT after timeout_s).  Queued
+ * requests are admitted only as budget frees up, so a caller that holds
+ * unreleased outputs must keep releasing them while it waits. */
+zipnn_status zipnn_server_drain(zipnn_server* s, double timeout_s);
+zipnn_status zipnn_server_get_stats(zipnn_server* s, zipnn_server_stats* st);
+/* Stop the scheduler: queued requests are cancelled (never run), running
+ * batches complete, then the arena and streams are freed. */
+void zipnn_server_destroy(zipnn_server* s);
 
 /* Wait for cuda_stream and return (and clear) the device error word:
  * ECORRUPT for a container rejected by a kernel, ETIMEOUT for a bounded wait

@@ -1,0 +1,122 @@
+"""Autotuner for the batched codec: chunk size, sub-stream lanes, decode table
+width and persistent-grid occupancy.
+
+Chunk size (64 KiB - 1 MiB) and lanes are container parameters (chosen at
+compression time, recorded in the header); table width W (10-12 bits) and CTAs
+per SM are decoder launch parameters.  None of them changes the decoded bytes.
+The tuner compresses a representative sample with each candidate chunk size,
+times the graph-captured batched decode for each decoder setting, and keeps
+the fastest decode (compression speed breaks ties).  Results are cached as JSON
+keyed by (GPU name, dtype, size class) in $ZIPNN_TUNE_CACHE or
+~/.cache/zipnn_gb300/tune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+from . import zipnn as Z
+
+CHUNKS = (64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20)
+LUT_BITS = (10, 11, 12)
+
+
+def cache_path() -> str:
+    p = os.environ.get("ZIPNN_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "zipnn_gb300", "tune.json")
+
+
+def size_class(nbytes: int) -> str:
+    return f"2^{max(16, int(math.log2(max(1, nbytes))))}"
+
+
+def key(dtype: int, nbytes: int) -> str:
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{name}|dtype{dtype}|{size_class(nbytes)}"
+
+
+def load_cache() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def save_cache(d: dict) -> None:
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def _time(fn, reps: int) -> float:
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_BITS,
+         ctas=(0, 2, 3, 4), verbose: bool = False) -> dict:
+    """Sweep the candidates on `sample` (CUDA tensors of one dtype); returns the
+    best setting with its measured decode / compress GB/s (original bytes)."""
+    orig = sum(t.numel() * t.element_size() for t in sample)
+    outs = [torch.empty_like(t) for t in sample]
+    results = []
+    for chunk in chunks:
+        bc = Z.BatchCompressor(sample, chunk_bytes=chunk)
+        bc()
+        Z.sync_status()
+        cs = bc.containers()
+        ratio = sum(c.nbytes for c in cs) / orig
+        pc = Z.plan_compress(bc)
+        t_comp = _time(pc.launch, reps)
+        for w in lut_bits:
+            for k in ctas:
+                pd = Z.plan_decompress(cs, outs, tune=Z.tuning(ctas_per_sm=k, lut_bits=w))
+                t_dec = _time(pd.launch, reps)
+                pd.close()
+                r = {"chunk_bytes": chunk, "lut_bits": w, "ctas_per_sm": k,
+                     "decode_gbs": orig / t_dec / 1e9, "compress_gbs": orig / t_comp / 1e9,
+                     "ratio": ratio}
+                results.append(r)
+                if verbose:
+                    print(r, flush=True)
+        pc.close()
+        del bc, cs
+    Z.sync_status()
+    best = max(results, key=lambda r: (round(r["decode_gbs"], 0), r["compress_gbs"]))
+    best = dict(best)
+    best["candidates"] = len(results)
+    return best
+
+
+def tuned(sample: list[torch.Tensor], force: bool = False, **kw) -> dict:
+    """Cached tune() for the sample's (GPU, dtype, size class)."""
+    dtype = Z.dtype_code(sample[0], None)
+    nbytes = sum(t.numel() * t.element_size() for t in sample)
+    k = key(dtype, nbytes)
+    cache = load_cache()
+    if k in cache and not force:
+        return cache[k]
+    best = tune(sample, **kw)
+    cache[k] = best
+    try:
+        save_cache(cache)
+    except OSError:
+        pass
+    return best

@@ -16,10 +16,10 @@ namespace zipnn {
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
                                      const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
-                                     int max_groups);
+                                     int max_groups, int uniform_dtype);
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int uniform_dtype);
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
@@ -49,6 +49,52 @@ uint32_t* err_word() {
   }
   return g_err_ptr[dev];
 }
+
+// Pinned staging for job tables: the host copy lands in page-locked memory so
+// the H2D copy is truly asynchronous (a pageable source would make the call
+// wait for the stream to drain).  Regions are reused only after the event
+// recorded behind their copy has completed.
+class PinnedRing {
+ public:
+  cudaError_t h2d(void* dst, const void* src, size_t n, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (!buf_) {
+      if (cudaHostAlloc(reinterpret_cast<void**>(&buf_), kCap, cudaHostAllocPortable) != cudaSuccess) {
+        buf_ = nullptr;
+        return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+      }
+    }
+    if (n > kCap / 2) return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    const size_t need = (n + 255) / 256 * 256;
+    if (head_ + need > kCap) {  // wrap: every earlier region must be consumed first
+      for (cudaEvent_t ev : events_) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+      }
+      events_.clear();
+      head_ = 0;
+    }
+    uint8_t* stage = buf_ + head_;
+    memcpy(stage, src, n);
+    head_ += need;
+    cudaError_t e = cudaMemcpyAsync(dst, stage, n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, st);
+    events_.push_back(ev);
+    return e;
+  }
+
+ private:
+  static constexpr size_t kCap = 8u << 20;
+  std::mutex mu_;
+  uint8_t* buf_ = nullptr;
+  size_t head_ = 0;
+  std::vector<cudaEvent_t> events_;
+};
+PinnedRing g_ring;
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -211,8 +257,8 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
   const uint64_t ngc = (uint64_t)J.n_chunks * elem_size(dtype);
   EncodeScratch s;
   encode_scratch_carve(d_workspace, J.n_chunks, ngc, 1, &s);
-  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0);
-  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st);
+  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0, -1);
+  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st, -1);
   return cuda_status(e);
 }
 
@@ -222,6 +268,7 @@ struct BatchPlan {
   uint64_t nchunks = 0, ngc = 0;
   int max_lanes = 1;
   int max_groups = 1;
+  int uniform = -2;  // common dtype of the batch, -1 if mixed
 };
 
 zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d_bases,
@@ -254,6 +301,7 @@ zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d
     bp->ngc += (uint64_t)J.n_chunks * elem_size(dt);
     if ((int)ln > bp->max_lanes) bp->max_lanes = (int)ln;
     if (elem_size(dt) > bp->max_groups) bp->max_groups = elem_size(dt);
+    bp->uniform = (bp->uniform == -2 || bp->uniform == dt) ? dt : -1;
     bp->jobs[i] = J;
   }
   return ZIPNN_OK;
@@ -293,13 +341,13 @@ extern "C" zipnn_status zipnn_batch_compress_into(
   ws += align_up(sizeof(Job) * bp.jobs.size(), 256);
   EncodeScratch s;
   encode_scratch_carve(ws, bp.nchunks, bp.ngc, count, &s);
-  cudaError_t e = cudaMemcpyAsync(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(),
-                                  cudaMemcpyHostToDevice, st);
+  cudaError_t e = g_ring.h2d(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(), st);
   if (e == cudaSuccess)
     e = launch_encode_analyse_ex(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st,
-                                 bp.max_groups);
+                                 bp.max_groups, bp.uniform);
   if (e == cudaSuccess)
-    e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st);
+    e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st,
+                              bp.uniform);
   return cuda_status(e);
 }
 
@@ -323,7 +371,7 @@ static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t
   if (e != cudaSuccess) return cuda_status(e);
   EncodeScratch s;
   encode_scratch_carve(scratch, J.n_chunks, ngc, 1, &s);
-  e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0);
+  e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0, -1);
   uint64_t total = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, s.totals, 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -332,7 +380,7 @@ static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t
   if (e == cudaSuccess) {
     J.dst = static_cast<uint8_t*>(buf);
     J.out_capacity = total;
-    e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st);
+    e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st, -1);
   }
   cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) {
@@ -436,7 +484,7 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   if (e != cudaSuccess) return cuda_status(e);
   Job* d_jobs = static_cast<Job*>(dmem);
   unsigned long long* d_ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dmem) + tbytes);
-  e = cudaMemcpyAsync(d_jobs, jobs.data(), tbytes, cudaMemcpyHostToDevice, st);
+  e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
                          uniform);

@@ -7,19 +7,23 @@
 // uneven sizes.  Per chunk the CTA
 //   1. loads and validates the chunk's map entries and Huffman tables with
 //      16-byte / 4-byte cooperative loads into shared memory,
-//   2. builds, per Huffman group, a 2^W-entry table (W = 10): the entry for a
-//      W-bit window holds up to three whole codes that fit in it (symbols and
-//      bits consumed); a window whose first code is longer than W bits points
-//      to a slow path that resolves it with the canonical limits (< 0.3% of
-//      exponent symbols),
-//   3. decodes: thread t owns interleaved sub-stream t, i.e. the vectors
+//   2. stages every Huffman payload that fits (table, start offsets,
+//      bitstream) into shared memory with one TMA bulk copy per payload
+//      (cp.async.bulk, completion on an mbarrier; payloads are 16-B aligned and
+//      padded by the format), overlapped with step 3,
+//   3. builds, per Huffman group, a 2^W-entry table (W = 10..12, chosen at
+//      launch): the entry for a W-bit window holds up to three whole codes
+//      that fit in it (symbols and bits consumed); a window whose first code
+//      is longer than W bits takes a slow path through the canonical limits,
+//   4. decodes: thread t owns interleaved sub-stream t, i.e. the vectors
 //      v = t, t+T, ... of the chunk, so each warp step touches 32 consecutive
 //      16-byte vectors: raw-group loads (prefetched one vector ahead) and the
 //      16-B output stores are fully coalesced; the inverse permutation and the
 //      XOR with a delta base happen in registers.
 // The decoder is total: symbol counts are fixed by the map, bit reads past a
 // payload return zero bits, invalid codes and bad map entries set the error
-// word, and every loop is bounded.
+// word, and every loop is bounded; the wait for a bulk copy gives up after 2 s
+// of %globaltimer (error ETIMEOUT, the CTA waits again, bounded, then exits).
 #include <cstdint>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -31,9 +35,47 @@ namespace zipnn {
 namespace {
 
 constexpr int kDecThreads = 128;
-constexpr int kW = 10;                 // primary table bits
-constexpr int kLut = 1 << kW;
-constexpr uint32_t kSlow = 0u;         // entry with n == 0: resolve on the slow path
+constexpr uint32_t kSlow = 0u;           // entry with n == 0: resolve on the slow path
+constexpr uint32_t kStageBytes = 45056;  // shared-memory staging for Huffman payloads
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+// 1-D TMA bulk copy global -> shared (16-B aligned addresses, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity`; false if it gave up after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > limit_ns) return false;
+  return true;
+}
 
 template <int DT> struct Traits;
 template <> struct Traits<ZIPNN_BF16> { static constexpr int G = 2, V = 8; };
@@ -61,8 +103,10 @@ struct ChunkInfo {
   uint32_t size[4];
   uint32_t nwords[4];       // bitstream words (HUFF)
   uint64_t payload[4];      // byte offset of the payload within the container
-  uint64_t bs[4];           // byte offset of the bitstream (HUFF)
-  uint64_t offs[4];         // byte offset of the start-bit table (HUFF)
+  uint64_t bs[4];           // bitstream offset within the payload (HUFF)
+  uint64_t offs[4];         // start-bit table offset within the payload (HUFF)
+  uint32_t staged[4];       // stage offset of the payload, or ~0 if read from global
+  uint32_t stage_bytes;
   uint32_t bad;
 };
 
@@ -108,11 +152,12 @@ struct BitReader {
   }
 };
 
-// Slow path: the first code of the 12-bit window is longer than kW bits.
-// Returns a one-symbol entry (n = 1, consumed = length); flags invalid codes.
+// Slow path: the first code of the 12-bit window is longer than W bits (or is
+// not a code at all).  Returns a one-symbol entry (n = 1, consumed = length).
+template <int W>
 __device__ __noinline__ uint32_t slow_entry(const GroupTab& t, const uint8_t* syms,
                                             uint32_t win12, uint32_t& bad) {
-  int l = kW + 1;
+  int l = W + 1;
   while (l <= kMaxLen && win12 >= t.lim[l]) l++;
   if (l > kMaxLen) {
     bad = 1;
@@ -122,9 +167,9 @@ __device__ __noinline__ uint32_t slow_entry(const GroupTab& t, const uint8_t* sy
   return (uint32_t)syms[r & 255] | (1u << 24) | ((uint32_t)l << 26);
 }
 
-// Decode the next V symbols of a sub-stream into acc (little-endian bytes).
-// Entries: bits 0-23 up to three symbols, 24-25 count n, 26-29 bits consumed.
-// lo:hi carry symbols decoded past the vector boundary to the next call.
+// Decode the next V symbols of a sub-stream into out[] (little-endian bytes).
+// Table entries: bits 0-23 up to three symbols, 24-25 count n, 26-29 bits
+// consumed.  lo:hi carry symbols decoded past the vector boundary.
 template <int V>
 struct SymQueue {
   uint64_t lo;
@@ -132,46 +177,29 @@ struct SymQueue {
   uint32_t p;  // symbols held
 };
 
-template <int V>
-__device__ __forceinline__ void decode_vec(BitReader& br, const uint32_t* lut, const GroupTab& t,
+template <int W, int V, class BR>
+__device__ __forceinline__ void decode_vec(BR& br, const uint32_t* lut, const GroupTab& t,
                                            const uint8_t* syms, SymQueue<V>& q, uint32_t out[4],
                                            uint32_t& bad) {
-  if (V == 16) {
-    // two halves of 8 symbols
+  constexpr int HALF = V == 16 ? 8 : V;
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
-      while (q.p < 8) {
-        uint32_t e = lut[br.peek32() >> (32 - kW)];
-        if ((e >> 24 & 3u) == kSlow) e = slow_entry(t, syms, br.peek32() >> (32 - kMaxLen), bad);
-        const uint32_t s24 = e & 0xFFFFFFu, sh = 8u * q.p;
-        q.lo |= (uint64_t)s24 << sh;
-        if (sh >= 48) q.hi |= s24 >> (64 - sh);
-        q.p += e >> 24 & 3u;
-        br.skip(e >> 26);
-      }
-      out[2 * half] = (uint32_t)q.lo;
-      out[2 * half + 1] = (uint32_t)(q.lo >> 32);
-      q.lo = q.hi;
-      q.hi = 0;
-      q.p -= 8;
-    }
-  } else {
-    while (q.p < (uint32_t)V) {
-      uint32_t e = lut[br.peek32() >> (32 - kW)];
-      if ((e >> 24 & 3u) == kSlow) e = slow_entry(t, syms, br.peek32() >> (32 - kMaxLen), bad);
+  for (int half = 0; half < V / HALF; half++) {
+    while (q.p < (uint32_t)HALF) {
+      uint32_t e = lut[br.peek32() >> (32 - W)];
+      if ((e >> 24 & 3u) == kSlow) e = slow_entry<W>(t, syms, br.peek32() >> (32 - kMaxLen), bad);
       const uint32_t s24 = e & 0xFFFFFFu, sh = 8u * q.p;
       q.lo |= (uint64_t)s24 << sh;
       if (sh >= 48) q.hi |= s24 >> (64 - sh);
       q.p += e >> 24 & 3u;
       br.skip(e >> 26);
     }
-    if (V == 8) {
-      out[0] = (uint32_t)q.lo;
-      out[1] = (uint32_t)(q.lo >> 32);
+    if (HALF == 8) {
+      out[2 * half] = (uint32_t)q.lo;
+      out[2 * half + 1] = (uint32_t)(q.lo >> 32);
       q.lo = q.hi;
       q.hi = 0;
       q.p -= 8;
-    } else {  // V == 4
+    } else {  // HALF == 4
       out[0] = (uint32_t)q.lo;
       q.lo = (q.lo >> 32) | ((uint64_t)q.hi << 32);
       q.hi = 0;
@@ -180,129 +208,59 @@ __device__ __forceinline__ void decode_vec(BitReader& br, const uint32_t* lut, c
   }
 }
 
+// Reader over a bitstream staged in shared memory (all words present).
+struct SmemBitReader {
+  const uint32_t* w;
+  uint32_t idx, w0, w1, pos;
+  __device__ __forceinline__ void init(const uint32_t* words, uint32_t nwords, uint32_t start) {
+    (void)nwords;
+    w = words;
+    idx = start >> 5;
+    pos = start & 31;
+    w0 = w[idx];
+    w1 = w[idx + 1];  // the format pads every payload: one word past the end is readable
+    idx += 2;
+  }
+  __device__ __forceinline__ uint32_t peek32() const { return __funnelshift_l(w1, w0, pos); }
+  __device__ __forceinline__ void skip(uint32_t bits) {
+    pos += bits;
+    if (pos >= 32) {
+      pos -= 32;
+      w0 = w1;
+      w1 = w[idx++];
+    }
+  }
+};
+
 __device__ __forceinline__ uint32_t rd_u32(const uint8_t* p) {
   return __ldg(reinterpret_cast<const uint32_t*>(p));
 }
 
-// Decode one chunk of a tensor of dtype DT.
-template <int DT>
-__device__ void decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
-                             uint32_t* err) {
-  constexpr int G = Traits<DT>::G, V = Traits<DT>::V, ES = 16 / V;
+struct Staging {
+  uint8_t* base;       // shared-memory stage
+  uint64_t* bar;       // its mbarrier
+  uint32_t parity;     // phase to wait for next
+  uint32_t extra_tx;   // fault injection: bytes expected but never sent (0 normally)
+  uint64_t limit_ns;   // wait limit
+};
+
+template <int DT, int W, class BR, bool STAGED>
+__device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
+                                            Staging& stg, uint32_t* err) {
+  constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
+  constexpr int kLut = 1 << W;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
   const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
-  const uint64_t m = nb / ES;
   const uint64_t nvec = (nb + 15) / 16;
   const uint32_t T = J.lanes;
   const uint8_t* cont = J.src;
-  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
   ChunkInfo& CI = S.ci;
-
-  // 1a. map entries (one 16-B load per group)
-  if (tid == 0) CI.bad = 0;
-  __syncthreads();
-  if (tid < G) {
-    const uint4 e = __ldg(reinterpret_cast<const uint4*>(cont + kHdrBytes + (c * G + tid) * kEntryBytes));
-    const uint64_t po = (uint64_t)e.x | ((uint64_t)e.y << 32);
-    const uint32_t size = e.z, mode = e.w & 0xFFu, value = (e.w >> 8) & 0xFFu;
-    uint32_t bad = (e.w >> 16) != 0;
-    const uint64_t avail = J.stream_bytes > P ? J.stream_bytes - P : 0;
-    if (mode > kConst || po > avail || align_up(size, 16) > avail - po || (po & 15)) bad = 1;
-    if (mode == kRaw && size != m) bad = 1;
-    if ((mode == kZero || mode == kConst) && size != 0) bad = 1;
-    if (mode == kHuff && size < 12) bad = 1;
-    CI.mode[tid] = bad ? kZero : mode;
-    CI.value[tid] = value;
-    CI.size[tid] = size;
-    CI.payload[tid] = P + po;
-    if (bad) atomicOr(&CI.bad, 1u);
-  }
-  __syncthreads();
-  if (CI.bad) {
-    if (tid == 0) atomicOr(err, 1u);
-    return;
-  }
-  // 1b. table bytes of every Huffman group (word loads, clamped to the payload)
-#pragma unroll
-  for (int g = 0; g < G; g++) {
-    if (CI.mode[g] != kHuff) continue;
-    const uint8_t* p = cont + CI.payload[g];
-    for (int i = tid; i < 68; i += nthr)
-      S.tab[g].words[i] = (4u * i + 4u <= CI.size[g]) ? rd_u32(p + 4 * i) : 0u;
-  }
-  __syncthreads();
-  // 1c. canonical limits (thread g), validation
-  if (tid < G && CI.mode[tid] == kHuff) {
-    GroupTab& t = S.tab[tid];
-    uint32_t nz = 0, kraft = 0, code = 0, idx = 0, prevc = 0;
-    t.lim[0] = 0;
-    for (int l = 1; l <= kMaxLen; l++) {
-      const uint32_t cl = tab_byte(t, l - 1);
-      code = (code + prevc) << 1;
-      t.first[l] = code;
-      t.index[l] = idx;
-      t.lim[l] = (code + cl) << (kMaxLen - l);
-      idx += cl;
-      prevc = cl;
-      nz += cl;
-      kraft += cl << (kMaxLen - l);
-    }
-    t.lim[kMaxLen + 1] = 0xFFFFFFFFu;
-    const uint64_t h = align_up(12 + nz, 4);
-    const uint64_t size = CI.size[tid];
-    if (nz < 2 || nz > 256 || kraft > (uint32_t)kLutSize || size < h + 4ull * (T - 1) ||
-        (size - h - 4ull * (T - 1)) % 4) {
-      atomicOr(&CI.bad, 1u);
-    } else {
-      CI.offs[tid] = CI.payload[tid] + h;
-      CI.bs[tid] = CI.payload[tid] + h + 4ull * (T - 1);
-      CI.nwords[tid] = (uint32_t)((size - h - 4ull * (T - 1)) / 4);
-    }
-  }
-  __syncthreads();
-  if (CI.bad) {
-    if (tid == 0) atomicOr(err, 1u);
-    return;
-  }
-
-  // 2. multi-symbol tables.  Window w (kW bits): first code length
-  // l1 = 1 + #{l <= kW : lim_W[l] <= w}; if l1 > kW, slow path.
-#pragma unroll
-  for (int g = 0; g < G; g++) {
-    if (CI.mode[g] != kHuff) continue;
-    const GroupTab& t = S.tab[g];
-    const uint8_t* syms = reinterpret_cast<const uint8_t*>(t.words) + 12;
-    uint32_t limw[kW + 1];
-#pragma unroll
-    for (int l = 1; l <= kW; l++) limw[l] = t.lim[l] >> (kMaxLen - kW);
-    uint32_t* L = lut_base + g * kLut;
-    for (int w = tid; w < kLut; w += nthr) {
-      uint32_t ent = 0, n = 0, used = 0;
-      uint32_t rest = (uint32_t)w;  // remaining window bits, left-aligned in kW bits
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        uint32_t l = 1;
-#pragma unroll
-        for (int q = 1; q <= kW; q++) l += (limw[q] <= rest);
-        if (l > (uint32_t)(kW - used)) break;  // code not wholly inside the window
-        const uint32_t r = t.index[l] + (rest >> (kW - l)) - t.first[l];
-        ent |= (uint32_t)syms[r & 255] << (8 * k);
-        n++;
-        used += l;
-        rest = (rest << l) & (kLut - 1);
-      }
-      L[w] = n ? (ent | (n << 24) | (used << 26)) : kSlow;
-    }
-  }
-  __syncthreads();
-
-  // 3. decode + merge
   uint8_t* dst = J.dst + off0;
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
   uint32_t bad = 0;
   for (uint32_t t = tid; t < T; t += nthr) {
-    BitReader br[G];
+    BR br[G];
     SymQueue<V> sq[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -310,12 +268,15 @@ __device__ void decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
       sq[g].hi = 0;
       sq[g].p = 0;
       if (CI.mode[g] != kHuff) continue;
-      uint32_t start = t ? rd_u32(cont + CI.offs[g] + 4ull * (t - 1)) : 0u;
+      const uint8_t* pay = STAGED ? stg.base + CI.staged[g] : cont + CI.payload[g];
+      uint32_t start = 0;
+      if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay + CI.offs[g] + 4ull * (t - 1))
+                            : rd_u32(pay + CI.offs[g] + 4ull * (t - 1));
       if (start > CI.nwords[g] * 32u) {
         bad = 1;
         start = CI.nwords[g] * 32u;
       }
-      br[g].init(reinterpret_cast<const uint32_t*>(cont + CI.bs[g]), CI.nwords[g], start);
+      br[g].init(reinterpret_cast<const uint32_t*>(pay + CI.bs[g]), CI.nwords[g], start);
     }
     // raw group bytes of the next vector, prefetched
     uint32_t rawn[G][4] = {};
@@ -351,7 +312,7 @@ __device__ void decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
         const uint32_t mode = CI.mode[g];
         if (mode == kHuff) {
           const uint8_t* syms = reinterpret_cast<const uint8_t*>(S.tab[g].words) + 12;
-          decode_vec<V>(br[g], lut_base + g * kLut, S.tab[g], syms, sq[g], gw[g], bad);
+          decode_vec<W, V>(br[g], lut_base + g * kLut, S.tab[g], syms, sq[g], gw[g], bad);
         } else if (mode != kRaw) {
           const uint32_t b = (mode == kConst) ? CI.value[g] * 0x01010101u : 0u;
           gw[g][0] = b; gw[g][1] = b; gw[g][2] = b; gw[g][3] = b;
@@ -382,14 +343,188 @@ __device__ void decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
   if (bad) atomicOr(err, 1u);
 }
 
+// Decode one chunk of a tensor of dtype DT with W-bit tables.  Returns false
+// if a bulk copy never completed (the caller must stop using shared memory).
+template <int DT, int W>
+__device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
+                             Staging& stg, uint32_t* err) {
+  constexpr int G = Traits<DT>::G, V = Traits<DT>::V, ES = 16 / V;
+  constexpr int kLut = 1 << W;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint64_t off0 = c * J.chunk_bytes;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
+  const uint64_t m = nb / ES;
+  const uint64_t nvec = (nb + 15) / 16;
+  const uint32_t T = J.lanes;
+  const uint8_t* cont = J.src;
+  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+  ChunkInfo& CI = S.ci;
+
+  // 1a. map entries (one 16-B load per group)
+  if (tid == 0) CI.bad = 0;
+  __syncthreads();
+  if (tid < G) {
+    const uint4 e = __ldg(reinterpret_cast<const uint4*>(cont + kHdrBytes + (c * G + tid) * kEntryBytes));
+    const uint64_t po = (uint64_t)e.x | ((uint64_t)e.y << 32);
+    const uint32_t size = e.z, mode = e.w & 0xFFu, value = (e.w >> 8) & 0xFFu;
+    uint32_t bad = (e.w >> 16) != 0;
+    const uint64_t avail = J.stream_bytes > P ? J.stream_bytes - P : 0;
+    if (mode > kConst || po > avail || align_up(size, 16) > avail - po || (po & 15)) bad = 1;
+    if (mode == kRaw && size != m) bad = 1;
+    if ((mode == kZero || mode == kConst) && size != 0) bad = 1;
+    if (mode == kHuff && size < 12) bad = 1;
+    CI.mode[tid] = bad ? kZero : mode;
+    CI.value[tid] = value;
+    CI.size[tid] = size;
+    CI.payload[tid] = P + po;
+    if (bad) atomicOr(&CI.bad, 1u);
+  }
+  __syncthreads();
+  if (CI.bad) {
+    if (tid == 0) atomicOr(err, 1u);
+    return true;
+  }
+  // 2. stage the Huffman payloads that fit (thread 0 issues the bulk copies)
+  if (tid == 0) {
+    uint32_t used = 0;
+    for (int g = 0; g < G; g++) {
+      CI.staged[g] = 0xFFFFFFFFu;
+      if (CI.mode[g] != kHuff) continue;
+      const uint32_t padded = (uint32_t)align_up(CI.size[g], 16);
+      if (used + padded + 32 <= kStageBytes) {  // 32 B slack: readers look ahead
+        CI.staged[g] = used;
+        used += padded;
+      }
+    }
+    CI.stage_bytes = used;
+    if (used) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(stg.bar, used + stg.extra_tx);
+      for (int g = 0; g < G; g++)
+        if (CI.staged[g] != 0xFFFFFFFFu)
+          bulk_g2s(stg.base + CI.staged[g], cont + CI.payload[g],
+                   (uint32_t)align_up(CI.size[g], 16), stg.bar);
+    }
+  }
+  // 3a. table bytes of every Huffman group (word loads, clamped to the payload)
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if (CI.mode[g] != kHuff) continue;
+    const uint8_t* p = cont + CI.payload[g];
+    for (int i = tid; i < 68; i += nthr)
+      S.tab[g].words[i] = (4u * i + 4u <= CI.size[g]) ? rd_u32(p + 4 * i) : 0u;
+  }
+  __syncthreads();
+  // 3b. canonical limits (thread g), validation
+  if (tid < G && CI.mode[tid] == kHuff) {
+    GroupTab& t = S.tab[tid];
+    uint32_t nz = 0, kraft = 0, code = 0, idx = 0, prevc = 0;
+    t.lim[0] = 0;
+    for (int l = 1; l <= kMaxLen; l++) {
+      const uint32_t cl = tab_byte(t, l - 1);
+      code = (code + prevc) << 1;
+      t.first[l] = code;
+      t.index[l] = idx;
+      t.lim[l] = (code + cl) << (kMaxLen - l);
+      idx += cl;
+      prevc = cl;
+      nz += cl;
+      kraft += cl << (kMaxLen - l);
+    }
+    t.lim[kMaxLen + 1] = 0xFFFFFFFFu;
+    const uint64_t h = align_up(12 + nz, 4);
+    const uint64_t size = CI.size[tid];
+    if (nz < 2 || nz > 256 || kraft > (uint32_t)kLutSize || size < h + 4ull * (T - 1) ||
+        (size - h - 4ull * (T - 1)) % 4) {
+      atomicOr(&CI.bad, 1u);
+    } else {
+      CI.offs[tid] = h;
+      CI.bs[tid] = h + 4ull * (T - 1);
+      CI.nwords[tid] = (uint32_t)((size - h - 4ull * (T - 1)) / 4);
+    }
+  }
+  __syncthreads();
+  const bool bad_tab = CI.bad != 0;
+  // 3c. multi-symbol tables.  Window w (W bits): first code length
+  // l1 = 1 + #{l <= W : lim_W[l] <= w}; if l1 > W, slow path.
+  if (!bad_tab) {
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      if (CI.mode[g] != kHuff) continue;
+      const GroupTab& t = S.tab[g];
+      const uint8_t* syms = reinterpret_cast<const uint8_t*>(t.words) + 12;
+      uint32_t limw[W + 1];
+#pragma unroll
+      for (int l = 1; l <= W; l++) limw[l] = t.lim[l] >> (kMaxLen - W);
+      uint32_t* L = lut_base + g * kLut;
+      for (int w = tid; w < kLut; w += nthr) {
+        uint32_t ent = 0, n = 0, used = 0;
+        uint32_t rest = (uint32_t)w;  // remaining window bits, left-aligned in W bits
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          uint32_t l = 1;
+#pragma unroll
+          for (int q = 1; q <= W; q++) l += (limw[q] <= rest);
+          if (l > (uint32_t)(W - used)) break;  // code not wholly inside the window
+          const uint32_t r = t.index[l] + (rest >> (W - l)) - t.first[l];
+          ent |= (uint32_t)syms[r & 255] << (8 * k);
+          n++;
+          used += l;
+          rest = (rest << l) & (kLut - 1);
+        }
+        L[w] = n ? (ent | (n << 24) | (used << 26)) : kSlow;
+      }
+    }
+  }
+  // wait for the staged payloads (every thread; bounded)
+  uint32_t timed_out = 0;
+  if (CI.stage_bytes) {
+    if (!mbar_wait(stg.bar, stg.parity, stg.limit_ns)) timed_out = 1;
+    stg.parity ^= 1u;
+  }
+  if (timed_out) atomicOr(&CI.bad, 2u);
+  __syncthreads();
+  if (CI.bad & 2u) {
+    if (tid == 0) atomicOr(err, 4u);
+    if (timed_out) mbar_wait(stg.bar, stg.parity ^ 1u, stg.limit_ns);  // copies may still land
+    return false;
+  }
+  if (bad_tab) {
+    if (tid == 0) atomicOr(err, 1u);
+    return true;
+  }
+
+  // 4. decode + merge: shared-memory readers when every Huffman payload was
+  // staged, global-memory readers otherwise (payload larger than the stage)
+  bool all_staged = true;
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if (CI.mode[g] == kHuff && CI.staged[g] == 0xFFFFFFFFu) all_staged = false;
+  if (all_staged) decode_loop<DT, W, SmemBitReader, true>(J, c, S, lut_base, stg, err);
+  else decode_loop<DT, W, BitReader, false>(J, c, S, lut_base, stg, err);
+  return true;
+}
+
 // DTS: the dtype of every job in the launch, or -1 for a mixed batch.
-template <int DTS>
+template <int DTS, int W>
 __global__ void __launch_bounds__(kDecThreads)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
-         unsigned long long* __restrict__ ticket) {
-  extern __shared__ uint32_t lut_smem[];  // [groups][kLut]
+         unsigned long long* __restrict__ ticket, int max_groups, uint32_t debug_flags) {
+  extern __shared__ __align__(128) uint8_t dsm[];  // [groups][2^W] tables | stage
   __shared__ Smem S;
+  __shared__ uint64_t bar;
+  uint32_t* lut_smem = reinterpret_cast<uint32_t*>(dsm);
+  Staging stg;
+  stg.base = dsm + (size_t)max_groups * (4u << W);
+  stg.bar = &bar;
+  stg.parity = 0;
+  // debug flag 1 (tests only): expect 16 bytes more than the bulk copies send,
+  // so the wait can only end by its (shortened) limit -> ETIMEOUT
+  stg.extra_tx = (debug_flags & 1u) ? 16u : 0u;
+  stg.limit_ns = (debug_flags & 1u) ? 100000000ull : kWaitLimitNs;
   const int tid = threadIdx.x;
+  if (tid == 0) mbar_init(&bar);
+  __syncthreads();
   for (uint64_t iter = 0;; iter++) {
     // work item: from the device queue (batched form) or a static stride
     uint64_t chunk;
@@ -404,23 +539,38 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     const int j = jr.table ? find_job(jr.table, jr.n, chunk) : 0;
     const Job& J = jr.table ? jr.table[j] : jr.one;
     const uint64_t c = chunk - J.chunk_begin;
+    bool ok;
     if (DTS >= 0) {
-      decode_chunk<(DTS < 0 ? 0 : DTS)>(J, c, S, lut_smem, err);
+      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W>(J, c, S, lut_smem, stg, err);
     } else {
       switch (J.dtype) {
-        case ZIPNN_BF16: decode_chunk<ZIPNN_BF16>(J, c, S, lut_smem, err); break;
-        case ZIPNN_FP16: decode_chunk<ZIPNN_FP16>(J, c, S, lut_smem, err); break;
-        case ZIPNN_FP32: decode_chunk<ZIPNN_FP32>(J, c, S, lut_smem, err); break;
-        default: decode_chunk<ZIPNN_U8>(J, c, S, lut_smem, err); break;
+        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W>(J, c, S, lut_smem, stg, err); break;
+        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W>(J, c, S, lut_smem, stg, err); break;
+        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W>(J, c, S, lut_smem, stg, err); break;
+        default: ok = decode_chunk<ZIPNN_U8, W>(J, c, S, lut_smem, stg, err); break;
       }
     }
+    if (!ok) return;  // a bulk copy timed out: leave the stage alone
     __syncthreads();
+  }
+}
+
+using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, int, uint32_t);
+
+template <int W>
+DecodeKernel pick_kernel(int dt) {
+  switch (dt) {
+    case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W>;
+    case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W>;
+    case ZIPNN_FP32: return k_decode<ZIPNN_FP32, W>;
+    case ZIPNN_U8: return k_decode<ZIPNN_U8, W>;
+    default: return k_decode<-1, W>;
   }
 }
 
 }  // namespace
 
-int decode_smem_bytes(int max_groups) { return max_groups * kLut * 4; }
+int decode_smem_bytes(int max_groups, int w) { return max_groups * (4 << w) + (int)kStageBytes; }
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
@@ -433,33 +583,32 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   else memset(&r.one, 0, sizeof(Job));
   r.n = njobs;
   if (h_one) uniform_dtype = h_one->dtype;
-  void (*kern)(JobRef, uint64_t, uint32_t*, unsigned long long*);
-  switch (uniform_dtype) {
-    case ZIPNN_BF16: kern = k_decode<ZIPNN_BF16>; break;
-    case ZIPNN_FP16: kern = k_decode<ZIPNN_FP16>; break;
-    case ZIPNN_FP32: kern = k_decode<ZIPNN_FP32>; break;
-    case ZIPNN_U8: kern = k_decode<ZIPNN_U8>; break;
-    default: kern = k_decode<-1>; break;
-  }
+  int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 11;
+  if (w < 10) w = 10;
+  if (w > 12) w = 12;
+  DecodeKernel kern = w == 10 ? pick_kernel<10>(uniform_dtype)
+                      : (w == 11 ? pick_kernel<11>(uniform_dtype) : pick_kernel<12>(uniform_dtype));
   const int threads = kDecThreads;
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
-  const int smem = decode_smem_bytes(max_groups);
+  const int smem = decode_smem_bytes(max_groups, w);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (per_sm == 0) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-    per_sm = occ > 0 ? occ : 1;
-  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+  if (occ < 1) occ = 1;
+  if (per_sm == 0 || per_sm > occ) per_sm = occ;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > nchunks_total) grid = nchunks_total;
   if (d_ticket) {
-    cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
+    e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
-  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket);
+  const uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
+  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, max_groups, dbg);
   return cudaGetLastError();
 }
 

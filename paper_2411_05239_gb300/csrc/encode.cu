@@ -115,23 +115,35 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   uint32_t* hr = sh + warp * WARP_WORDS + kECopies * kEStride;
   const uint64_t nvec = (nb + 15) / 16;
   const uint64_t m = nb / ES;
-  for (uint64_t v = tid; v < nvec; v += kHistThreads) {
-    uint32_t g[4][4];
-    split_vec(DT, load_vec(src, base, v, nb), g);
-    if ((v + 1) * V <= m) {
+  constexpr int U = 4;  // vectors in flight per thread
+  for (uint64_t v0 = tid; v0 < nvec; v0 += (uint64_t)kHistThreads * U) {
+    uint4 a[U];
 #pragma unroll
-      for (int k = 0; k < V; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+    for (int u = 0; u < U; u++) {
+      const uint64_t v = v0 + (uint64_t)u * kHistThreads;
+      a[u] = v < nvec ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
+    }
 #pragma unroll
-      for (int gg = 1; gg < G; gg++)
+    for (int u = 0; u < U; u++) {
+      const uint64_t v = v0 + (uint64_t)u * kHistThreads;
+      if (v >= nvec) break;
+      uint32_t g[4][4];
+      split_vec(DT, a[u], g);
+      if ((v + 1) * V <= m) {
 #pragma unroll
-        for (int k = 0; k < V; k++)
-          atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
-    } else {
-      const int valid = (int)(m - v * V);
-      for (int k = 0; k < valid; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
-      for (int gg = 1; gg < G; gg++)
-        for (int k = 0; k < valid; k++)
-          atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+        for (int k = 0; k < V; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+#pragma unroll
+        for (int gg = 1; gg < G; gg++)
+#pragma unroll
+          for (int k = 0; k < V; k++)
+            atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+      } else {
+        const int valid = (int)(m - v * V);
+        for (int k = 0; k < valid; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+        for (int gg = 1; gg < G; gg++)
+          for (int k = 0; k < valid; k++)
+            atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+      }
     }
   }
   __syncthreads();
@@ -148,12 +160,17 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   }
 }
 
+template <int DTS>
 __global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __restrict__ hist) {
   extern __shared__ uint32_t hsm[];
   const uint64_t chunk = blockIdx.x;
   const int j = find_job_chunk(jr, chunk);
   const Job& J = job_at(jr, j);
   const uint64_t c = chunk - J.chunk_begin;
+  if (DTS >= 0) {
+    hist_chunk<(DTS < 0 ? 0 : DTS)>(J, c, hsm, hist);
+    return;
+  }
   switch (J.dtype) {
     case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, hist); break;
     case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, hist); break;
@@ -562,11 +579,20 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
 #pragma unroll
     for (int g = 0; g < G; g++) bits[g] = 0;
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
-    for (uint64_t i = (uint64_t)k * per; i < i1; i++) {
-      const uint64_t v = t + i * T;
-      if (v >= nvec) break;
+    constexpr int U = 4;  // vectors in flight per thread
+    for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
+      uint4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t v = t + (i0 + u) * T;
+        a[u] = (i0 + u < i1 && v < nvec) ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+      const uint64_t v = t + (i0 + u) * T;
+      if (i0 + u >= i1 || v >= nvec) break;
       uint32_t g4[4][4];
-      split_vec(DT, load_vec(src, base, v, nb), g4);
+      split_vec(DT, a[u], g4);
       const bool full = (v + 1) * V <= m;
       const int valid = full ? V : (int)(m - v * V);
 #pragma unroll
@@ -588,6 +614,7 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
             for (int q = 0; q < valid; q++) p[q] = (uint8_t)(g4[g][q >> 2] >> (8 * (q & 3)));
           }
         }
+      }
       }
     }
 #pragma unroll
@@ -643,11 +670,20 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
       capw[g] = S.capw[g];
     }
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
-    for (uint64_t i = (uint64_t)k * per; i < i1; i++) {
-      const uint64_t v = t + i * T;
-      if (v >= nvec) break;
+    constexpr int U = 4;  // vectors in flight per thread
+    for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
+      uint4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t v = t + (i0 + u) * T;
+        a[u] = (i0 + u < i1 && v < nvec) ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+      const uint64_t v = t + (i0 + u) * T;
+      if (i0 + u >= i1 || v >= nvec) break;
       uint32_t g4[4][4];
-      split_vec(DT, load_vec(src, base, v, nb), g4);
+      split_vec(DT, a[u], g4);
       const int valid = (int)min((uint64_t)V, m - v * V);
 #pragma unroll
       for (int g = 0; g < G; g++) {
@@ -671,6 +707,7 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
           }
         }
       }
+      }
     }
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -681,7 +718,8 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
   }
 }
 
-__global__ void __launch_bounds__(kPackThreads)
+template <int DTS>
+__global__ void __launch_bounds__(kPackThreads, 2)
 k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
        const uint8_t* __restrict__ tabs, const GcMeta* __restrict__ meta,
        const uint64_t* __restrict__ offs, const uint64_t* __restrict__ totals) {
@@ -715,6 +753,10 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
   const Job& J = job_at(jr, j);
   if (totals[j] > J.out_capacity) return;
   const uint64_t c = chunk - J.chunk_begin;
+  if (DTS >= 0) {
+    pack_chunk<(DTS < 0 ? 0 : DTS)>(J, c, S, codes, tabs, meta, offs);
+    return;
+  }
   switch (J.dtype) {
     case ZIPNN_BF16: pack_chunk<ZIPNN_BF16>(J, c, S, codes, tabs, meta, offs); break;
     case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, codes, tabs, meta, offs); break;
@@ -760,16 +802,32 @@ static JobRef make_ref(const Job* d_jobs, int njobs, const Job* h_one) {
 
 // Launch k_hist, k_build and k_scan.  d_jobs is a device table of njobs jobs,
 // unless njobs == 1 and h_one is given (then the job is passed by value).
+template <class K>
+static K pick(int dt, K k0, K k1, K k2, K k3, K kmix) {
+  switch (dt) {
+    case ZIPNN_BF16: return k0;
+    case ZIPNN_FP16: return k1;
+    case ZIPNN_FP32: return k2;
+    case ZIPNN_U8: return k3;
+    default: return kmix;
+  }
+}
+
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
                                      const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
-                                     int max_groups) {
+                                     int max_groups, int uniform_dtype) {
   JobRef r = make_ref(d_jobs, njobs, h_one);
-  if (h_one) max_groups = elem_size(h_one->dtype);
+  if (h_one) {
+    max_groups = elem_size(h_one->dtype);
+    uniform_dtype = h_one->dtype;
+  }
   if (nchunks_total) {
     const int hs = hist_smem_bytes(max_groups < 1 ? 4 : (max_groups > 4 ? 4 : max_groups));
-    if (hs > 48 * 1024) cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, hs);
-    k_hist<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist);
+    auto kh = pick(uniform_dtype, k_hist<ZIPNN_BF16>, k_hist<ZIPNN_FP16>, k_hist<ZIPNN_FP32>,
+                   k_hist<ZIPNN_U8>, k_hist<-1>);
+    if (hs > 48 * 1024) cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, hs);
+    kh<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist);
     unsigned nb = (unsigned)((ngc_total + kBuildWarps - 1) / kBuildWarps);
     k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.codes, s.tabs, s.meta);
   }
@@ -779,10 +837,13 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
 
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int uniform_dtype) {
   JobRef r = make_ref(d_jobs, njobs, h_one);
   (void)max_lanes;
-  k_pack<<<(unsigned)(nchunks_total + njobs), kPackThreads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
+  if (h_one) uniform_dtype = h_one->dtype;
+  auto kp = pick(uniform_dtype, k_pack<ZIPNN_BF16>, k_pack<ZIPNN_FP16>, k_pack<ZIPNN_FP32>,
+                 k_pack<ZIPNN_U8>, k_pack<-1>);
+  kp<<<(unsigned)(nchunks_total + njobs), kPackThreads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
                                                                 s.meta, s.offs, s.totals);
   return cudaGetLastError();
 }

@@ -38,10 +38,10 @@ namespace zipnn {
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
                                      const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
-                                     int max_groups);
+                                     int max_groups, int uniform_dtype);
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int uniform_dtype);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
@@ -121,7 +121,7 @@ extern "C" zipnn_status zipnn_compress_into_static(const void* d_src, const void
   EncodeScratch s;
   encode_scratch_carve(scratch, nch, ngc, 1, &s);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  e = launch_encode_analyse_ex(nullptr, &J, 1, nch, ngc, s, err, st, 0);
-  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, nch, (int)lanes, s, st);
+  e = launch_encode_analyse_ex(nullptr, &J, 1, nch, ngc, s, err, st, 0, -1);
+  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, nch, (int)lanes, s, st, -1);
   return e == cudaSuccess ? ZIPNN_OK : ZIPNN_ECUDA;
 }

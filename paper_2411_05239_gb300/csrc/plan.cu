@@ -17,10 +17,10 @@ namespace zipnn {
 cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                      uint64_t nchunks_total, uint64_t ngc_total,
                                      const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
-                                     int max_groups);
+                                     int max_groups, int uniform_dtype);
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int uniform_dtype);
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
@@ -148,9 +148,10 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   *out = nullptr;
   std::vector<Job> jobs((size_t)count);
   uint64_t nch = 0, ngc = 0;
-  int max_lanes = 1, max_groups = 1;
+  int max_lanes = 1, max_groups = 1, uniform = dtypes[0];
   for (int i = 0; i < count; i++) {
     const int dt = dtypes[i];
+    if (dt != uniform) uniform = -1;
     if (dt < ZIPNN_BF16 || dt > ZIPNN_U8) return ZIPNN_EINVAL;
     const uint32_t ln = lanes ? lanes : zipnn_default_lanes(dt, chunk_bytes);
     const int es = elem_size(dt);
@@ -202,8 +203,9 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   if (e != cudaSuccess) return fail(p, e);
   e = capture(p, [&](cudaStream_t cs) {
     cudaError_t e2 = launch_encode_analyse_ex(d_jobs, nullptr, count, nch, ngc, s, err, cs,
-                                              max_groups);
-    if (e2 == cudaSuccess) e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs);
+                                              max_groups, uniform);
+    if (e2 == cudaSuccess)
+      e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs, uniform);
     return e2;
   });
   if (e != cudaSuccess) return fail(p, e);

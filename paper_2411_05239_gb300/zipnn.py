@@ -52,7 +52,7 @@ class ZStream(ctypes.Structure):
 
 class ZTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("lut_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lut_bits", ctypes.c_int32), ("debug_flags", ctypes.c_int32)]
 
 
 _lib = None
@@ -289,8 +289,9 @@ def decompress(c: Compressed, out: torch.Tensor | None = None, base: torch.Tenso
     return out
 
 
-def tuning(threads: int = 0, ctas_per_sm: int = 0, lut_bits: int = 0) -> ZTuning:
-    return ZTuning(threads, ctas_per_sm, lut_bits, 0)
+def tuning(threads: int = 0, ctas_per_sm: int = 0, lut_bits: int = 0,
+           debug_flags: int = 0) -> ZTuning:
+    return ZTuning(threads, ctas_per_sm, lut_bits, debug_flags)
 
 
 def batch_decompress(cs: list[Compressed], outs: list[torch.Tensor],
@@ -406,3 +407,133 @@ def plan_compress(bc: BatchCompressor) -> Plan:
                                    ctypes.byref(h))
     _check(rc, "zipnn_plan_compress")
     return Plan(h.value, [bc])
+
+
+# ---------------------------------------------------------------------------
+# Request server (continuous batching with HBM admission)
+
+OP_COMPRESS, OP_DECOMPRESS = 0, 1
+
+
+class ZRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("d_input", ctypes.c_void_p), ("input_bytes", ctypes.c_uint64),
+                ("container", ZStream), ("d_base", ctypes.c_void_p),
+                ("chunk_bytes", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class ZCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("op", ctypes.c_int32), ("d_output", ctypes.c_void_p),
+                ("output_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ZServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_batch", ctypes.c_uint64),
+                ("bytes_processed", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+                ("inputs_charged", ctypes.c_uint64)]
+
+
+def _server_lib():
+    L = lib()
+    if getattr(L, "_server_sigs", False):
+        return L
+    vp = ctypes.c_void_p
+    L.zipnn_server_create.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(vp)]
+    L.zipnn_server_create.restype = ctypes.c_int
+    L.zipnn_server_submit.argtypes = [vp, ctypes.POINTER(ZRequest), ctypes.POINTER(ctypes.c_uint64)]
+    L.zipnn_server_submit.restype = ctypes.c_int
+    L.zipnn_server_poll.argtypes = [vp, ctypes.POINTER(ZCompletion), ctypes.c_int]
+    L.zipnn_server_poll.restype = ctypes.c_int
+    L.zipnn_server_release.argtypes = [vp, ctypes.c_uint64]
+    L.zipnn_server_release.restype = ctypes.c_int
+    L.zipnn_server_drain.argtypes = [vp, ctypes.c_double]
+    L.zipnn_server_drain.restype = ctypes.c_int
+    L.zipnn_server_get_stats.argtypes = [vp, ctypes.POINTER(ZServerStats)]
+    L.zipnn_server_get_stats.restype = ctypes.c_int
+    L.zipnn_server_destroy.argtypes = [vp]
+    L.zipnn_server_destroy.restype = None
+    L._server_sigs = True
+    return L
+
+
+class Server:
+    """Continuous-batching request server on the current CUDA device.
+
+    Inputs (tensors, containers, bases) are caller-owned and must stay alive
+    until their request completes; outputs live in the server's arena until
+    release()."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4):
+        self.L = _server_lib()
+        h = ctypes.c_void_p()
+        _check(self.L.zipnn_server_create(budget_bytes, slots, ctypes.byref(h)),
+               "zipnn_server_create")
+        self.h = h.value
+        self._keep: dict[int, tuple] = {}
+
+    def submit_compress(self, x: torch.Tensor, base: torch.Tensor | None = None,
+                        chunk_bytes: int = 0, tag: int = 0) -> int:
+        src = _flat_u8(x)
+        r = ZRequest()
+        r.op = OP_COMPRESS
+        r.dtype = dtype_code(x, None)
+        r.d_input = src.data_ptr() if src.numel() else None
+        r.input_bytes = src.numel()
+        r.d_base = _flat_u8(base).data_ptr() if base is not None else None
+        r.chunk_bytes = chunk_bytes
+        r.tag = tag
+        rid = ctypes.c_uint64()
+        _check(self.L.zipnn_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid)),
+               "zipnn_server_submit")
+        self._keep[rid.value] = (x, base)
+        return rid.value
+
+    def submit_decompress(self, c: Compressed, base: torch.Tensor | None = None,
+                          tag: int = 0) -> int:
+        r = ZRequest()
+        r.op = OP_DECOMPRESS
+        r.container = c.zs
+        r.d_base = _flat_u8(base).data_ptr() if base is not None else None
+        r.tag = tag
+        rid = ctypes.c_uint64()
+        _check(self.L.zipnn_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid)),
+               "zipnn_server_submit")
+        self._keep[rid.value] = (c, base)
+        return rid.value
+
+    def poll(self, max_n: int = 1024) -> list[ZCompletion]:
+        arr = (ZCompletion * max_n)()
+        n = self.L.zipnn_server_poll(self.h, arr, max_n)
+        out = [ZCompletion.from_buffer_copy(arr[i]) for i in range(n)]
+        for c in out:
+            self._keep.pop(c.id, None)
+        return out
+
+    def output(self, c: ZCompletion) -> torch.Tensor:
+        """The completion's output bytes as a uint8 CUDA tensor (aliases the arena)."""
+        return device_bytes(c.d_output, c.output_bytes)
+
+    def release(self, rid: int) -> None:
+        _check(self.L.zipnn_server_release(self.h, rid), "zipnn_server_release")
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(self.L.zipnn_server_drain(self.h, timeout_s), "zipnn_server_drain")
+
+    def stats(self) -> ZServerStats:
+        st = ZServerStats()
+        _check(self.L.zipnn_server_get_stats(self.h, ctypes.byref(st)), "zipnn_server_get_stats")
+        return st
+
+    def close(self) -> None:
+        if self.h:
+            self.L.zipnn_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

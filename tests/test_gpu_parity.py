@@ -309,3 +309,32 @@ def test_batch_compress_deltas():
     assert c0.is_delta and not c1.is_delta
     assert c0.to_bytes() == O.delta(u8(nxt), u8(base), Z.BF16, 8192)
     assert c1.to_bytes() == O.compress(u8(other), Z.BF16, 8192)
+
+
+def test_bounded_wait_gives_up_with_etimeout_and_context_survives():
+    """Fault injection without faulting the GPU: the decoder is told to wait for
+    bytes that never arrive; its bounded wait must give up (ETIMEOUT), the CTAs
+    exit cleanly and the next call works."""
+    x = W.gaussian(300_000, 0.02, 60)
+    c = Z.compress(x.cuda(), chunk_bytes=65536)
+    out = torch.empty_like(x, device="cuda")
+    Z.batch_decompress([c], [out], tune=Z.tuning(debug_flags=1))
+    with pytest.raises(Z.ZipnnError) as e:
+        Z.sync_status()
+    assert e.value.status == -5
+    Z.batch_decompress([c], [out])
+    Z.sync_status()
+    assert torch.equal(out.cpu().view(torch.int16), x.view(torch.int16))
+
+
+@pytest.mark.parametrize("w", [10, 11, 12])
+@pytest.mark.parametrize("ctas", [0, 1, 3])
+def test_decoder_settings_do_not_change_bytes(w, ctas):
+    xs = [W.gaussian(n, 0.02, 61 + i) for i, n in enumerate([100_001, 3000, 262_144])]
+    xs.append(W.gaussian(50_000, 1.0, 64, torch.bfloat16).float())     # clean FP32
+    cs = [Z.compress(x.cuda(), chunk_bytes=65536) for x in xs]
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    Z.batch_decompress(cs, outs, tune=Z.tuning(lut_bits=w, ctas_per_sm=ctas))
+    Z.sync_status()
+    for x, o in zip(xs, outs):
+        assert torch.equal(o.cpu().view(torch.uint8), x.view(torch.uint8))
