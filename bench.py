@@ -255,14 +255,27 @@ def run_gb300(args):
     ts = W.checkpoint_bf16(specs, seed=2, device=dev)
     orig = sum(t.numel() * 2 for t in ts)
 
+    # autotuned container (chunk size, lanes) and decoder (table width, CTAs/SM)
+    # settings, measured on a sample of the checkpoint (embedding rows + 2 layers)
+    tuned = None
+    lanes = 0
+    if args.autotune:
+        from paper_2411_05239_gb300 import autotune as AT
+        sample = [ts[0][: 64 * 1024 * 1024]] + ts[1:1 + 2 * 9]
+        tuned = AT.tune(sample, reps=3, ctas=(0, 2, 3))
+        args.chunk = tuned["chunk_bytes"]
+        lanes = tuned["lanes"]
+        args.lut_bits = tuned["lut_bits"]
+        args.ctas_per_sm = tuned["ctas_per_sm"]
+        torch.cuda.synchronize()
     # compression plan (batched, graph-captured) and a first pass for the sizes
-    bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk)
+    bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk, lanes=lanes)
     bc()
     Z.sync_status()
     cs = bc.containers()
     comp_bytes = sum(c.nbytes for c in cs)
     outs = [torch.empty_like(t) for t in ts]
-    tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+    tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm, lut_bits=args.lut_bits)
     comp_plan = Z.plan_compress(bc)
     dec_plan = Z.plan_decompress(cs, outs, tune=tune)
 
@@ -392,7 +405,9 @@ def run_gb300(args):
                                 else f"llama_bf16_checkpoint_{args.layers}l_{args.vocab}v"),
                    "tensors": len(ts),
                    "params": orig // 2, "bytes": orig, "chunk_bytes": args.chunk,
-                   "lanes": Z.default_lanes(Z.BF16, args.chunk),
+                   "lanes": cs[0].zs.lanes, "lut_bits": args.lut_bits or 11,
+                   "ctas_per_sm": args.ctas_per_sm,
+                   "autotuned": tuned is not None,
                    "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
                    "form": "batched: 1 graph launch compress + 1 graph launch persistent decode"},
         "decompress_gbs": value, "compress_gbs": world * orig / comp_s / 1e9,
@@ -540,6 +555,9 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=256 * 1024)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--lut-bits", type=int, default=0)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="pick chunk size, lanes, table width, CTAs/SM on a sample first")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--per-tensor", type=int, default=1)
     ap.add_argument("--cpu-sample-mb", type=int, default=384)

@@ -71,14 +71,16 @@ def _time(fn, reps: int) -> float:
 
 
 def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_BITS,
-         ctas=(0, 2, 3, 4), verbose: bool = False) -> dict:
+         ctas=(0, 2, 3, 4), lane_scales=(1, 2), verbose: bool = False) -> dict:
     """Sweep the candidates on `sample` (CUDA tensors of one dtype); returns the
     best setting with its measured decode / compress GB/s (original bytes)."""
     orig = sum(t.numel() * t.element_size() for t in sample)
     outs = [torch.empty_like(t) for t in sample]
     results = []
-    for chunk in chunks:
-        bc = Z.BatchCompressor(sample, chunk_bytes=chunk)
+    dtype = Z.dtype_code(sample[0], None)
+    for chunk, scale in [(c, k) for c in chunks for k in lane_scales]:
+        lanes = min(1024, Z.default_lanes(dtype, chunk) * scale, chunk // 16)
+        bc = Z.BatchCompressor(sample, chunk_bytes=chunk, lanes=lanes)
         bc()
         Z.sync_status()
         cs = bc.containers()
@@ -90,7 +92,7 @@ def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_
                 pd = Z.plan_decompress(cs, outs, tune=Z.tuning(ctas_per_sm=k, lut_bits=w))
                 t_dec = _time(pd.launch, reps)
                 pd.close()
-                r = {"chunk_bytes": chunk, "lut_bits": w, "ctas_per_sm": k,
+                r = {"chunk_bytes": chunk, "lanes": lanes, "lut_bits": w, "ctas_per_sm": k,
                      "decode_gbs": orig / t_dec / 1e9, "compress_gbs": orig / t_comp / 1e9,
                      "ratio": ratio}
                 results.append(r)

@@ -244,98 +244,192 @@ struct Staging {
   uint64_t limit_ns;   // wait limit
 };
 
-template <int DT, int W, class BR, bool STAGED>
+// One lookup of a sub-stream into its queue (up to three symbols).
+template <int W, int V, class BR>
+__device__ __forceinline__ void lookup_once(BR& br, const uint32_t* lut, const GroupTab& t,
+                                            const uint8_t* syms, SymQueue<V>& q, uint32_t& bad) {
+  uint32_t e = lut[br.peek32() >> (32 - W)];
+  if ((e >> 24 & 3u) == kSlow) e = slow_entry<W>(t, syms, br.peek32() >> (32 - kMaxLen), bad);
+  const uint32_t s24 = e & 0xFFFFFFu, sh = 8u * q.p;
+  q.lo |= (uint64_t)s24 << sh;
+  if (sh >= 48) q.hi |= s24 >> (64 - sh);
+  q.p += e >> 24 & 3u;
+  br.skip(e >> 26);
+}
+
+template <int V>
+__device__ __forceinline__ void pop_vec(SymQueue<V>& q, uint32_t* out) {
+  if (V == 4) {
+    out[0] = (uint32_t)q.lo;
+    q.lo = (q.lo >> 32) | ((uint64_t)q.hi << 32);
+    q.hi = 0;
+    q.p -= 4;
+  } else {  // 8 symbols
+    out[0] = (uint32_t)q.lo;
+    out[1] = (uint32_t)(q.lo >> 32);
+    q.lo = q.hi;
+    q.hi = 0;
+    q.p -= 8;
+  }
+}
+
+// Decode loop of one chunk.  Each thread owns NS sub-streams (t, t + nthr,
+// ...) and advances them in lockstep, one vector each per step; the lookups
+// of different sub-streams are independent, which gives the scheduler
+// instruction-level parallelism inside a warp.
+template <int DT, int W, class BR, bool STAGED, int NS>
 __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
                                             Staging& stg, uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
+  constexpr int HV = V == 16 ? 8 : V;  // symbols per queue pop
   constexpr int kLut = 1 << W;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
-  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
-  const uint64_t nvec = (nb + 15) / 16;
+  const uint32_t nb = (uint32_t)min((uint64_t)J.chunk_bytes, J.nbytes - off0);
+  const uint32_t nvec = (nb + 15) / 16;
   const uint32_t T = J.lanes;
   const uint8_t* cont = J.src;
   ChunkInfo& CI = S.ci;
   uint8_t* dst = J.dst + off0;
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
-  uint32_t bad = 0;
-  for (uint32_t t = tid; t < T; t += nthr) {
-    BR br[G];
-    SymQueue<V> sq[G];
+  // per-chunk values in registers
+  uint32_t mode[G], cval[G], nwords[G];
+  const uint8_t* rawp[G];
+  const uint8_t* pay[G];
+  uint32_t offs[G], bsoff[G];
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-      sq[g].lo = 0;
-      sq[g].hi = 0;
-      sq[g].p = 0;
-      if (CI.mode[g] != kHuff) continue;
-      const uint8_t* pay = STAGED ? stg.base + CI.staged[g] : cont + CI.payload[g];
-      uint32_t start = 0;
-      if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay + CI.offs[g] + 4ull * (t - 1))
-                            : rd_u32(pay + CI.offs[g] + 4ull * (t - 1));
-      if (start > CI.nwords[g] * 32u) {
-        bad = 1;
-        start = CI.nwords[g] * 32u;
-      }
-      br[g].init(reinterpret_cast<const uint32_t*>(pay + CI.bs[g]), CI.nwords[g], start);
-    }
-    // raw group bytes of the next vector, prefetched
-    uint32_t rawn[G][4] = {};
-    auto load_raw = [&](uint64_t v, uint32_t (&r)[G][4]) {
+  for (int g = 0; g < G; g++) {
+    mode[g] = CI.mode[g];
+    cval[g] = CI.value[g] * 0x01010101u;
+    nwords[g] = CI.nwords[g];
+    rawp[g] = cont + CI.payload[g];
+    pay[g] = STAGED ? stg.base + CI.staged[g] : cont + CI.payload[g];
+    offs[g] = (uint32_t)CI.offs[g];
+    bsoff[g] = (uint32_t)CI.bs[g];
+  }
+  uint32_t bad = 0;
+  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
+    BR br[NS][G];
+    SymQueue<V> sq[NS][G];
+    uint32_t tt[NS];
+    bool act[NS];
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+      tt[j] = t0 + j * nthr;
+      act[j] = tt[j] < T;
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        if (CI.mode[g] != kRaw || v >= nvec) continue;
-        const uint8_t* p = cont + CI.payload[g] + v * V;
+        sq[j][g].lo = 0;
+        sq[j][g].hi = 0;
+        sq[j][g].p = 0;
+        if (mode[g] != kHuff) continue;
+        const uint32_t t = act[j] ? tt[j] : 0u;
+        uint32_t start = 0;
+        if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
+                              : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
+        if (start > nwords[g] * 32u) {
+          bad = 1;
+          start = nwords[g] * 32u;
+        }
+        br[j][g].init(reinterpret_cast<const uint32_t*>(pay[g] + bsoff[g]), nwords[g], start);
+      }
+    }
+    // raw group bytes, prefetched one vector ahead
+    uint32_t rawn[NS][G][4] = {};
+    auto load_raw = [&](int j, uint32_t v) {
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (mode[g] != kRaw || v >= nvec) continue;
+        const uint8_t* p = rawp[g] + (size_t)v * V;
         if (V == 8) {
           const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
-          r[g][0] = x.x; r[g][1] = x.y;
+          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y;
         } else if (V == 4) {
-          r[g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+          rawn[j][g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
         } else {
           const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
-          r[g][0] = x.x; r[g][1] = x.y; r[g][2] = x.z; r[g][3] = x.w;
+          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y; rawn[j][g][2] = x.z; rawn[j][g][3] = x.w;
         }
       }
     };
-    load_raw(t, rawn);
-    for (uint64_t v = t; v < nvec; v += T) {
-      uint32_t gw[G][4];
 #pragma unroll
-      for (int g = 0; g < G; g++)
+    for (int j = 0; j < NS; j++)
+      if (act[j]) load_raw(j, tt[j]);
+    for (uint32_t kstep = 0;; kstep++) {
+      uint32_t vv[NS];
+      bool live[NS];
+      bool any = false;
 #pragma unroll
-        for (int k = 0; k < 4; k++) gw[g][k] = rawn[g][k];
-      load_raw(v + T, rawn);
-      uint4 bv = make_uint4(0, 0, 0, 0);
-      const bool full = (v + 1) * 16 <= nb;
-      if (base && full) bv = __ldg(reinterpret_cast<const uint4*>(base) + v);
+      for (int j = 0; j < NS; j++) {
+        vv[j] = tt[j] + kstep * T;
+        live[j] = act[j] && vv[j] < nvec;
+        any |= live[j];
+      }
+      if (!any) break;
+      uint32_t gw[NS][G][4];
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+#pragma unroll
+        for (int g = 0; g < G; g++)
+#pragma unroll
+          for (int k = 0; k < 4; k++) gw[j][g][k] = rawn[j][g][k];
+        if (live[j]) load_raw(j, vv[j] + T);
+      }
+      // Huffman groups: the NS queues are filled in one loop (independent lookups)
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        const uint32_t mode = CI.mode[g];
-        if (mode == kHuff) {
-          const uint8_t* syms = reinterpret_cast<const uint8_t*>(S.tab[g].words) + 12;
-          decode_vec<W, V>(br[g], lut_base + g * kLut, S.tab[g], syms, sq[g], gw[g], bad);
-        } else if (mode != kRaw) {
-          const uint32_t b = (mode == kConst) ? CI.value[g] * 0x01010101u : 0u;
-          gw[g][0] = b; gw[g][1] = b; gw[g][2] = b; gw[g][3] = b;
+        if (mode[g] != kHuff) continue;
+        const uint32_t* L = lut_base + g * kLut;
+        const GroupTab& tb = S.tab[g];
+        const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+#pragma unroll
+        for (int h = 0; h < V / HV; h++) {
+          for (;;) {
+            bool need = false;
+#pragma unroll
+            for (int j = 0; j < NS; j++) need |= live[j] && sq[j][g].p < (uint32_t)HV;
+            if (!need) break;
+#pragma unroll
+            for (int j = 0; j < NS; j++)
+              if (live[j] && sq[j][g].p < (uint32_t)HV)
+                lookup_once<W, V>(br[j][g], L, tb, syms, sq[j][g], bad);
+          }
+#pragma unroll
+          for (int j = 0; j < NS; j++)
+            if (live[j]) pop_vec<V>(sq[j][g], &gw[j][g][h * 2]);
         }
       }
-      uint32_t x[4];
-      if (DT == ZIPNN_FP32) {
-        uint32_t g4[4] = {gw[0][0], gw[1 % G][0], gw[2 % G][0], gw[3 % G][0]};
-        merge32(g4, x);
-      } else if (DT == ZIPNN_U8) {
-        x[0] = gw[0][0]; x[1] = gw[0][1]; x[2] = gw[0][2]; x[3] = gw[0][3];
-      } else {
-        merge16(gw[0][0], gw[1 % G][0], x[0], x[1]);
-        merge16(gw[0][1], gw[1 % G][1], x[2], x[3]);
-      }
-      if (full) {
-        x[0] ^= bv.x; x[1] ^= bv.y; x[2] ^= bv.z; x[3] ^= bv.w;
-        reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
-      } else {
-        for (uint64_t k = v * 16; k < nb; k++) {
-          uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
-          if (base) byte ^= base[k];
-          dst[k] = (uint8_t)byte;
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+        if (!live[j]) continue;
+        const uint32_t v = vv[j];
+#pragma unroll
+        for (int g = 0; g < G; g++)
+          if (mode[g] == kZero || mode[g] == kConst) {
+            gw[j][g][0] = cval[g]; gw[j][g][1] = cval[g]; gw[j][g][2] = cval[g]; gw[j][g][3] = cval[g];
+          }
+        uint32_t x[4];
+        if (DT == ZIPNN_FP32) {
+          uint32_t g4[4] = {gw[j][0][0], gw[j][1 % G][0], gw[j][2 % G][0], gw[j][3 % G][0]};
+          merge32(g4, x);
+        } else if (DT == ZIPNN_U8) {
+          x[0] = gw[j][0][0]; x[1] = gw[j][0][1]; x[2] = gw[j][0][2]; x[3] = gw[j][0][3];
+        } else {
+          merge16(gw[j][0][0], gw[j][1 % G][0], x[0], x[1]);
+          merge16(gw[j][0][1], gw[j][1 % G][1], x[2], x[3]);
+        }
+        if ((v + 1) * 16 <= nb) {
+          if (base) {
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
+            x[0] ^= b.x; x[1] ^= b.y; x[2] ^= b.z; x[3] ^= b.w;
+          }
+          reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
+        } else {
+          for (uint32_t k = v * 16; k < nb; k++) {
+            uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
+            if (base) byte ^= base[k];
+            dst[k] = (uint8_t)byte;
+          }
         }
       }
     }
@@ -500,8 +594,13 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
 #pragma unroll
   for (int g = 0; g < G; g++)
     if (CI.mode[g] == kHuff && CI.staged[g] == 0xFFFFFFFFu) all_staged = false;
-  if (all_staged) decode_loop<DT, W, SmemBitReader, true>(J, c, S, lut_base, stg, err);
-  else decode_loop<DT, W, BitReader, false>(J, c, S, lut_base, stg, err);
+  const bool two = J.lanes >= 2u * blockDim.x;  // two sub-streams per thread
+  if (all_staged) {
+    if (two) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, lut_base, stg, err);
+    else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, lut_base, stg, err);
+  } else {
+    decode_loop<DT, W, BitReader, false, 1>(J, c, S, lut_base, stg, err);
+  }
   return true;
 }
 

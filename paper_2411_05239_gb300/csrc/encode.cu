@@ -528,6 +528,60 @@ __device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* wsum) {
   __syncthreads();
 }
 
+// MSB-first writer of one unit's bits: acc holds nacc (< 32) pending bits;
+// whole words go out with a plain store, except the unit's first word, which
+// it shares with the previous unit (atomicOr into a zeroed word).
+struct BitWriter {
+  uint32_t* words;
+  uint64_t acc;
+  uint32_t nacc, wi, capw;
+  bool first;
+  __device__ __forceinline__ void put(uint32_t x, uint32_t n) {  // n <= 32, x < 2^n
+    acc = (acc << n) | x;
+    nacc += n;
+    if (nacc >= 32) {
+      nacc -= 32;
+      const uint32_t word = (uint32_t)(acc >> nacc);
+      if (wi < capw) {  // always true when the input did not change
+        if (first) atomicOr(&words[wi], word);
+        else words[wi] = word;
+      }
+      first = false;
+      wi++;
+      acc &= (1ull << nacc) - 1ull;
+    }
+  }
+  __device__ __forceinline__ void put64(uint64_t x, uint32_t n) {  // n <= 64
+    if (n > 32) {
+      put((uint32_t)(x >> 32), n - 32);
+      put((uint32_t)x, 32);
+    } else {
+      put((uint32_t)x, n);
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if (nacc > 0 && wi < capw) atomicOr(&words[wi], (uint32_t)(acc << (32 - nacc)));
+  }
+};
+
+// Codes of 4 consecutive symbols (bytes of w) joined MSB-first: <= 48 bits.
+__device__ __forceinline__ uint64_t join4(const uint32_t* codes, uint32_t w, uint32_t& len) {
+  uint32_t e0 = codes[__byte_perm(w, 0, 0x4440)], e1 = codes[__byte_perm(w, 0, 0x4441)];
+  uint32_t e2 = codes[__byte_perm(w, 0, 0x4442)], e3 = codes[__byte_perm(w, 0, 0x4443)];
+  const uint32_t l1 = e1 >> 16, l3 = e3 >> 16;
+  const uint32_t p0 = ((e0 & 0xFFFFu) << l1) | (e1 & 0xFFFFu);   // <= 24 bits
+  const uint32_t p1 = ((e2 & 0xFFFFu) << l3) | (e3 & 0xFFFFu);
+  const uint32_t lp0 = (e0 >> 16) + l1, lp1 = (e2 >> 16) + l3;
+  len = lp0 + lp1;
+  return ((uint64_t)p0 << lp1) | p1;
+}
+
+// Sum of the code lengths of the 4 bytes of w.
+__device__ __forceinline__ uint32_t len4(const uint32_t* codes, uint32_t w) {
+  return (codes[__byte_perm(w, 0, 0x4440)] >> 16) + (codes[__byte_perm(w, 0, 0x4441)] >> 16) +
+         (codes[__byte_perm(w, 0, 0x4442)] >> 16) + (codes[__byte_perm(w, 0, 0x4443)] >> 16);
+}
+
 template <int DT>
 __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t* codes,
                            const uint8_t* tabs, const GcMeta* meta, const uint64_t* offs) {
@@ -600,7 +654,7 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
         if (huff >> g & 1) {
           if (full) {
 #pragma unroll
-            for (int q = 0; q < V; q++) bits[g] += S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu] >> 16;
+            for (int q = 0; q < V / 4; q++) bits[g] += len4(S.codes[g], g4[g][q]);
           } else {
             for (int q = 0; q < valid; q++) bits[g] += S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu] >> 16;
           }
@@ -655,22 +709,19 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
   // pass B: emit
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T;
-    uint32_t* words[G];
-    uint64_t acc[G];
-    uint32_t nacc[G], wi[G], capw[G];
-    bool first[G];
+    BitWriter bw[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      words[g] = reinterpret_cast<uint32_t*>(out + P + S.off[g] + S.hsz[g]);
+      bw[g].words = reinterpret_cast<uint32_t*>(out + P + S.off[g] + S.hsz[g]);
       const uint32_t st = (huff >> g & 1) ? S.part[g][t * R + k] : 0u;
-      acc[g] = 0;
-      nacc[g] = st & 31;
-      wi[g] = st >> 5;
-      first[g] = (st & 31) != 0;
-      capw[g] = S.capw[g];
+      bw[g].acc = 0;
+      bw[g].nacc = st & 31;
+      bw[g].wi = st >> 5;
+      bw[g].first = (st & 31) != 0;
+      bw[g].capw = S.capw[g];
     }
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
-    constexpr int U = 4;  // vectors in flight per thread
+    constexpr int U = 2;  // vectors in flight per thread
     for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
       uint4 a[U];
 #pragma unroll
@@ -680,41 +731,34 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
       }
 #pragma unroll
       for (int u = 0; u < U; u++) {
-      const uint64_t v = t + (i0 + u) * T;
-      if (i0 + u >= i1 || v >= nvec) break;
-      uint32_t g4[4][4];
-      split_vec(DT, a[u], g4);
-      const int valid = (int)min((uint64_t)V, m - v * V);
+        const uint64_t v = t + (i0 + u) * T;
+        if (i0 + u >= i1 || v >= nvec) break;
+        uint32_t g4[4][4];
+        split_vec(DT, a[u], g4);
+        const bool full = (v + 1) * V <= m;
 #pragma unroll
-      for (int g = 0; g < G; g++) {
-        if (!(huff >> g & 1)) continue;
+        for (int g = 0; g < G; g++) {
+          if (!(huff >> g & 1)) continue;
+          if (full) {
 #pragma unroll
-        for (int q = 0; q < V; q++) {
-          if (q >= valid) break;
-          const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
-          const uint32_t len = cl >> 16;
-          acc[g] = (acc[g] << len) | (cl & 0xFFFFu);
-          nacc[g] += len;
-          if (nacc[g] >= 32) {
-            nacc[g] -= 32;
-            const uint32_t word = (uint32_t)(acc[g] >> nacc[g]);
-            if (wi[g] < capw[g]) {  // always true when the input did not change
-              if (first[g]) atomicOr(&words[g][wi[g]], word);
-              else words[g][wi[g]] = word;
+            for (int q = 0; q < V / 4; q++) {
+              uint32_t len;
+              const uint64_t x = join4(S.codes[g], g4[g][q], len);
+              bw[g].put64(x, len);
             }
-            first[g] = false;
-            wi[g]++;
+          } else {
+            const int valid = (int)(m - v * V);
+            for (int q = 0; q < valid; q++) {
+              const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
+              bw[g].put(cl & 0xFFFFu, cl >> 16);
+            }
           }
         }
       }
-      }
     }
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-      if (!(huff >> g & 1)) continue;
-      if (nacc[g] > 0 && wi[g] < capw[g])
-        atomicOr(&words[g][wi[g]], (uint32_t)(acc[g] << (32 - nacc[g])));
-    }
+    for (int g = 0; g < G; g++)
+      if (huff >> g & 1) bw[g].flush();
   }
 }
 

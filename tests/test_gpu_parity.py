@@ -338,3 +338,24 @@ def test_decoder_settings_do_not_change_bytes(w, ctas):
     Z.sync_status()
     for x, o in zip(xs, outs):
         assert torch.equal(o.cpu().view(torch.uint8), x.view(torch.uint8))
+
+
+@pytest.mark.parametrize("lanes", [256, 300, 512])
+def test_two_substreams_per_thread_path(lanes):
+    """Chunks with >= 2x as many sub-streams as decoder threads take the
+    two-streams-per-thread decode loop; bytes must not change."""
+    xs = [W.gaussian(n, 0.02, 70 + i) for i, n in enumerate([300_001, 131_072, 5000])]
+    cs = []
+    for x in xs:
+        c = Z.compress(x.cuda(), chunk_bytes=262144, lanes=lanes)
+        assert c.to_bytes() == O.compress(u8(x), Z.BF16, 262144, lanes)
+        cs.append(c)
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    for w in (10, 12):
+        Z.batch_decompress(cs, outs, tune=Z.tuning(lut_bits=w))
+        Z.sync_status()
+        for x, o in zip(xs, outs):
+            assert torch.equal(o.cpu().view(torch.int16), x.view(torch.int16))
+    y = Z.decompress(cs[0])
+    Z.sync_status()
+    assert torch.equal(y.cpu().view(torch.int16), xs[0].view(torch.int16))
