@@ -35,7 +35,6 @@ namespace zipnn {
 namespace {
 
 constexpr int kDecThreads = 128;
-constexpr uint32_t kSlow = 0u;           // entry with n == 0: resolve on the slow path
 constexpr uint32_t kStageBytes = 45056;  // shared-memory staging for Huffman payloads
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -113,6 +112,7 @@ struct ChunkInfo {
 struct Smem {
   ChunkInfo ci;
   GroupTab tab[4];
+  uint32_t* lut_ptr[4];  // pair table of each Huffman group
   unsigned long long chunk;
 };
 
@@ -152,63 +152,8 @@ struct BitReader {
   }
 };
 
-// Slow path: the first code of the 12-bit window is longer than W bits (or is
-// not a code at all).  Returns a one-symbol entry (n = 1, consumed = length).
-template <int W>
-__device__ __noinline__ uint32_t slow_entry(const GroupTab& t, const uint8_t* syms,
-                                            uint32_t win12, uint32_t& bad) {
-  int l = W + 1;
-  while (l <= kMaxLen && win12 >= t.lim[l]) l++;
-  if (l > kMaxLen) {
-    bad = 1;
-    return (1u << 24) | ((uint32_t)kMaxLen << 26);
-  }
-  const uint32_t r = t.index[l] + (win12 >> (kMaxLen - l)) - t.first[l];
-  return (uint32_t)syms[r & 255] | (1u << 24) | ((uint32_t)l << 26);
-}
-
-// Decode the next V symbols of a sub-stream into out[] (little-endian bytes).
-// Table entries: bits 0-23 up to three symbols, 24-25 count n, 26-29 bits
-// consumed.  lo:hi carry symbols decoded past the vector boundary.
-template <int V>
-struct SymQueue {
-  uint64_t lo;
-  uint32_t hi;
-  uint32_t p;  // symbols held
-};
-
-template <int W, int V, class BR>
-__device__ __forceinline__ void decode_vec(BR& br, const uint32_t* lut, const GroupTab& t,
-                                           const uint8_t* syms, SymQueue<V>& q, uint32_t out[4],
-                                           uint32_t& bad) {
-  constexpr int HALF = V == 16 ? 8 : V;
-#pragma unroll
-  for (int half = 0; half < V / HALF; half++) {
-    while (q.p < (uint32_t)HALF) {
-      uint32_t e = lut[br.peek32() >> (32 - W)];
-      if ((e >> 24 & 3u) == kSlow) e = slow_entry<W>(t, syms, br.peek32() >> (32 - kMaxLen), bad);
-      const uint32_t s24 = e & 0xFFFFFFu, sh = 8u * q.p;
-      q.lo |= (uint64_t)s24 << sh;
-      if (sh >= 48) q.hi |= s24 >> (64 - sh);
-      q.p += e >> 24 & 3u;
-      br.skip(e >> 26);
-    }
-    if (HALF == 8) {
-      out[2 * half] = (uint32_t)q.lo;
-      out[2 * half + 1] = (uint32_t)(q.lo >> 32);
-      q.lo = q.hi;
-      q.hi = 0;
-      q.p -= 8;
-    } else {  // HALF == 4
-      out[0] = (uint32_t)q.lo;
-      q.lo = (q.lo >> 32) | ((uint64_t)q.hi << 32);
-      q.hi = 0;
-      q.p -= 4;
-    }
-  }
-}
-
-// Reader over a bitstream staged in shared memory (all words present).
+// Reader over a bitstream staged in shared memory (all words present; the
+// staging leaves slack after each payload for the look-ahead word).
 struct SmemBitReader {
   const uint32_t* w;
   uint32_t idx, w0, w1, pos;
@@ -218,7 +163,7 @@ struct SmemBitReader {
     idx = start >> 5;
     pos = start & 31;
     w0 = w[idx];
-    w1 = w[idx + 1];  // the format pads every payload: one word past the end is readable
+    w1 = w[idx + 1];
     idx += 2;
   }
   __device__ __forceinline__ uint32_t peek32() const { return __funnelshift_l(w1, w0, pos); }
@@ -236,6 +181,50 @@ __device__ __forceinline__ uint32_t rd_u32(const uint8_t* p) {
   return __ldg(reinterpret_cast<const uint32_t*>(p));
 }
 
+// Pair tables.  The entry for a W-bit window w describes the codes at its
+// start:  bits 0-7 first symbol, 8-15 second symbol, 16-19 length l1 of the
+// first code (0: longer than W or invalid -> slow path), 20-24 length of both
+// codes, bit 25 set when both codes lie wholly inside the window.
+constexpr uint32_t kPair = 1u << 25;
+
+// Slow path: resolve the first code of a 12-bit window with the canonical
+// limits.  Returns (symbol | length << 16); flags windows that start no code.
+__device__ __noinline__ uint32_t slow_code(const GroupTab& t, const uint8_t* syms, uint32_t win12,
+                                           uint32_t& bad) {
+  int l = 1;
+  while (l <= kMaxLen && win12 >= t.lim[l]) l++;
+  if (l > kMaxLen) {
+    bad = 1;
+    return (uint32_t)kMaxLen << 16;
+  }
+  const uint32_t r = t.index[l] + (win12 >> (kMaxLen - l)) - t.first[l];
+  return (uint32_t)syms[r & 255] | ((uint32_t)l << 16);
+}
+
+// One symbol from the table (first code only), with the slow path.
+template <int W, class BR>
+__device__ __forceinline__ uint32_t one_symbol(BR& br, const uint32_t* lut, const GroupTab& t,
+                                               const uint8_t* syms, uint32_t& bad) {
+  uint32_t e = lut[br.peek32() >> (32 - W)];
+  if (((e >> 16) & 15u) == 0) e = slow_code(t, syms, br.peek32() >> (32 - kMaxLen), bad);
+  br.skip((e >> 16) & 15u);
+  return e & 0xFFu;
+}
+
+// Two symbols (sym0 | sym1 << 8): one lookup when both codes fit in the window.
+template <int W, class BR>
+__device__ __forceinline__ uint32_t two_symbols(BR& br, const uint32_t* lut, const GroupTab& t,
+                                                const uint8_t* syms, uint32_t& bad) {
+  const uint32_t e = lut[br.peek32() >> (32 - W)];
+  if (e & kPair) {
+    br.skip((e >> 20) & 31u);
+    return e & 0xFFFFu;
+  }
+  const uint32_t s0 = one_symbol<W>(br, lut, t, syms, bad);
+  const uint32_t s1 = one_symbol<W>(br, lut, t, syms, bad);
+  return s0 | (s1 << 8);
+}
+
 struct Staging {
   uint8_t* base;       // shared-memory stage
   uint64_t* bar;       // its mbarrier
@@ -244,45 +233,13 @@ struct Staging {
   uint64_t limit_ns;   // wait limit
 };
 
-// One lookup of a sub-stream into its queue (up to three symbols).
-template <int W, int V, class BR>
-__device__ __forceinline__ void lookup_once(BR& br, const uint32_t* lut, const GroupTab& t,
-                                            const uint8_t* syms, SymQueue<V>& q, uint32_t& bad) {
-  uint32_t e = lut[br.peek32() >> (32 - W)];
-  if ((e >> 24 & 3u) == kSlow) e = slow_entry<W>(t, syms, br.peek32() >> (32 - kMaxLen), bad);
-  const uint32_t s24 = e & 0xFFFFFFu, sh = 8u * q.p;
-  q.lo |= (uint64_t)s24 << sh;
-  if (sh >= 48) q.hi |= s24 >> (64 - sh);
-  q.p += e >> 24 & 3u;
-  br.skip(e >> 26);
-}
-
-template <int V>
-__device__ __forceinline__ void pop_vec(SymQueue<V>& q, uint32_t* out) {
-  if (V == 4) {
-    out[0] = (uint32_t)q.lo;
-    q.lo = (q.lo >> 32) | ((uint64_t)q.hi << 32);
-    q.hi = 0;
-    q.p -= 4;
-  } else {  // 8 symbols
-    out[0] = (uint32_t)q.lo;
-    out[1] = (uint32_t)(q.lo >> 32);
-    q.lo = q.hi;
-    q.hi = 0;
-    q.p -= 8;
-  }
-}
-
-// Decode loop of one chunk.  Each thread owns NS sub-streams (t, t + nthr,
-// ...) and advances them in lockstep, one vector each per step; the lookups
-// of different sub-streams are independent, which gives the scheduler
-// instruction-level parallelism inside a warp.
-template <int DT, int W, class BR, bool STAGED, int NS>
-__device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
-                                            Staging& stg, uint32_t* err) {
+// Decode loop of one chunk: thread t owns sub-stream t; each step decodes one
+// 16-byte vector (V symbols per Huffman group, V/2 pair lookups each), merges
+// it with the raw / constant groups and stores it.
+template <int DT, int W, class BR, bool STAGED>
+__device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
+                                            uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
-  constexpr int HV = V == 16 ? 8 : V;  // symbols per queue pop
-  constexpr int kLut = 1 << W;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
   const uint32_t nb = (uint32_t)min((uint64_t)J.chunk_bytes, J.nbytes - off0);
@@ -292,11 +249,10 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, u
   ChunkInfo& CI = S.ci;
   uint8_t* dst = J.dst + off0;
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
-  // per-chunk values in registers
-  uint32_t mode[G], cval[G], nwords[G];
+  uint32_t mode[G], cval[G], nwords[G], offs[G], bsoff[G];
   const uint8_t* rawp[G];
   const uint8_t* pay[G];
-  uint32_t offs[G], bsoff[G];
+  const uint32_t* lut[G];
 #pragma unroll
   for (int g = 0; g < G; g++) {
     mode[g] = CI.mode[g];
@@ -306,130 +262,85 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, u
     pay[g] = STAGED ? stg.base + CI.staged[g] : cont + CI.payload[g];
     offs[g] = (uint32_t)CI.offs[g];
     bsoff[g] = (uint32_t)CI.bs[g];
+    lut[g] = reinterpret_cast<const uint32_t*>(S.lut_ptr[g]);
   }
   uint32_t bad = 0;
-  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
-    BR br[NS][G];
-    SymQueue<V> sq[NS][G];
-    uint32_t tt[NS];
-    bool act[NS];
+  for (uint32_t t = tid; t < T; t += nthr) {
+    BR br[G];
 #pragma unroll
-    for (int j = 0; j < NS; j++) {
-      tt[j] = t0 + j * nthr;
-      act[j] = tt[j] < T;
-#pragma unroll
-      for (int g = 0; g < G; g++) {
-        sq[j][g].lo = 0;
-        sq[j][g].hi = 0;
-        sq[j][g].p = 0;
-        if (mode[g] != kHuff) continue;
-        const uint32_t t = act[j] ? tt[j] : 0u;
-        uint32_t start = 0;
-        if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
-                              : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
-        if (start > nwords[g] * 32u) {
-          bad = 1;
-          start = nwords[g] * 32u;
-        }
-        br[j][g].init(reinterpret_cast<const uint32_t*>(pay[g] + bsoff[g]), nwords[g], start);
+    for (int g = 0; g < G; g++) {
+      if (mode[g] != kHuff) continue;
+      uint32_t start = 0;
+      if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
+                            : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
+      if (start > nwords[g] * 32u) {
+        bad = 1;
+        start = nwords[g] * 32u;
       }
+      br[g].init(reinterpret_cast<const uint32_t*>(pay[g] + bsoff[g]), nwords[g], start);
     }
     // raw group bytes, prefetched one vector ahead
-    uint32_t rawn[NS][G][4] = {};
-    auto load_raw = [&](int j, uint32_t v) {
+    uint32_t rawn[G][4] = {};
+    auto load_raw = [&](uint32_t v) {
 #pragma unroll
       for (int g = 0; g < G; g++) {
         if (mode[g] != kRaw || v >= nvec) continue;
         const uint8_t* p = rawp[g] + (size_t)v * V;
         if (V == 8) {
           const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
-          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y;
+          rawn[g][0] = x.x; rawn[g][1] = x.y;
         } else if (V == 4) {
-          rawn[j][g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+          rawn[g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
         } else {
           const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
-          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y; rawn[j][g][2] = x.z; rawn[j][g][3] = x.w;
+          rawn[g][0] = x.x; rawn[g][1] = x.y; rawn[g][2] = x.z; rawn[g][3] = x.w;
         }
       }
     };
+    load_raw(t);
+    for (uint32_t v = t; v < nvec; v += T) {
+      uint32_t gw[G][4];
 #pragma unroll
-    for (int j = 0; j < NS; j++)
-      if (act[j]) load_raw(j, tt[j]);
-    for (uint32_t kstep = 0;; kstep++) {
-      uint32_t vv[NS];
-      bool live[NS];
-      bool any = false;
+      for (int g = 0; g < G; g++)
 #pragma unroll
-      for (int j = 0; j < NS; j++) {
-        vv[j] = tt[j] + kstep * T;
-        live[j] = act[j] && vv[j] < nvec;
-        any |= live[j];
-      }
-      if (!any) break;
-      uint32_t gw[NS][G][4];
-#pragma unroll
-      for (int j = 0; j < NS; j++) {
-#pragma unroll
-        for (int g = 0; g < G; g++)
-#pragma unroll
-          for (int k = 0; k < 4; k++) gw[j][g][k] = rawn[j][g][k];
-        if (live[j]) load_raw(j, vv[j] + T);
-      }
-      // Huffman groups: the NS queues are filled in one loop (independent lookups)
+        for (int k = 0; k < 4; k++) gw[g][k] = rawn[g][k];
+      load_raw(v + T);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        if (mode[g] != kHuff) continue;
-        const uint32_t* L = lut_base + g * kLut;
-        const GroupTab& tb = S.tab[g];
-        const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+        if (mode[g] == kHuff) {
+          const GroupTab& tb = S.tab[g];
+          const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
 #pragma unroll
-        for (int h = 0; h < V / HV; h++) {
-          for (;;) {
-            bool need = false;
-#pragma unroll
-            for (int j = 0; j < NS; j++) need |= live[j] && sq[j][g].p < (uint32_t)HV;
-            if (!need) break;
-#pragma unroll
-            for (int j = 0; j < NS; j++)
-              if (live[j] && sq[j][g].p < (uint32_t)HV)
-                lookup_once<W, V>(br[j][g], L, tb, syms, sq[j][g], bad);
+          for (int q = 0; q < V / 4; q++) {
+            const uint32_t a = two_symbols<W>(br[g], lut[g], tb, syms, bad);
+            const uint32_t b = two_symbols<W>(br[g], lut[g], tb, syms, bad);
+            gw[g][q] = a | (b << 16);
           }
-#pragma unroll
-          for (int j = 0; j < NS; j++)
-            if (live[j]) pop_vec<V>(sq[j][g], &gw[j][g][h * 2]);
+        } else if (mode[g] != kRaw) {
+          gw[g][0] = cval[g]; gw[g][1] = cval[g]; gw[g][2] = cval[g]; gw[g][3] = cval[g];
         }
       }
-#pragma unroll
-      for (int j = 0; j < NS; j++) {
-        if (!live[j]) continue;
-        const uint32_t v = vv[j];
-#pragma unroll
-        for (int g = 0; g < G; g++)
-          if (mode[g] == kZero || mode[g] == kConst) {
-            gw[j][g][0] = cval[g]; gw[j][g][1] = cval[g]; gw[j][g][2] = cval[g]; gw[j][g][3] = cval[g];
-          }
-        uint32_t x[4];
-        if (DT == ZIPNN_FP32) {
-          uint32_t g4[4] = {gw[j][0][0], gw[j][1 % G][0], gw[j][2 % G][0], gw[j][3 % G][0]};
-          merge32(g4, x);
-        } else if (DT == ZIPNN_U8) {
-          x[0] = gw[j][0][0]; x[1] = gw[j][0][1]; x[2] = gw[j][0][2]; x[3] = gw[j][0][3];
-        } else {
-          merge16(gw[j][0][0], gw[j][1 % G][0], x[0], x[1]);
-          merge16(gw[j][0][1], gw[j][1 % G][1], x[2], x[3]);
+      uint32_t x[4];
+      if (DT == ZIPNN_FP32) {
+        uint32_t g4[4] = {gw[0][0], gw[1 % G][0], gw[2 % G][0], gw[3 % G][0]};
+        merge32(g4, x);
+      } else if (DT == ZIPNN_U8) {
+        x[0] = gw[0][0]; x[1] = gw[0][1]; x[2] = gw[0][2]; x[3] = gw[0][3];
+      } else {
+        merge16(gw[0][0], gw[1 % G][0], x[0], x[1]);
+        merge16(gw[0][1], gw[1 % G][1], x[2], x[3]);
+      }
+      if ((v + 1) * 16 <= nb) {
+        if (base) {
+          const uint4 bb = __ldg(reinterpret_cast<const uint4*>(base) + v);
+          x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
         }
-        if ((v + 1) * 16 <= nb) {
-          if (base) {
-            const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
-            x[0] ^= b.x; x[1] ^= b.y; x[2] ^= b.z; x[3] ^= b.w;
-          }
-          reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
-        } else {
-          for (uint32_t k = v * 16; k < nb; k++) {
-            uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
-            if (base) byte ^= base[k];
-            dst[k] = (uint8_t)byte;
-          }
+        reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
+      } else {
+        for (uint32_t k = v * 16; k < nb; k++) {
+          uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
+          if (base) byte ^= base[k];
+          dst[k] = (uint8_t)byte;
         }
       }
     }
@@ -437,18 +348,20 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, u
   if (bad) atomicOr(err, 1u);
 }
 
-// Decode one chunk of a tensor of dtype DT with W-bit tables.  Returns false
-// if a bulk copy never completed (the caller must stop using shared memory).
+// Decode one chunk of a tensor of dtype DT with W-bit pair tables.  Returns
+// false if a bulk copy never completed (the caller must stop using the stage).
+// Shared memory: one table slot (lut0) for the first Huffman group; tables of
+// further Huffman groups and the staged payloads share the stage.
 template <int DT, int W>
-__device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_base,
-                             Staging& stg, uint32_t* err) {
+__device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, Staging& stg,
+                             uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V, ES = 16 / V;
   constexpr int kLut = 1 << W;
+  constexpr uint32_t kLutBytes = 4u << W;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
   const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off0);
   const uint64_t m = nb / ES;
-  const uint64_t nvec = (nb + 15) / 16;
   const uint32_t T = J.lanes;
   const uint8_t* cont = J.src;
   const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
@@ -478,19 +391,34 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
     if (tid == 0) atomicOr(err, 1u);
     return true;
   }
-  // 2. stage the Huffman payloads that fit (thread 0 issues the bulk copies)
+  // 2. placement of tables and payloads; thread 0 issues the bulk copies
   if (tid == 0) {
-    uint32_t used = 0;
+    uint32_t nhuff = 0, pay_total = 0;
+    for (int g = 0; g < G; g++)
+      if (CI.mode[g] == kHuff) {
+        nhuff++;
+        pay_total += (uint32_t)align_up(CI.size[g], 16);
+      }
+    const uint32_t extra = nhuff > 1 ? (nhuff - 1) * kLutBytes : 0u;
+    const bool stage_payloads = nhuff && pay_total + extra + 32 <= kStageBytes;
+    uint32_t used = 0, k = 0;
     for (int g = 0; g < G; g++) {
       CI.staged[g] = 0xFFFFFFFFu;
+      S.lut_ptr[g] = lut0;
       if (CI.mode[g] != kHuff) continue;
-      const uint32_t padded = (uint32_t)align_up(CI.size[g], 16);
-      if (used + padded + 32 <= kStageBytes) {  // 32 B slack: readers look ahead
+      if (stage_payloads) {
         CI.staged[g] = used;
-        used += padded;
+        used += (uint32_t)align_up(CI.size[g], 16);
       }
+      if (k++) S.lut_ptr[g] = nullptr;  // placed after the staged payloads below
     }
     CI.stage_bytes = used;
+    uint32_t lo = (used + 32 + 127) & ~127u;
+    for (int g = 0; g < G; g++)
+      if (CI.mode[g] == kHuff && S.lut_ptr[g] == nullptr) {
+        S.lut_ptr[g] = reinterpret_cast<uint32_t*>(stg.base + lo);
+        lo += kLutBytes;
+      }
     if (used) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(stg.bar, used + stg.extra_tx);
@@ -539,8 +467,9 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
   }
   __syncthreads();
   const bool bad_tab = CI.bad != 0;
-  // 3c. multi-symbol tables.  Window w (W bits): first code length
-  // l1 = 1 + #{l <= W : lim_W[l] <= w}; if l1 > W, slow path.
+  // 3c. pair tables.  For window w (W bits) the first code has length
+  // l1 = 1 + #{l <= W : lim_W[l] <= w}; the second code is found the same way
+  // in the remaining W - l1 bits (zero-filled), and kept only if it fits.
   if (!bad_tab) {
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -550,23 +479,25 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
       uint32_t limw[W + 1];
 #pragma unroll
       for (int l = 1; l <= W; l++) limw[l] = t.lim[l] >> (kMaxLen - W);
-      uint32_t* L = lut_base + g * kLut;
+      uint32_t* L = S.lut_ptr[g];
       for (int w = tid; w < kLut; w += nthr) {
-        uint32_t ent = 0, n = 0, used = 0;
-        uint32_t rest = (uint32_t)w;  // remaining window bits, left-aligned in W bits
+        uint32_t l1 = 1;
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-          uint32_t l = 1;
+        for (int q = 1; q <= W; q++) l1 += (limw[q] <= (uint32_t)w);
+        uint32_t ent = 0;
+        if (l1 <= (uint32_t)W) {
+          const uint32_t r1 = t.index[l1] + ((uint32_t)w >> (W - l1)) - t.first[l1];
+          ent = (uint32_t)syms[r1 & 255] | (l1 << 16);
+          const uint32_t rest = ((uint32_t)w << l1) & (kLut - 1);
+          uint32_t l2 = 1;
 #pragma unroll
-          for (int q = 1; q <= W; q++) l += (limw[q] <= rest);
-          if (l > (uint32_t)(W - used)) break;  // code not wholly inside the window
-          const uint32_t r = t.index[l] + (rest >> (W - l)) - t.first[l];
-          ent |= (uint32_t)syms[r & 255] << (8 * k);
-          n++;
-          used += l;
-          rest = (rest << l) & (kLut - 1);
+          for (int q = 1; q <= W; q++) l2 += (limw[q] <= rest);
+          if (l1 + l2 <= (uint32_t)W) {
+            const uint32_t r2 = t.index[l2] + (rest >> (W - l2)) - t.first[l2];
+            ent |= ((uint32_t)syms[r2 & 255] << 8) | ((l1 + l2) << 20) | kPair;
+          }
         }
-        L[w] = n ? (ent | (n << 24) | (used << 26)) : kSlow;
+        L[w] = ent;
       }
     }
   }
@@ -587,20 +518,9 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
     if (tid == 0) atomicOr(err, 1u);
     return true;
   }
-
-  // 4. decode + merge: shared-memory readers when every Huffman payload was
-  // staged, global-memory readers otherwise (payload larger than the stage)
-  bool all_staged = true;
-#pragma unroll
-  for (int g = 0; g < G; g++)
-    if (CI.mode[g] == kHuff && CI.staged[g] == 0xFFFFFFFFu) all_staged = false;
-  const bool two = J.lanes >= 2u * blockDim.x;  // two sub-streams per thread
-  if (all_staged) {
-    if (two) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, lut_base, stg, err);
-    else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, lut_base, stg, err);
-  } else {
-    decode_loop<DT, W, BitReader, false, 1>(J, c, S, lut_base, stg, err);
-  }
+  // 4. decode + merge
+  if (CI.stage_bytes) decode_loop<DT, W, SmemBitReader, true>(J, c, S, stg, err);
+  else decode_loop<DT, W, BitReader, false>(J, c, S, stg, err);
   return true;
 }
 
@@ -608,13 +528,13 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut_ba
 template <int DTS, int W>
 __global__ void __launch_bounds__(kDecThreads)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
-         unsigned long long* __restrict__ ticket, int max_groups, uint32_t debug_flags) {
-  extern __shared__ __align__(128) uint8_t dsm[];  // [groups][2^W] tables | stage
+         unsigned long long* __restrict__ ticket, uint32_t debug_flags) {
+  extern __shared__ __align__(128) uint8_t dsm[];  // [table slot 0] | stage
   __shared__ Smem S;
   __shared__ uint64_t bar;
-  uint32_t* lut_smem = reinterpret_cast<uint32_t*>(dsm);
+  uint32_t* lut0 = reinterpret_cast<uint32_t*>(dsm);
   Staging stg;
-  stg.base = dsm + (size_t)max_groups * (4u << W);
+  stg.base = dsm + (4u << W);
   stg.bar = &bar;
   stg.parity = 0;
   // debug flag 1 (tests only): expect 16 bytes more than the bulk copies send,
@@ -640,13 +560,13 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     const uint64_t c = chunk - J.chunk_begin;
     bool ok;
     if (DTS >= 0) {
-      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W>(J, c, S, lut_smem, stg, err);
+      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W>(J, c, S, lut0, stg, err);
     } else {
       switch (J.dtype) {
-        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W>(J, c, S, lut_smem, stg, err); break;
-        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W>(J, c, S, lut_smem, stg, err); break;
-        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W>(J, c, S, lut_smem, stg, err); break;
-        default: ok = decode_chunk<ZIPNN_U8, W>(J, c, S, lut_smem, stg, err); break;
+        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W>(J, c, S, lut0, stg, err); break;
+        default: ok = decode_chunk<ZIPNN_U8, W>(J, c, S, lut0, stg, err); break;
       }
     }
     if (!ok) return;  // a bulk copy timed out: leave the stage alone
@@ -654,7 +574,7 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   }
 }
 
-using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, int, uint32_t);
+using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, uint32_t);
 
 template <int W>
 DecodeKernel pick_kernel(int dt) {
@@ -669,7 +589,10 @@ DecodeKernel pick_kernel(int dt) {
 
 }  // namespace
 
-int decode_smem_bytes(int max_groups, int w) { return max_groups * (4 << w) + (int)kStageBytes; }
+int decode_smem_bytes(int max_groups, int w) {
+  (void)max_groups;  // further groups' tables live in the stage
+  return (4 << w) + (int)kStageBytes;
+}
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
@@ -707,7 +630,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     if (e != cudaSuccess) return e;
   }
   const uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
-  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, max_groups, dbg);
+  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, dbg);
   return cudaGetLastError();
 }
 

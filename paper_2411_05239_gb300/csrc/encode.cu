@@ -129,7 +129,8 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
       if (v >= nvec) break;
       uint32_t g[4][4];
       split_vec(DT, a[u], g);
-      if ((v + 1) * V <= m) {
+      const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
+      if (valid == V) {
 #pragma unroll
         for (int k = 0; k < V; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
 #pragma unroll
@@ -138,7 +139,6 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
           for (int k = 0; k < V; k++)
             atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
       } else {
-        const int valid = (int)(m - v * V);
         for (int k = 0; k < valid; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
         for (int gg = 1; gg < G; gg++)
           for (int k = 0; k < valid; k++)
@@ -469,6 +469,7 @@ k_scan(JobRef jr, const GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
 
 constexpr int kPackThreads = 512;
 constexpr int kPackMaxUnits = 1024;
+constexpr uint32_t kPackSlotWords = 20480;  // 80 KiB of unit slots
 
 __device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
   for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
@@ -491,6 +492,7 @@ struct PackSmem {
   uint64_t off[4];
   uint32_t capw[4];   // bitstream words available in the payload
   uint32_t hsz[4];    // table + start-offset bytes before the bitstream
+  uint32_t sbits[kPackMaxUnits];  // bits of each unit of the slot-staged group
 };
 
 // Exclusive scan of a[0..n) in place (block-wide); n <= kPackMaxUnits.
@@ -564,6 +566,37 @@ struct BitWriter {
   }
 };
 
+// MSB-first writer into a unit's private shared-memory slot of cap words.
+// Counts every bit; words past the slot are dropped (the unit then takes the
+// fallback path that re-reads its input).
+struct SlotWriter {
+  uint32_t* slot;
+  uint64_t acc;
+  uint32_t nacc, wi, cap, bits;
+  __device__ __forceinline__ void put(uint32_t x, uint32_t n) {  // n <= 32, x < 2^n
+    acc = (acc << n) | x;
+    nacc += n;
+    bits += n;
+    if (nacc >= 32) {
+      nacc -= 32;
+      if (wi < cap) slot[wi] = (uint32_t)(acc >> nacc);
+      wi++;
+      acc &= (1ull << nacc) - 1ull;
+    }
+  }
+  __device__ __forceinline__ void put64(uint64_t x, uint32_t n) {
+    if (n > 32) {
+      put((uint32_t)(x >> 32), n - 32);
+      put((uint32_t)x, 32);
+    } else {
+      put((uint32_t)x, n);
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    if (nacc > 0 && wi < cap) slot[wi] = (uint32_t)(acc << (32 - nacc));
+  }
+};
+
 // Codes of 4 consecutive symbols (bytes of w) joined MSB-first: <= 48 bits.
 __device__ __forceinline__ uint64_t join4(const uint32_t* codes, uint32_t w, uint32_t& len) {
   uint32_t e0 = codes[__byte_perm(w, 0, 0x4440)], e1 = codes[__byte_perm(w, 0, 0x4441)];
@@ -583,8 +616,9 @@ __device__ __forceinline__ uint32_t len4(const uint32_t* codes, uint32_t w) {
 }
 
 template <int DT>
-__device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t* codes,
-                           const uint8_t* tabs, const GcMeta* meta, const uint64_t* offs) {
+__device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
+                           const uint32_t* codes, const uint8_t* tabs, const GcMeta* meta,
+                           const uint64_t* offs) {
   constexpr int G = PTraits<DT>::G, V = PTraits<DT>::V, ES = 16 / V;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
@@ -626,14 +660,31 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
       for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
   __syncthreads();
 
-  // pass A: unit bits (+ raw planes)
+  // The first Huffman group is encoded once, in pass A, into per-unit slots in
+  // shared memory (slot_cap words each, odd so that neighbouring slots fall in
+  // different banks); pass B only shifts the slot words into place.
+  int sg = -1;
+#pragma unroll
+  for (int g = G - 1; g >= 0; g--)
+    if (huff >> g & 1) sg = g;
+  uint32_t slot_cap = (uint32_t)(kPackSlotWords / units);
+  if (!(slot_cap & 1u)) slot_cap--;
+
+  // pass A: unit bits (+ raw planes, + slot encoding of group sg)
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T;
     uint32_t bits[G];
 #pragma unroll
     for (int g = 0; g < G; g++) bits[g] = 0;
+    SlotWriter sw;
+    sw.slot = slots + (size_t)(t * R + k) * slot_cap;
+    sw.acc = 0;
+    sw.nacc = 0;
+    sw.wi = 0;
+    sw.cap = slot_cap;
+    sw.bits = 0;
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
-    constexpr int U = 4;  // vectors in flight per thread
+    constexpr int U = 2;  // vectors in flight per thread
     for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
       uint4 a[U];
 #pragma unroll
@@ -651,7 +702,21 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
       const int valid = full ? V : (int)(m - v * V);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        if (huff >> g & 1) {
+        if (g == sg) {
+          if (full) {
+#pragma unroll
+            for (int q = 0; q < V / 4; q++) {
+              uint32_t len;
+              const uint64_t x = join4(S.codes[g], g4[g][q], len);
+              sw.put64(x, len);
+            }
+          } else {
+            for (int q = 0; q < valid; q++) {
+              const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
+              sw.put(cl & 0xFFFFu, cl >> 16);
+            }
+          }
+        } else if (huff >> g & 1) {
           if (full) {
 #pragma unroll
             for (int q = 0; q < V / 4; q++) bits[g] += len4(S.codes[g], g4[g][q]);
@@ -670,6 +735,11 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
         }
       }
       }
+    }
+    if (sg >= 0) {
+      sw.finish();
+      bits[sg] = sw.bits;
+      S.sbits[t * R + k] = sw.bits;
     }
 #pragma unroll
     for (int g = 0; g < G; g++) S.part[g][t * R + k] = bits[g];
@@ -706,14 +776,47 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
   }
   __syncthreads();
 
-  // pass B: emit
+  // pass B
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T;
+    const uint32_t ui = t * R + k;
+    // (1) slot-staged group: shift the unit's slot words to its bit offset
+    bool refill = false;
+    if (sg >= 0) {
+      const uint32_t nbits = S.sbits[ui];
+      if (nbits > slot_cap * 32u) {
+        refill = true;  // slot overflowed: re-encode below from the input
+      } else if (nbits) {
+        uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[sg] + S.hsz[sg]);
+        const uint32_t* sl = slots + (size_t)ui * slot_cap;
+        const uint32_t o = S.part[sg][ui], sh = o & 31, w0 = o >> 5;
+        const uint32_t end = o + nbits, wl = (end - 1) >> 5;
+        const uint32_t nsw = (nbits + 31) >> 5;
+        uint32_t prev = 0;
+        for (uint32_t w = w0; w <= wl; w++) {
+          const uint32_t i = w - w0;
+          const uint32_t cur = i < nsw ? sl[i] : 0u;
+          const uint32_t word = __funnelshift_r(cur, prev, sh);
+          prev = cur;
+          if (w >= S.capw[sg]) break;  // never taken for a consistent input
+          if ((w == w0 && sh) || (w == wl && (end & 31))) atomicOr(&words[w], word);
+          else words[w] = word;
+        }
+      }
+    }
+    // (2) other Huffman groups (and overflowed units): encode from the input
+    bool any = refill;
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      if ((huff >> g & 1) && g != sg) any = true;
+    if (!any) continue;
     BitWriter bw[G];
+    bool emit[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
+      emit[g] = (huff >> g & 1) && (g != sg || refill);
       bw[g].words = reinterpret_cast<uint32_t*>(out + P + S.off[g] + S.hsz[g]);
-      const uint32_t st = (huff >> g & 1) ? S.part[g][t * R + k] : 0u;
+      const uint32_t st = emit[g] ? S.part[g][ui] : 0u;
       bw[g].acc = 0;
       bw[g].nacc = st & 31;
       bw[g].wi = st >> 5;
@@ -721,44 +824,34 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, const uint32_t
       bw[g].capw = S.capw[g];
     }
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
-    constexpr int U = 2;  // vectors in flight per thread
-    for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
-      uint4 a[U];
+    for (uint64_t i = (uint64_t)k * per; i < i1; i++) {
+      const uint64_t v = t + i * T;
+      if (v >= nvec) break;
+      uint32_t g4[4][4];
+      split_vec(DT, load_vec(src, base, v, nb), g4);
+      const bool full = (v + 1) * V <= m;
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const uint64_t v = t + (i0 + u) * T;
-        a[u] = (i0 + u < i1 && v < nvec) ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
-      }
+      for (int g = 0; g < G; g++) {
+        if (!emit[g]) continue;
+        if (full) {
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const uint64_t v = t + (i0 + u) * T;
-        if (i0 + u >= i1 || v >= nvec) break;
-        uint32_t g4[4][4];
-        split_vec(DT, a[u], g4);
-        const bool full = (v + 1) * V <= m;
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-          if (!(huff >> g & 1)) continue;
-          if (full) {
-#pragma unroll
-            for (int q = 0; q < V / 4; q++) {
-              uint32_t len;
-              const uint64_t x = join4(S.codes[g], g4[g][q], len);
-              bw[g].put64(x, len);
-            }
-          } else {
-            const int valid = (int)(m - v * V);
-            for (int q = 0; q < valid; q++) {
-              const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
-              bw[g].put(cl & 0xFFFFu, cl >> 16);
-            }
+          for (int q = 0; q < V / 4; q++) {
+            uint32_t len;
+            const uint64_t x = join4(S.codes[g], g4[g][q], len);
+            bw[g].put64(x, len);
+          }
+        } else {
+          const int valid = (int)(m - v * V);
+          for (int q = 0; q < valid; q++) {
+            const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
+            bw[g].put(cl & 0xFFFFu, cl >> 16);
           }
         }
       }
     }
 #pragma unroll
     for (int g = 0; g < G; g++)
-      if (huff >> g & 1) bw[g].flush();
+      if (emit[g]) bw[g].flush();
   }
 }
 
@@ -768,6 +861,7 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
        const uint8_t* __restrict__ tabs, const GcMeta* __restrict__ meta,
        const uint64_t* __restrict__ offs, const uint64_t* __restrict__ totals) {
   __shared__ PackSmem S;
+  extern __shared__ uint32_t slots[];  // kPackSlotWords
   const int tid = threadIdx.x;
   if (blockIdx.x >= nchunks_total) {  // header CTAs
     const int j = (int)(blockIdx.x - nchunks_total);
@@ -798,14 +892,14 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
   if (totals[j] > J.out_capacity) return;
   const uint64_t c = chunk - J.chunk_begin;
   if (DTS >= 0) {
-    pack_chunk<(DTS < 0 ? 0 : DTS)>(J, c, S, codes, tabs, meta, offs);
+    pack_chunk<(DTS < 0 ? 0 : DTS)>(J, c, S, slots, codes, tabs, meta, offs);
     return;
   }
   switch (J.dtype) {
-    case ZIPNN_BF16: pack_chunk<ZIPNN_BF16>(J, c, S, codes, tabs, meta, offs); break;
-    case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, codes, tabs, meta, offs); break;
-    case ZIPNN_FP32: pack_chunk<ZIPNN_FP32>(J, c, S, codes, tabs, meta, offs); break;
-    default: pack_chunk<ZIPNN_U8>(J, c, S, codes, tabs, meta, offs); break;
+    case ZIPNN_BF16: pack_chunk<ZIPNN_BF16>(J, c, S, slots, codes, tabs, meta, offs); break;
+    case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, slots, codes, tabs, meta, offs); break;
+    case ZIPNN_FP32: pack_chunk<ZIPNN_FP32>(J, c, S, slots, codes, tabs, meta, offs); break;
+    default: pack_chunk<ZIPNN_U8>(J, c, S, slots, codes, tabs, meta, offs); break;
   }
 }
 
@@ -887,7 +981,10 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
   if (h_one) uniform_dtype = h_one->dtype;
   auto kp = pick(uniform_dtype, k_pack<ZIPNN_BF16>, k_pack<ZIPNN_FP16>, k_pack<ZIPNN_FP32>,
                  k_pack<ZIPNN_U8>, k_pack<-1>);
-  kp<<<(unsigned)(nchunks_total + njobs), kPackThreads, 0, st>>>(r, nchunks_total, s.codes, s.tabs,
+  const int ps = (int)(kPackSlotWords * 4);
+  cudaError_t ea = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  if (ea != cudaSuccess) return ea;
+  kp<<<(unsigned)(nchunks_total + njobs), kPackThreads, ps, st>>>(r, nchunks_total, s.codes, s.tabs,
                                                                 s.meta, s.offs, s.totals);
   return cudaGetLastError();
 }
