@@ -233,10 +233,12 @@ struct Staging {
   uint64_t limit_ns;   // wait limit
 };
 
-// Decode loop of one chunk: thread t owns sub-stream t; each step decodes one
-// 16-byte vector (V symbols per Huffman group, V/2 pair lookups each), merges
-// it with the raw / constant groups and stores it.
-template <int DT, int W, class BR, bool STAGED>
+// Decode loop of one chunk.  Each thread owns NS sub-streams (t, t + nthr,
+// ...) and advances them in lockstep, one 16-byte vector each per step (V
+// symbols per Huffman group = V/2 pair lookups, independent across the NS
+// sub-streams, which gives the scheduler instruction-level parallelism); each
+// vector is merged with the raw / constant groups and stored.
+template <int DT, int W, class BR, bool STAGED, int NS>
 __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
                                             uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
@@ -265,46 +267,69 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
     lut[g] = reinterpret_cast<const uint32_t*>(S.lut_ptr[g]);
   }
   uint32_t bad = 0;
-  for (uint32_t t = tid; t < T; t += nthr) {
-    BR br[G];
+  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
+    BR br[NS][G];
+    uint32_t tt[NS];
+    bool act[NS];
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-      if (mode[g] != kHuff) continue;
-      uint32_t start = 0;
-      if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
-                            : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
-      if (start > nwords[g] * 32u) {
-        bad = 1;
-        start = nwords[g] * 32u;
+    for (int j = 0; j < NS; j++) {
+      tt[j] = t0 + j * nthr;
+      act[j] = tt[j] < T;
+      const uint32_t t = act[j] ? tt[j] : 0u;
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (mode[g] != kHuff) continue;
+        uint32_t start = 0;
+        if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
+                              : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
+        if (start > nwords[g] * 32u) {
+          bad = 1;
+          start = nwords[g] * 32u;
+        }
+        br[j][g].init(reinterpret_cast<const uint32_t*>(pay[g] + bsoff[g]), nwords[g], start);
       }
-      br[g].init(reinterpret_cast<const uint32_t*>(pay[g] + bsoff[g]), nwords[g], start);
     }
     // raw group bytes, prefetched one vector ahead
-    uint32_t rawn[G][4] = {};
-    auto load_raw = [&](uint32_t v) {
+    uint32_t rawn[NS][G][4] = {};
+    auto load_raw = [&](int j, uint32_t v) {
 #pragma unroll
       for (int g = 0; g < G; g++) {
         if (mode[g] != kRaw || v >= nvec) continue;
         const uint8_t* p = rawp[g] + (size_t)v * V;
         if (V == 8) {
           const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
-          rawn[g][0] = x.x; rawn[g][1] = x.y;
+          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y;
         } else if (V == 4) {
-          rawn[g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+          rawn[j][g][0] = __ldg(reinterpret_cast<const uint32_t*>(p));
         } else {
           const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
-          rawn[g][0] = x.x; rawn[g][1] = x.y; rawn[g][2] = x.z; rawn[g][3] = x.w;
+          rawn[j][g][0] = x.x; rawn[j][g][1] = x.y; rawn[j][g][2] = x.z; rawn[j][g][3] = x.w;
         }
       }
     };
-    load_raw(t);
-    for (uint32_t v = t; v < nvec; v += T) {
-      uint32_t gw[G][4];
 #pragma unroll
-      for (int g = 0; g < G; g++)
+    for (int j = 0; j < NS; j++)
+      if (act[j]) load_raw(j, tt[j]);
+    for (uint32_t ks = 0;; ks++) {
+      uint32_t vv[NS];
+      bool live[NS];
+      bool any = false;
 #pragma unroll
-        for (int k = 0; k < 4; k++) gw[g][k] = rawn[g][k];
-      load_raw(v + T);
+      for (int j = 0; j < NS; j++) {
+        vv[j] = tt[j] + ks * T;
+        live[j] = act[j] && vv[j] < nvec;
+        any |= live[j];
+      }
+      if (!any) break;
+      uint32_t gw[NS][G][4];
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+#pragma unroll
+        for (int g = 0; g < G; g++)
+#pragma unroll
+          for (int k = 0; k < 4; k++) gw[j][g][k] = rawn[j][g][k];
+        if (live[j]) load_raw(j, vv[j] + T);
+      }
 #pragma unroll
       for (int g = 0; g < G; g++) {
         if (mode[g] == kHuff) {
@@ -312,35 +337,47 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
           const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
 #pragma unroll
           for (int q = 0; q < V / 4; q++) {
-            const uint32_t a = two_symbols<W>(br[g], lut[g], tb, syms, bad);
-            const uint32_t b = two_symbols<W>(br[g], lut[g], tb, syms, bad);
-            gw[g][q] = a | (b << 16);
+            uint32_t a[NS], b[NS];
+#pragma unroll
+            for (int j = 0; j < NS; j++) a[j] = two_symbols<W>(br[j][g], lut[g], tb, syms, bad);
+#pragma unroll
+            for (int j = 0; j < NS; j++) b[j] = two_symbols<W>(br[j][g], lut[g], tb, syms, bad);
+#pragma unroll
+            for (int j = 0; j < NS; j++) gw[j][g][q] = a[j] | (b[j] << 16);
           }
         } else if (mode[g] != kRaw) {
-          gw[g][0] = cval[g]; gw[g][1] = cval[g]; gw[g][2] = cval[g]; gw[g][3] = cval[g];
+#pragma unroll
+          for (int j = 0; j < NS; j++) {
+            gw[j][g][0] = cval[g]; gw[j][g][1] = cval[g]; gw[j][g][2] = cval[g]; gw[j][g][3] = cval[g];
+          }
         }
       }
-      uint32_t x[4];
-      if (DT == ZIPNN_FP32) {
-        uint32_t g4[4] = {gw[0][0], gw[1 % G][0], gw[2 % G][0], gw[3 % G][0]};
-        merge32(g4, x);
-      } else if (DT == ZIPNN_U8) {
-        x[0] = gw[0][0]; x[1] = gw[0][1]; x[2] = gw[0][2]; x[3] = gw[0][3];
-      } else {
-        merge16(gw[0][0], gw[1 % G][0], x[0], x[1]);
-        merge16(gw[0][1], gw[1 % G][1], x[2], x[3]);
-      }
-      if ((v + 1) * 16 <= nb) {
-        if (base) {
-          const uint4 bb = __ldg(reinterpret_cast<const uint4*>(base) + v);
-          x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+        if (!live[j]) continue;
+        const uint32_t v = vv[j];
+        uint32_t x[4];
+        if (DT == ZIPNN_FP32) {
+          uint32_t g4[4] = {gw[j][0][0], gw[j][1 % G][0], gw[j][2 % G][0], gw[j][3 % G][0]};
+          merge32(g4, x);
+        } else if (DT == ZIPNN_U8) {
+          x[0] = gw[j][0][0]; x[1] = gw[j][0][1]; x[2] = gw[j][0][2]; x[3] = gw[j][0][3];
+        } else {
+          merge16(gw[j][0][0], gw[j][1 % G][0], x[0], x[1]);
+          merge16(gw[j][0][1], gw[j][1 % G][1], x[2], x[3]);
         }
-        reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
-      } else {
-        for (uint32_t k = v * 16; k < nb; k++) {
-          uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
-          if (base) byte ^= base[k];
-          dst[k] = (uint8_t)byte;
+        if ((v + 1) * 16 <= nb) {
+          if (base) {
+            const uint4 bb = __ldg(reinterpret_cast<const uint4*>(base) + v);
+            x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
+          }
+          reinterpret_cast<uint4*>(dst)[v] = make_uint4(x[0], x[1], x[2], x[3]);
+        } else {
+          for (uint32_t k = v * 16; k < nb; k++) {
+            uint32_t byte = (x[(k - v * 16) >> 2] >> (8 * (k & 3))) & 0xFFu;
+            if (base) byte ^= base[k];
+            dst[k] = (uint8_t)byte;
+          }
         }
       }
     }
@@ -518,9 +555,13 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     if (tid == 0) atomicOr(err, 1u);
     return true;
   }
-  // 4. decode + merge
-  if (CI.stage_bytes) decode_loop<DT, W, SmemBitReader, true>(J, c, S, stg, err);
-  else decode_loop<DT, W, BitReader, false>(J, c, S, stg, err);
+  // 4. decode + merge (two sub-streams per thread when the chunk has enough)
+  if (CI.stage_bytes) {
+    if (T >= 2u * nthr) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, stg, err);
+    else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, stg, err);
+  } else {
+    decode_loop<DT, W, BitReader, false, 1>(J, c, S, stg, err);
+  }
   return true;
 }
 

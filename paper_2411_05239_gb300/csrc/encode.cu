@@ -281,21 +281,28 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
     }
   }
 
-  // --- sort the leaves by key = count << 8 | (255 - symbol) (ascending)
-  for (int k = 0; k < 8; k++) {
-    int s = lane + 32 * k;
-    S.keys[s] = cnt[k] ? ((cnt[k] << 8) | (uint32_t)(255 - s)) : 0u;
+  // --- sort the leaves by key = count << 8 | (255 - symbol) (ascending):
+  // compact the non-zero symbols (ballot prefix), then rank each key among
+  // the nz compacted keys (keys are distinct: the symbol part differs)
+  {
+    uint32_t basek = 0;
+    const uint32_t ltm = (1u << lane) - 1u;
+    for (int k = 0; k < 8; k++) {
+      const uint32_t b = __ballot_sync(0xffffffffu, cnt[k] > 0);
+      if (cnt[k]) {
+        const int s = lane + 32 * k;
+        S.keys[basek + __popc(b & ltm)] = (cnt[k] << 8) | (uint32_t)(255 - s);
+      }
+      basek += __popc(b);
+    }
   }
   __syncwarp();
-  const uint32_t nempty = 256 - nz;
-  for (int k = 0; k < 8; k++) {
-    if (!cnt[k]) continue;
-    uint32_t key = S.keys[lane + 32 * k];
+  for (uint32_t i = lane; i < nz; i += 32) {
+    const uint32_t key = S.keys[i];
     uint32_t r = 0;
-    for (int q = 0; q < 256; q++) r += (S.keys[q] < key);
-    r -= nempty;  // empty slots hold 0, smaller than every key
-    S.leafw[r] = cnt[k];
-    S.leafsym[r] = (uint8_t)(lane + 32 * k);
+    for (uint32_t q = 0; q < nz; q++) r += (S.keys[q] < key);
+    S.leafw[r] = key >> 8;
+    S.leafsym[r] = (uint8_t)(255 - (key & 0xFFu));
   }
   for (int i = lane; i < kMaxLen * 16; i += 32) (&S.leafbits[0][0])[i] = 0;
   __syncwarp();
