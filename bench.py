@@ -183,12 +183,15 @@ def oracle_sample(ts: list[torch.Tensor], chunk: int, sample_bytes: int) -> np.n
     return np.concatenate(pieces)
 
 
-def time_oracle(sample: np.ndarray, chunk: int) -> dict:
+def time_oracle(sample: np.ndarray, chunk: int, dtype: int | None = None,
+                base: np.ndarray | None = None) -> dict:
+    """Oracle compress (or delta against `base`) then decompress of `sample`."""
     import oracle as O
+    dtype = O.BF16 if dtype is None else dtype
     t0 = time.perf_counter()
-    s = O.compress(sample, O.BF16, chunk)
+    s = O.compress(sample, dtype, chunk) if base is None else O.delta(sample, base, dtype, chunk)
     t1 = time.perf_counter()
-    y = O.decompress(s)
+    y = O.decompress(s, base)
     t2 = time.perf_counter()
     assert np.array_equal(y, sample)
     return {"compress_s": t1 - t0, "decompress_s": t2 - t1, "bytes": int(sample.size),
@@ -258,14 +261,16 @@ def run_gb300(args):
     # autotuned container (chunk size, lanes) and decoder (table width, CTAs/SM)
     # settings, measured on a sample of the checkpoint (embedding rows + 2 layers)
     tuned = None
-    lanes = 0
+    lanes = args.lanes
     if args.autotune:
         from paper_2411_05239_gb300 import autotune as AT
         sample = [ts[0][: 64 * 1024 * 1024]] + ts[1:1 + 2 * 9]
-        tuned = AT.tune(sample, reps=3, ctas=(0, 2, 3))
+        tuned = AT.tune(sample, reps=3, chunks=(128 << 10, 256 << 10, 512 << 10),
+                        lut_bits=(11, 12), ctas=(0, 2, 3))
         args.chunk = tuned["chunk_bytes"]
         lanes = tuned["lanes"]
         args.lut_bits = tuned["lut_bits"]
+        args.threads = tuned["threads"]
         args.ctas_per_sm = tuned["ctas_per_sm"]
         torch.cuda.synchronize()
     # compression plan (batched, graph-captured) and a first pass for the sizes
@@ -405,7 +410,7 @@ def run_gb300(args):
                                 else f"llama_bf16_checkpoint_{args.layers}l_{args.vocab}v"),
                    "tensors": len(ts),
                    "params": orig // 2, "bytes": orig, "chunk_bytes": args.chunk,
-                   "lanes": cs[0].zs.lanes, "lut_bits": args.lut_bits or 11,
+                   "lanes": cs[0].zs.lanes, "lut_bits": args.lut_bits or 12, "threads": args.threads or 256,
                    "ctas_per_sm": args.ctas_per_sm,
                    "autotuned": tuned is not None,
                    "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
@@ -463,7 +468,7 @@ def run_tensors(args):
         xs, bases = [nxt], [base]
         name = "checkpoint_delta_1.7b_bf16"
     orig = sum(x.numel() * x.element_size() for x in xs)
-    bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases)
+    bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases, lanes=args.lanes)
     bc()
     Z.sync_status()
     cs = bc.containers()
@@ -497,6 +502,19 @@ def run_tensors(args):
     dm = sorted(e[2].elapsed_time(e[3]) for e in ev)
     dmean = statistics.mean(dm)
     alg = comp + orig + (orig if bases else 0)
+    # CPU baseline: the oracle on (a prefix of) the same tensor, 1 thread
+    cpu = None
+    if args.cpu_sample_mb > 0:
+        lim = max(args.chunk, (args.cpu_sample_mb << 20) // args.chunk * args.chunk)
+        xb = xs[0].view(torch.uint8).reshape(-1)
+        samp = xb[:lim].cpu().numpy()
+        bsamp = bases[0].view(torch.uint8).reshape(-1)[:lim].cpu().numpy() if bases else None
+        r = time_oracle(samp, args.chunk, Z.dtype_code(xs[0], None), bsamp)
+        cpu = {"value": r["bytes"] / r["decompress_s"] / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle", "compress_gbs": r["bytes"] / r["compress_s"] / 1e9,
+               "sample": f"first {r['bytes'] >> 20} MiB of the tensor"
+                         + (" and its base" if bases else "")
+                         + "; oracle compress then decompress, 1 thread"}
     line = {
         "metric": METRIC, "value": orig / (dmean / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1,
         "steps": K, "warmup": args.warmup, "higher_is_better": True, "dtype": "u8",
@@ -507,6 +525,7 @@ def run_tensors(args):
         "roofline": {"kernel": "k_decode", "bound": "hbm", "achieved": alg / (dmean / 1e3) / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": alg / (dmean / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
         "impl": "gb300",
     }
     print(json.dumps(line), flush=True)
@@ -628,6 +647,7 @@ def main(argv=None):
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--lut-bits", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0, help="sub-streams per chunk (0 = default)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick chunk size, lanes, table width, CTAs/SM on a sample first")
     ap.add_argument("--e2e-steps", type=int, default=3)

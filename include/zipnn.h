@@ -81,10 +81,15 @@ typedef struct zipnn_stream {
 /* Decoder launch parameters for batched decoding.  Zero fields take defaults;
  * the values change speed only, never the decoded bytes. */
 typedef struct zipnn_tuning {
-    int32_t threads;      /* threads per CTA (multiple of 32, 0 = default) */
+    int32_t threads;      /* decoder threads per CTA: 128 or 256 (0 = 256);
+                             256 applies to batches of one dtype with W >= 11
+                             whose lane counts are all multiples of 256;
+                             otherwise, and for any other value, 128 */
     int32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid */
-    int32_t lut_bits;     /* decode table width W in bits: 10, 11 or 12 (0 = 11);
-                             codes longer than W take a slow path */
+    int32_t lut_bits;     /* decode table width W in bits: 10, 11 or 12 (0 = 12);
+                             W = 10 resolves codes longer than 10 bits through
+                             the canonical limits, W = 11 resolves 12-bit codes
+                             inside the table */
     int32_t debug_flags;  /* 0.  Bit 0 is fault injection for tests: the decoder
                              waits for 16 bytes that are never copied, so its
                              bounded wait gives up after 100 ms and the call
@@ -98,7 +103,8 @@ int zipnn_version(void);
 const char* zipnn_strerror(int status);
 
 /* Sub-streams per Huffman group-chunk used when a call takes no lanes value:
- * chunk_bytes / (element size * 1024), clamped to [1, 1024]. */
+ * chunk_bytes / (element size * 512), clamped to [1, 1024] (sub-streams of
+ * about 512 symbols; 256 lanes for BF16 / FP16 at 256 KiB). */
 uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes);
 
 /* Upper bound on the container size for nbytes of the given dtype and chunk

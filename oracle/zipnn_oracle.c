@@ -108,11 +108,11 @@ int or_elem_size(int dtype) {
 }
 int or_n_groups(int dtype) { return or_elem_size(dtype); }
 
-/* default interleave width: sub-streams of about 1024 symbols */
+/* default interleave width: sub-streams of about 512 symbols */
 uint32_t or_default_lanes(int dtype, uint32_t chunk_bytes) {
     int es = or_elem_size(dtype);
     if (es == 0) return 0;
-    uint32_t t = chunk_bytes / ((uint32_t)es * 1024u);
+    uint32_t t = chunk_bytes / ((uint32_t)es * 512u);
     if (t < 1) t = 1;
     if (t > OR_MAX_LANES) t = OR_MAX_LANES;
     return t;

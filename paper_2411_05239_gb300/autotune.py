@@ -1,9 +1,9 @@
 """Autotuner for the batched codec: chunk size, sub-stream lanes, decode table
-width and persistent-grid occupancy.
+width, decoder CTA size and persistent-grid occupancy.
 
 Chunk size (64 KiB - 1 MiB) and lanes are container parameters (chosen at
-compression time, recorded in the header); table width W (10-12 bits) and CTAs
-per SM are decoder launch parameters.  None of them changes the decoded bytes.
+compression time, recorded in the header); table width W (10-12 bits), threads
+per CTA (128 / 256) and CTAs per SM are decoder launch parameters.  None of them changes the decoded bytes.
 The tuner compresses a representative sample with each candidate chunk size,
 times the graph-captured batched decode for each decoder setting, and keeps
 the fastest decode (compression speed breaks ties).  Results are cached as JSON
@@ -71,7 +71,8 @@ def _time(fn, reps: int) -> float:
 
 
 def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_BITS,
-         ctas=(0, 2, 3, 4), lane_scales=(1, 2), verbose: bool = False) -> dict:
+         ctas=(0, 2, 3, 4), lane_scales=(1, 2), threads=(128, 256),
+         verbose: bool = False) -> dict:
     """Sweep the candidates on `sample` (CUDA tensors of one dtype); returns the
     best setting with its measured decode / compress GB/s (original bytes)."""
     orig = sum(t.numel() * t.element_size() for t in sample)
@@ -87,17 +88,18 @@ def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_
         ratio = sum(c.nbytes for c in cs) / orig
         pc = Z.plan_compress(bc)
         t_comp = _time(pc.launch, reps)
-        for w in lut_bits:
-            for k in ctas:
-                pd = Z.plan_decompress(cs, outs, tune=Z.tuning(ctas_per_sm=k, lut_bits=w))
-                t_dec = _time(pd.launch, reps)
-                pd.close()
-                r = {"chunk_bytes": chunk, "lanes": lanes, "lut_bits": w, "ctas_per_sm": k,
-                     "decode_gbs": orig / t_dec / 1e9, "compress_gbs": orig / t_comp / 1e9,
-                     "ratio": ratio}
-                results.append(r)
-                if verbose:
-                    print(r, flush=True)
+        for w, nt, k in [(w, nt, k) for w in lut_bits for nt in threads for k in ctas]:
+            if nt != 128 and w < 11:
+                continue  # 256-thread CTAs exist for W >= 11 only
+            pd = Z.plan_decompress(cs, outs, tune=Z.tuning(threads=nt, ctas_per_sm=k, lut_bits=w))
+            t_dec = _time(pd.launch, reps)
+            pd.close()
+            r = {"chunk_bytes": chunk, "lanes": lanes, "lut_bits": w, "threads": nt,
+                 "ctas_per_sm": k, "decode_gbs": orig / t_dec / 1e9,
+                 "compress_gbs": orig / t_comp / 1e9, "ratio": ratio}
+            results.append(r)
+            if verbose:
+                print(r, flush=True)
         pc.close()
         del bc, cs
     Z.sync_status()

@@ -23,7 +23,7 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256);
 }  // namespace zipnn
 
 using namespace zipnn;
@@ -117,7 +117,7 @@ zipnn_status cuda_status(cudaError_t e) {
 
 uint32_t lanes_default(int dtype, size_t chunk_bytes) {
   const int es = elem_size(dtype);
-  uint64_t t = chunk_bytes / ((uint64_t)es * 1024u);
+  uint64_t t = chunk_bytes / ((uint64_t)es * 512u);
   if (t < 1) t = 1;
   if (t > ZIPNN_MAX_LANES) t = ZIPNN_MAX_LANES;
   return (uint32_t)t;
@@ -448,7 +448,7 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   Job J = decode_job(s, d_base_or_null, d_dst);
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
-                                   nullptr, st, s->dtype);
+                                   nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0);
   return cuda_status(e);
 }
 
@@ -458,12 +458,15 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   if (count < 0 || (count > 0 && (!streams || !d_dsts))) return ZIPNN_EINVAL;
   if (count == 0) return ZIPNN_OK;
   std::vector<Job> jobs((size_t)count);
-  uint64_t chunk = 0;
+  uint64_t chunk = 0, max_chunk = 0;
   int max_groups = 1;
   int uniform = streams[0].dtype;
+  bool lanes256 = true;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
     if (s->dtype != uniform) uniform = -1;
+    if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
+    if (s->lanes % 256) lanes256 = false;
     zipnn_status rc = check_stream(s);
     if (rc) return rc;
     const void* base = d_bases ? d_bases[i] : nullptr;
@@ -487,7 +490,7 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
-                         uniform);
+                         uniform, max_chunk, lanes256);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

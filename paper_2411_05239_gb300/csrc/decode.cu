@@ -12,14 +12,17 @@
 //      (cp.async.bulk, completion on an mbarrier; payloads are 16-B aligned and
 //      padded by the format), overlapped with step 3,
 //   3. builds, per Huffman group, a 2^W-entry table (W = 10..12, chosen at
-//      launch): the entry for a W-bit window holds up to three whole codes
-//      that fit in it (symbols and bits consumed); a window whose first code
-//      is longer than W bits takes a slow path through the canonical limits,
+//      launch): the entry for a W-bit window holds its first two codes when
+//      both fit in it (symbols and bits consumed), else its first code; with
+//      W = 11 a 12-bit first code is resolved in the entry by its last bit,
+//      with W = 10 longer first codes go through the canonical limits,
 //   4. decodes: thread t owns interleaved sub-stream t, i.e. the vectors
 //      v = t, t+T, ... of the chunk, so each warp step touches 32 consecutive
-//      16-byte vectors: raw-group loads (prefetched one vector ahead) and the
+//      16-byte vectors: raw-group loads (two vectors ahead of use) and the
 //      16-B output stores are fully coalesced; the inverse permutation and the
-//      XOR with a delta base happen in registers.
+//      XOR with a delta base happen in registers.  Chunks laid out as
+//      "exponent Huffman, every other group raw" (nearly every chunk of a
+//      model) take a specialised loop without per-group mode tests.
 // The decoder is total: symbol counts are fixed by the map, bit reads past a
 // payload return zero bits, invalid codes and bad map entries set the error
 // word, and every loop is bounded; the wait for a bulk copy gives up after 2 s
@@ -34,12 +37,28 @@ namespace zipnn {
 
 namespace {
 
-constexpr int kDecThreads = 128;
-constexpr uint32_t kStageBytes = 45056;  // shared-memory staging for Huffman payloads
+constexpr int kDecThreads = 128;  // CTA size of mixed-dtype and W = 10 launches; else 256
+// Shared-memory staging for Huffman payloads: sized for the largest chunk of
+// the launch (an exponent payload of a 16-bit chunk is about a sixth of the
+// chunk), at most kStageBytes; payloads that do not fit are read from global
+// memory instead.
+constexpr uint32_t kStageBytes = 45056;
+constexpr uint32_t kStageMin = 4096;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+// Loads and stores through 32-bit shared-window addresses, so that table
+// lookups compile to shared-memory instructions even where the table's
+// location is only known at run time.
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t saddr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -152,18 +171,19 @@ struct BitReader {
   }
 };
 
-// Reader over a bitstream staged in shared memory (all words present; the
-// staging leaves slack after each payload for the look-ahead word).
+// Reader over a bitstream staged in shared memory.  Word reads are clamped to
+// index nwords + 1 (the staging leaves 32 bytes of slack after each payload),
+// so a corrupt stream cannot walk the reader out of the stage.
 struct SmemBitReader {
   const uint32_t* w;
-  uint32_t idx, w0, w1, pos;
+  uint32_t idx, lim, w0, w1, pos;
   __device__ __forceinline__ void init(const uint32_t* words, uint32_t nwords, uint32_t start) {
-    (void)nwords;
     w = words;
+    lim = nwords + 1;
     idx = start >> 5;
     pos = start & 31;
-    w0 = w[idx];
-    w1 = w[idx + 1];
+    w0 = w[min(idx, lim)];
+    w1 = w[min(idx + 1, lim)];
     idx += 2;
   }
   __device__ __forceinline__ uint32_t peek32() const { return __funnelshift_l(w1, w0, pos); }
@@ -172,7 +192,8 @@ struct SmemBitReader {
     if (pos >= 32) {
       pos -= 32;
       w0 = w1;
-      w1 = w[idx++];
+      w1 = w[min(idx, lim)];
+      idx++;
     }
   }
 };
@@ -182,13 +203,25 @@ __device__ __forceinline__ uint32_t rd_u32(const uint8_t* p) {
 }
 
 // Pair tables.  The entry for a W-bit window w describes the codes at its
-// start:  bits 0-7 first symbol, 8-15 second symbol, 16-19 length l1 of the
-// first code (0: longer than W or invalid -> slow path), 20-24 length of both
-// codes, bit 25 set when both codes lie wholly inside the window.
-constexpr uint32_t kPair = 1u << 25;
+// start:
+//   bits 0-7    first symbol (or, for a long first code, its symbol when the
+//               window's next bit is 0)
+//   bits 8-15   second symbol (pair) or the long code's symbol for next bit 1
+//   bits 16-19  length l1 of the first code (0: invalid window, or, for W = 10,
+//               a first code longer than the window -> slow path)
+//   bit 20      pair: both codes lie wholly inside the window
+//   bit 21      long: the first code has W + 1 bits (W = 11 only)
+//   bits 22-23  long code invalid for next bit 0 / 1
+//   bits 27-31  bits consumed by the entry (pair: l1 + l2)
+// Symbols are stored rotated right by one bit when the chunk takes the fast
+// loop (the merge then needs only bit selects, see merge16r).
+constexpr uint32_t kPair = 1u << 20;
+constexpr uint32_t kLong = 1u << 21;
+constexpr uint32_t kBadLong0 = 1u << 22;
 
-// Slow path: resolve the first code of a 12-bit window with the canonical
-// limits.  Returns (symbol | length << 16); flags windows that start no code.
+// Slow path (W = 10): resolve the first code of a 12-bit window with the
+// canonical limits.  Returns (symbol | length << 16); flags windows that start
+// no code.
 __device__ __noinline__ uint32_t slow_code(const GroupTab& t, const uint8_t* syms, uint32_t win12,
                                            uint32_t& bad) {
   int l = 1;
@@ -201,32 +234,63 @@ __device__ __noinline__ uint32_t slow_code(const GroupTab& t, const uint8_t* sym
   return (uint32_t)syms[r & 255] | ((uint32_t)l << 16);
 }
 
-// One symbol from the table (first code only), with the slow path.
-template <int W, class BR>
-__device__ __forceinline__ uint32_t one_symbol(BR& br, const uint32_t* lut, const GroupTab& t,
+// First code of the 32-bit window `win` whose table entry is e:
+// (symbol | length << 16).
+template <int W>
+__device__ __forceinline__ uint32_t first_code(uint32_t e, uint32_t win, const GroupTab& t,
                                                const uint8_t* syms, uint32_t& bad) {
-  uint32_t e = lut[br.peek32() >> (32 - W)];
-  if (((e >> 16) & 15u) == 0) e = slow_code(t, syms, br.peek32() >> (32 - kMaxLen), bad);
-  br.skip((e >> 16) & 15u);
-  return e & 0xFFu;
+  if (W == 11 && (e & kLong)) {
+    const uint32_t nb = (win >> (31 - W)) & 1u;
+    bad |= (e >> (22 + nb)) & 1u;
+    return ((e >> (8 * nb)) & 0xFFu) | ((uint32_t)(W + 1) << 16);
+  }
+  const uint32_t l = (e >> 16) & 15u;
+  if (l == 0) {
+    if (W == 10) return slow_code(t, syms, win >> (32 - kMaxLen), bad);
+    bad = 1;
+    return (uint32_t)W << 16;
+  }
+  return (e & 0xFFu) | (l << 16);
 }
 
-// Two symbols (sym0 | sym1 << 8): one lookup when both codes fit in the window.
-template <int W, class BR>
-__device__ __forceinline__ uint32_t two_symbols(BR& br, const uint32_t* lut, const GroupTab& t,
-                                                const uint8_t* syms, uint32_t& bad) {
-  const uint32_t e = lut[br.peek32() >> (32 - W)];
-  if (e & kPair) {
-    br.skip((e >> 20) & 31u);
-    return e & 0xFFFFu;
+// Entry for two symbols at the window: the table entry when it is a pair,
+// otherwise the two first codes resolved one after the other (rare).  Bits
+// 0-15 hold the symbols, 27-31 the bits consumed.
+template <int W>
+__device__ __forceinline__ uint32_t pair_at(uint32_t win, uint32_t lut, const GroupTab& t,
+                                            const uint8_t* syms, uint32_t& bad) {
+  uint32_t e = lds32(lut + ((win >> (32 - W)) << 2));
+  if (!(e & kPair)) {
+    const uint32_t c0 = first_code<W>(e, win, t, syms, bad);
+    const uint32_t l0 = c0 >> 16;
+    const uint32_t win2 = win << l0;
+    const uint32_t c1 = first_code<W>(lds32(lut + ((win2 >> (32 - W)) << 2)), win2, t, syms, bad);
+    e = (c0 & 0xFFu) | ((c1 & 0xFFu) << 8) | ((l0 + (c1 >> 16)) << 27);
   }
-  const uint32_t s0 = one_symbol<W>(br, lut, t, syms, bad);
-  const uint32_t s1 = one_symbol<W>(br, lut, t, syms, bad);
-  return s0 | (s1 << 8);
+  return e;
+}
+
+// Two symbols (sym0 | sym1 << 8).
+template <int W, class BR>
+__device__ __forceinline__ uint32_t two_symbols(BR& br, uint32_t lut, const GroupTab& t,
+                                                const uint8_t* syms, uint32_t& bad) {
+  const uint32_t e = pair_at<W>(br.peek32(), lut, t, syms, bad);
+  br.skip(e >> 27);
+  return e & 0xFFFFu;
+}
+
+// merge16 / merge32 for exponent bytes stored rotated right by one bit
+// (e' = e >> 1 | e << 7 per byte): each output byte is a bit select.
+__device__ __forceinline__ void merge16r(uint32_t er, uint32_t r, uint32_t& w0, uint32_t& w1) {
+  const uint32_t hi = (r & 0x80808080u) | (er & 0x7F7F7F7Fu);
+  const uint32_t lo = (er & 0x80808080u) | (r & 0x7F7F7F7Fu);
+  w0 = __byte_perm(lo, hi, 0x5140);
+  w1 = __byte_perm(lo, hi, 0x7362);
 }
 
 struct Staging {
   uint8_t* base;       // shared-memory stage
+  uint32_t cap;        // its size in bytes
   uint64_t* bar;       // its mbarrier
   uint32_t parity;     // phase to wait for next
   uint32_t extra_tx;   // fault injection: bytes expected but never sent (0 normally)
@@ -254,7 +318,7 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
   uint32_t mode[G], cval[G], nwords[G], offs[G], bsoff[G];
   const uint8_t* rawp[G];
   const uint8_t* pay[G];
-  const uint32_t* lut[G];
+  uint32_t lut[G];  // shared-window addresses of the pair tables
 #pragma unroll
   for (int g = 0; g < G; g++) {
     mode[g] = CI.mode[g];
@@ -264,7 +328,7 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
     pay[g] = STAGED ? stg.base + CI.staged[g] : cont + CI.payload[g];
     offs[g] = (uint32_t)CI.offs[g];
     bsoff[g] = (uint32_t)CI.bs[g];
-    lut[g] = reinterpret_cast<const uint32_t*>(S.lut_ptr[g]);
+    lut[g] = smem_u32(S.lut_ptr[g]);
   }
   uint32_t bad = 0;
   for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
@@ -385,6 +449,158 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
   if (bad) atomicOr(err, 1u);
 }
 
+// merge32 for a rotated exponent byte (see merge16r).
+__device__ __forceinline__ void merge32r(uint32_t er, uint32_t g1, uint32_t g2, uint32_t g3,
+                                         uint32_t x[4]) {
+  const uint32_t b3 = (g1 & 0x80808080u) | (er & 0x7F7F7F7Fu);
+  const uint32_t b2 = (er & 0x80808080u) | (g1 & 0x7F7F7F7Fu);
+  const uint32_t lo01 = __byte_perm(g3, g2, 0x5140), hi01 = __byte_perm(b2, b3, 0x5140);
+  const uint32_t lo23 = __byte_perm(g3, g2, 0x7362), hi23 = __byte_perm(b2, b3, 0x7362);
+  x[0] = __byte_perm(lo01, hi01, 0x5410);
+  x[1] = __byte_perm(lo01, hi01, 0x7632);
+  x[2] = __byte_perm(lo23, hi23, 0x5410);
+  x[3] = __byte_perm(lo23, hi23, 0x7632);
+}
+
+// Words of the groups 1..G-1 of one vector (V bytes per group): loaded from
+// the raw payload when bit g of rawm is set, else the group's constant byte
+// (ZERO / CONST) replicated in cw[g].
+template <int DT>
+__device__ __forceinline__ void load_raw_vec(const uint8_t* const* rawp, uint32_t rawm,
+                                             const uint32_t* cw, uint32_t v, uint32_t* rw) {
+  if constexpr (DT == ZIPNN_FP32) {
+#pragma unroll
+    for (int g = 1; g < 4; g++)
+      rw[g - 1] = (rawm >> g & 1u) ? __ldg(reinterpret_cast<const uint32_t*>(rawp[g]) + v) : cw[g];
+  } else if constexpr (DT != ZIPNN_U8) {
+    if (rawm & 2u) {
+      const uint2 x = __ldg(reinterpret_cast<const uint2*>(rawp[1]) + v);
+      rw[0] = x.x;
+      rw[1] = x.y;
+    } else {
+      rw[0] = cw[1];
+      rw[1] = cw[1];
+    }
+  }
+}
+
+// Fast loop for the dominant chunk layout: group 0 Huffman and staged, every
+// other group raw, zero or constant, a whole chunk whose nvec vectors split evenly over the T
+// sub-streams, and T a multiple of NS * nthr.  Thread t decodes sub-streams
+// t, t + nthr, ... (NS in lockstep, interleaved for instruction-level
+// parallelism); every vector is 16 B of output: V/2 pair lookups, one raw
+// load per raw group (prefetched two vectors ahead), bit-select merge with the
+// rotated exponent symbols, a 16-B store.  No mode tests and no tails inside
+// the loop.  Each sub-stream must end exactly where the next one starts (the
+// last one within the bitstream); a mismatch flags the chunk as corrupt.
+template <int DT, int W, int NS>
+__device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem& S,
+                                            const Staging& stg, uint32_t* err) {
+  constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
+  constexpr int RW = DT == ZIPNN_FP32 ? 3 : (DT == ZIPNN_U8 ? 1 : 2);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const ChunkInfo& CI = S.ci;
+  const uint64_t off0 = c * J.chunk_bytes;
+  const uint32_t T = J.lanes;
+  const uint32_t nper = (J.chunk_bytes / 16u) / T;
+  const uint8_t* pay = stg.base + CI.staged[0];
+  const uint32_t* starts = reinterpret_cast<const uint32_t*>(pay + (uint32_t)CI.offs[0]);
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(pay + (uint32_t)CI.bs[0]);
+  const uint32_t nwords = CI.nwords[0], nbits = nwords * 32u, wlim = nwords + 1u;
+  const uint32_t lut = smem_u32(S.lut_ptr[0]);
+  const GroupTab& tb = S.tab[0];
+  const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+  const uint8_t* rawp[G];
+  uint32_t cw[G], rawm = 0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    rawp[g] = J.src + CI.payload[g];
+    cw[g] = CI.value[g] * 0x01010101u;  // ZERO groups carry value 0
+    if (CI.mode[g] == kRaw) rawm |= 1u << g;
+  }
+  uint4* dst = reinterpret_cast<uint4*>(J.dst + off0);
+  const uint4* base = J.base ? reinterpret_cast<const uint4*>(J.base + off0) : nullptr;
+  uint32_t bad = 0;
+  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
+    uint32_t w0[NS], w1[NS], pos[NS], idx[NS], vt[NS];
+    uint32_t ra[NS][RW], rb[NS][RW];  // raw words of vectors k (even) and k + 1
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+      const uint32_t t = t0 + j * nthr;
+      vt[j] = t;
+      uint32_t start = t ? starts[t - 1] : 0u;
+      if (start > nbits) {
+        bad = 1;
+        start = nbits;
+      }
+      idx[j] = start >> 5;
+      pos[j] = start & 31u;
+      w0[j] = words[min(idx[j], wlim)];
+      w1[j] = words[min(idx[j] + 1u, wlim)];
+      idx[j] += 2;
+      load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
+      if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
+    }
+    // vector k of every sub-stream; rr holds its raw words and receives those
+    // of vector k + 2
+    auto vec = [&](uint32_t k, uint32_t (&rr)[NS][RW]) {
+      uint32_t ex[NS][V / 4];
+#pragma unroll
+      for (int q = 0; q < V / 4; q++) {
+        uint32_t h[2][NS];
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+#pragma unroll
+          for (int j = 0; j < NS; j++) {
+            const uint32_t e = pair_at<W>(__funnelshift_l(w1[j], w0[j], pos[j]), lut, tb, syms, bad);
+            pos[j] += e >> 27;
+            if (pos[j] >= 32u) {
+              pos[j] -= 32u;
+              w0[j] = w1[j];
+              w1[j] = words[min(idx[j], wlim)];
+              idx[j]++;
+            }
+            h[p][j] = e;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NS; j++) ex[j][q] = __byte_perm(h[0][j], h[1][j], 0x5410);
+      }
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+        const uint32_t v = vt[j] + k * T;
+        uint32_t x[4];
+        if constexpr (DT == ZIPNN_FP32) {
+          merge32r(ex[j][0], rr[j][0], rr[j][1], rr[j][2], x);
+        } else if constexpr (DT == ZIPNN_U8) {
+          x[0] = ex[j][0]; x[1] = ex[j][1]; x[2] = ex[j][2]; x[3] = ex[j][3];
+        } else {
+          merge16r(ex[j][0], rr[j][0], x[0], x[1]);
+          merge16r(ex[j][1 % (V / 4)], rr[j][1 % RW], x[2], x[3]);
+        }
+        if (k + 2 < nper) load_raw_vec<DT>(rawp, rawm, cw, v + 2 * T, rr[j]);
+        if (base) {
+          const uint4 bb = __ldg(base + v);
+          x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
+        }
+        dst[v] = make_uint4(x[0], x[1], x[2], x[3]);
+      }
+    };
+    for (uint32_t k = 0; k < nper; k += 2) {
+      vec(k, ra);
+      if (k + 1 < nper) vec(k + 1, rb);
+    }
+    // every sub-stream ends where the next begins
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+      const uint32_t end = (idx[j] - 2u) * 32u + pos[j];
+      if (vt[j] + 1u < T) bad |= end != starts[vt[j]];
+      else bad |= end > nbits;
+    }
+  }
+  if (bad) atomicOr(err, 1u);
+}
+
 // Decode one chunk of a tensor of dtype DT with W-bit pair tables.  Returns
 // false if a bulk copy never completed (the caller must stop using the stage).
 // Shared memory: one table slot (lut0) for the first Huffman group; tables of
@@ -437,7 +653,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
         pay_total += (uint32_t)align_up(CI.size[g], 16);
       }
     const uint32_t extra = nhuff > 1 ? (nhuff - 1) * kLutBytes : 0u;
-    const bool stage_payloads = nhuff && pay_total + extra + 32 <= kStageBytes;
+    const bool stage_payloads = nhuff && pay_total + extra + 32 <= stg.cap;
     uint32_t used = 0, k = 0;
     for (int g = 0; g < G; g++) {
       CI.staged[g] = 0xFFFFFFFFu;
@@ -453,6 +669,10 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     uint32_t lo = (used + 32 + 127) & ~127u;
     for (int g = 0; g < G; g++)
       if (CI.mode[g] == kHuff && S.lut_ptr[g] == nullptr) {
+        if (lo + kLutBytes > stg.cap) {  // cannot happen with the launch's sizing; fail closed
+          CI.bad = 1;
+          lo = 0;
+        }
         S.lut_ptr[g] = reinterpret_cast<uint32_t*>(stg.base + lo);
         lo += kLutBytes;
       }
@@ -504,9 +724,21 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   }
   __syncthreads();
   const bool bad_tab = CI.bad != 0;
+  // fast loop (decode_fast) when the chunk has its layout; symbols are then
+  // stored rotated in the table
+  int fast = 0;
+  if constexpr (W >= 11) {
+    bool ok = CI.mode[0] == kHuff && CI.staged[0] != 0xFFFFFFFFu && nb == J.chunk_bytes &&
+              ((uint32_t)(nb / 16) % T) == 0;
+#pragma unroll
+    for (int g = 1; g < G; g++) ok = ok && CI.mode[g] != kHuff;
+    if (ok) fast = (T % (2u * nthr) == 0) ? 2 : ((T % (uint32_t)nthr == 0) ? 1 : 0);
+  }
+  const bool rot = fast != 0 && DT != ZIPNN_U8;
   // 3c. pair tables.  For window w (W bits) the first code has length
   // l1 = 1 + #{l <= W : lim_W[l] <= w}; the second code is found the same way
-  // in the remaining W - l1 bits (zero-filled), and kept only if it fits.
+  // in the remaining W - l1 bits (zero-filled), and kept only if it fits.  With
+  // W = 11 a first code of 12 bits is resolved in the entry by its last bit.
   if (!bad_tab) {
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -516,7 +748,11 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
       uint32_t limw[W + 1];
 #pragma unroll
       for (int l = 1; l <= W; l++) limw[l] = t.lim[l] >> (kMaxLen - W);
-      uint32_t* L = S.lut_ptr[g];
+      auto sym = [&](uint32_t r) -> uint32_t {
+        const uint32_t v = syms[r & 255];
+        return rot ? (((v >> 1) | (v << 7)) & 0xFFu) : v;
+      };
+      const uint32_t L = smem_u32(S.lut_ptr[g]);
       for (int w = tid; w < kLut; w += nthr) {
         uint32_t l1 = 1;
 #pragma unroll
@@ -524,17 +760,28 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
         uint32_t ent = 0;
         if (l1 <= (uint32_t)W) {
           const uint32_t r1 = t.index[l1] + ((uint32_t)w >> (W - l1)) - t.first[l1];
-          ent = (uint32_t)syms[r1 & 255] | (l1 << 16);
+          ent = sym(r1) | (l1 << 16) | (l1 << 27);
           const uint32_t rest = ((uint32_t)w << l1) & (kLut - 1);
           uint32_t l2 = 1;
 #pragma unroll
           for (int q = 1; q <= W; q++) l2 += (limw[q] <= rest);
           if (l1 + l2 <= (uint32_t)W) {
             const uint32_t r2 = t.index[l2] + (rest >> (W - l2)) - t.first[l2];
-            ent |= ((uint32_t)syms[r2 & 255] << 8) | ((l1 + l2) << 20) | kPair;
+            ent = (ent & 0x07FFFFFFu) | (sym(r2) << 8) | ((l1 + l2) << 27) | kPair;
+          }
+        } else if (W == 11) {
+          // first code of 12 bits: w is its prefix, the next bit selects
+          ent = kLong | (12u << 16) | (12u << 27);
+#pragma unroll
+          for (uint32_t nb = 0; nb < 2; nb++) {
+            const uint32_t w12 = ((uint32_t)w << 1) | nb;
+            if (w12 < t.lim[kMaxLen])
+              ent |= sym(t.index[kMaxLen] + w12 - t.first[kMaxLen]) << (8 * nb);
+            else
+              ent |= kBadLong0 << nb;
           }
         }
-        L[w] = ent;
+        sts32(L + 4u * (uint32_t)w, ent);
       }
     }
   }
@@ -556,6 +803,16 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     return true;
   }
   // 4. decode + merge (two sub-streams per thread when the chunk has enough)
+  if constexpr (W >= 11) {
+    if (fast == 2) {
+      decode_fast<DT, W, 2>(J, c, S, stg, err);
+      return true;
+    }
+    if (fast == 1) {
+      decode_fast<DT, W, 1>(J, c, S, stg, err);
+      return true;
+    }
+  }
   if (CI.stage_bytes) {
     if (T >= 2u * nthr) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, stg, err);
     else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, stg, err);
@@ -566,16 +823,17 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
 }
 
 // DTS: the dtype of every job in the launch, or -1 for a mixed batch.
-template <int DTS, int W>
-__global__ void __launch_bounds__(kDecThreads)
+template <int DTS, int W, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
-         unsigned long long* __restrict__ ticket, uint32_t debug_flags) {
+         unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap) {
   extern __shared__ __align__(128) uint8_t dsm[];  // [table slot 0] | stage
   __shared__ Smem S;
   __shared__ uint64_t bar;
   uint32_t* lut0 = reinterpret_cast<uint32_t*>(dsm);
   Staging stg;
   stg.base = dsm + (4u << W);
+  stg.cap = stage_cap;
   stg.bar = &bar;
   stg.parity = 0;
   // debug flag 1 (tests only): expect 16 bytes more than the bulk copies send,
@@ -615,47 +873,76 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   }
 }
 
-using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, uint32_t);
+using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, uint32_t,
+                             uint32_t);
 
-template <int W>
+template <int W, int NT>
 DecodeKernel pick_kernel(int dt) {
   switch (dt) {
-    case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W>;
-    case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W>;
-    case ZIPNN_FP32: return k_decode<ZIPNN_FP32, W>;
-    case ZIPNN_U8: return k_decode<ZIPNN_U8, W>;
-    default: return k_decode<-1, W>;
+    case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W, NT>;
+    case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W, NT>;
+    case ZIPNN_FP32: return k_decode<ZIPNN_FP32, W, NT>;
+    case ZIPNN_U8: return k_decode<ZIPNN_U8, W, NT>;
+    default: return k_decode<-1, W, kDecThreads>;  // mixed batches: 128 threads
   }
 }
 
 }  // namespace
 
-int decode_smem_bytes(int max_groups, int w) {
-  (void)max_groups;  // further groups' tables live in the stage
-  return (4 << w) + (int)kStageBytes;
+// Stage size: room for the payloads of the largest chunk (capped), and always
+// for the tables of every Huffman group after the first.
+uint32_t decode_stage_bytes(uint64_t max_chunk, int max_groups, int w) {
+  const uint64_t want = (max_chunk * 11 / 64 + 1024 + 127) & ~127ull;
+  uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > kStageBytes ? kStageBytes : want));
+  const uint32_t tabs = (uint32_t)(max_groups - 1) * (4u << w) + 256u;
+  return st > tabs ? st : tabs;
+}
+
+// Dynamic shared memory of one decode CTA: one table slot + the stage.
+int decode_smem_bytes(int w, uint64_t max_chunk, int max_groups) {
+  return (4 << w) + (int)decode_stage_bytes(max_chunk, max_groups, w);
 }
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype) {
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256) {
   if (nchunks_total == 0) return cudaSuccess;
   JobRef r;
   r.table = h_one ? nullptr : d_jobs;
   if (h_one) r.one = *h_one;
   else memset(&r.one, 0, sizeof(Job));
   r.n = njobs;
-  if (h_one) uniform_dtype = h_one->dtype;
-  int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 11;
+  if (h_one) {
+    uniform_dtype = h_one->dtype;
+    max_chunk = h_one->chunk_bytes;
+    lanes256 = h_one->lanes % 256 == 0;
+  }
+  int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 12;
   if (w < 10) w = 10;
   if (w > 12) w = 12;
-  DecodeKernel kern = w == 10 ? pick_kernel<10>(uniform_dtype)
-                      : (w == 11 ? pick_kernel<11>(uniform_dtype) : pick_kernel<12>(uniform_dtype));
-  const int threads = kDecThreads;
+  // CTA size: 256 threads (default) for single-dtype launches with W >= 11
+  // whose lane counts are multiples of 256 (one or two sub-streams per
+  // thread in the fast loop), else 128
+  const int want = (tuning && tuning->threads) ? tuning->threads : 256;
+  const int threads =
+      (want == 256 && w >= 11 && uniform_dtype >= 0 && lanes256) ? 256 : kDecThreads;
+  DecodeKernel kern = w == 10    ? pick_kernel<10, kDecThreads>(uniform_dtype)
+                      : w == 11  ? (threads == 256 ? pick_kernel<11, 256>(uniform_dtype)
+                                                   : pick_kernel<11, kDecThreads>(uniform_dtype))
+                                 : (threads == 256 ? pick_kernel<12, 256>(uniform_dtype)
+                                                   : pick_kernel<12, kDecThreads>(uniform_dtype));
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
-  const int smem = decode_smem_bytes(max_groups, w);
+  if (max_groups < 1 || max_groups > 4) max_groups = 4;
+  const uint32_t stage = decode_stage_bytes(max_chunk, max_groups, w);
+  const int smem = decode_smem_bytes(w, max_chunk, max_groups);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  // all of the unified L1 / shared array as shared memory, so the CTAs per
+  // SM that the occupancy query reports are the ones that become resident
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -671,7 +958,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     if (e != cudaSuccess) return e;
   }
   const uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
-  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, dbg);
+  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, dbg, stage);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,6 @@ namespace zipnn {
 namespace {
 
 constexpr int kHistThreads = 256;
-constexpr int kHistWarps = kHistThreads / 32;
 constexpr int kBuildWarps = 4;
 
 struct JobRef {
@@ -63,11 +62,12 @@ __device__ __forceinline__ uint4 load_vec(const uint8_t* src, const uint8_t* bas
       uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
       a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
     }
-  } else {
+  } else {  // ragged last vector (static indices: the words stay in registers)
     uint32_t w[4] = {0, 0, 0, 0};
-    for (uint64_t k = v * 16; k < nb; k++) {
-      uint32_t byte = src[k] ^ (base ? base[k] : 0u);
-      w[(k - v * 16) >> 2] |= byte << (8 * (k & 3));
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const uint64_t k = v * 16 + i;
+      if (k < nb) w[i >> 2] |= (uint32_t)(src[k] ^ (base ? base[k] : 0u)) << (8 * (i & 3));
     }
     a = make_uint4(w[0], w[1], w[2], w[3]);
   }
@@ -89,30 +89,26 @@ __device__ __forceinline__ void split_vec(int dtype, uint4 a, uint32_t out[4][4]
 }
 
 // ---------------------------------------------------------------------------
-// k_hist: shared-memory atomics into per-warp histograms.  The exponent group
-// is concentrated on a few values, so its atomics collide on the same address:
-// it gets 4 copies per warp (lanes 8q..8q+7 use copy q), spaced 257 words apart
-// so equal symbols of different copies fall in different banks.
-
-constexpr int kECopies = 4;
-constexpr int kEStride = 257;
+// k_hist: shared-memory atomics into lane-indexed histograms.  Group g's
+// counter for bin b and lane l sits at word (g * 256 + b) * 32 + l, shared by
+// all warps of the CTA: the 32 lanes of one atomic instruction always address
+// 32 different banks (one wavefront, whatever the symbols), which removes the
+// bank conflicts that bound a plain per-warp histogram.
 
 template <int DT>
 __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist) {
   constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
   constexpr int V = 16 / (DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2));
   constexpr int ES = 16 / V;
-  constexpr int WARP_WORDS = kECopies * kEStride + (G - 1) * 256;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint64_t off = c * J.chunk_bytes;
   const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off);
   const uint8_t* src = J.src + off;
   const uint8_t* base = J.base ? J.base + off : nullptr;
 
-  for (int i = tid; i < kHistWarps * WARP_WORDS; i += kHistThreads) sh[i] = 0;
+  for (int i = tid; i < G * 256 * 32; i += kHistThreads) sh[i] = 0;
   __syncthreads();
-  uint32_t* he = sh + warp * WARP_WORDS + (lane >> 3) * kEStride;
-  uint32_t* hr = sh + warp * WARP_WORDS + kECopies * kEStride;
+  uint32_t* hl = sh + lane;
   const uint64_t nvec = (nb + 15) / 16;
   const uint64_t m = nb / ES;
   constexpr int U = 4;  // vectors in flight per thread
@@ -132,31 +128,28 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
       const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
       if (valid == V) {
 #pragma unroll
-        for (int k = 0; k < V; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
-#pragma unroll
-        for (int gg = 1; gg < G; gg++)
+        for (int gg = 0; gg < G; gg++)
 #pragma unroll
           for (int k = 0; k < V; k++)
-            atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+            atomicAdd(&hl[(gg * 256 + __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3))) * 32], 1u);
       } else {
-        for (int k = 0; k < valid; k++) atomicAdd(&he[(g[0][k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
-        for (int gg = 1; gg < G; gg++)
-          for (int k = 0; k < valid; k++)
-            atomicAdd(&hr[(gg - 1) * 256 + ((g[gg][k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
+#pragma unroll
+        for (int gg = 0; gg < G; gg++)
+#pragma unroll
+          for (int k = 0; k < V; k++)
+            if (k < valid)
+              atomicAdd(&hl[(gg * 256 + __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3))) * 32], 1u);
       }
     }
   }
   __syncthreads();
-  for (int b = tid; b < 256; b += kHistThreads) {
-    uint32_t s0 = 0;
-    for (int w = 0; w < kHistWarps; w++)
-      for (int q = 0; q < kECopies; q++) s0 += sh[w * WARP_WORDS + q * kEStride + b];
-    hist[(J.gc_begin + c * G) * 256 + b] = s0;
-    for (int gg = 1; gg < G; gg++) {
-      uint32_t s = 0;
-      for (int w = 0; w < kHistWarps; w++) s += sh[w * WARP_WORDS + kECopies * kEStride + (gg - 1) * 256 + b];
-      hist[(J.gc_begin + c * G + gg) * 256 + b] = s;
-    }
+  // bin totals: thread b sums the 32 lane counters of bin b (rotated start so
+  // the 32 threads of a warp read 32 different banks)
+  for (int b = tid; b < G * 256; b += kHistThreads) {
+    uint32_t s = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) s += sh[b * 32 + ((i + b) & 31)];
+    hist[(J.gc_begin + c * G + b / 256) * 256 + (b & 255)] = s;
   }
 }
 
@@ -179,9 +172,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __re
   }
 }
 
-static int hist_smem_bytes(int max_groups) {
-  return kHistWarps * (kECopies * kEStride + (max_groups - 1) * 256) * 4;
-}
+static int hist_smem_bytes(int max_groups) { return max_groups * 256 * 32 * 4; }
 
 // ---------------------------------------------------------------------------
 // k_build: one warp per group-chunk.
@@ -622,6 +613,72 @@ __device__ __forceinline__ uint32_t len4(const uint32_t* codes, uint32_t w) {
          (codes[__byte_perm(w, 0, 0x4442)] >> 16) + (codes[__byte_perm(w, 0, 0x4443)] >> 16);
 }
 
+// Pass A for the dominant chunk layout: group 0 Huffman (slot-encoded), every
+// other group raw, zero or constant (bit g of raw set for raw groups), a whole
+// chunk whose vectors split evenly over the T sub-streams and R parts (per
+// vectors per unit).  No tails: per vector one 16-B load (two in flight), the
+// split, V/4 joined code appends into the unit's slot and one store per raw
+// group.
+template <int DT>
+__device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* base, uint32_t T,
+                                            uint32_t R, uint32_t per, uint32_t* slots,
+                                            uint32_t slot_cap, PackSmem& S, uint8_t* out,
+                                            uint64_t P, uint32_t raw) {
+  constexpr int G = PTraits<DT>::G, V = PTraits<DT>::V;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t units = T * R;
+  uint8_t* rawp[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) rawp[g] = out + P + S.off[g];
+  const uint32_t* codes0 = S.codes[0];
+  auto ld = [&](uint64_t v) -> uint4 {
+    uint4 a = __ldg(reinterpret_cast<const uint4*>(src) + v);
+    if (base) {
+      const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
+      a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+    }
+    return a;
+  };
+  for (uint32_t u = tid; u < units; u += nthr) {
+    const uint32_t t = u % T, k = u / T, ui = t * R + k;
+    SlotWriter sw;
+    sw.slot = slots + (size_t)ui * slot_cap;
+    sw.acc = 0;
+    sw.nacc = 0;
+    sw.wi = 0;
+    sw.cap = slot_cap;
+    sw.bits = 0;
+    uint64_t v = t + (uint64_t)k * per * T;
+    uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
+    auto one = [&](uint4& a, uint32_t i) {
+      uint32_t g4[4][4];
+      split_vec(DT, a, g4);
+      if (i + 2 < per) a = ld(v + 2ull * T);
+#pragma unroll
+      for (int q = 0; q < V / 4; q++) {
+        uint32_t len;
+        const uint64_t x = join4(codes0, g4[0][q], len);
+        sw.put64(x, len);
+      }
+#pragma unroll
+      for (int g = 1; g < G; g++) {
+        if (!(raw >> g & 1u)) continue;
+        uint8_t* p = rawp[g] + v * V;
+        if (V == 8) *reinterpret_cast<uint2*>(p) = make_uint2(g4[g][0], g4[g][1]);
+        else *reinterpret_cast<uint32_t*>(p) = g4[g][0];
+      }
+      v += T;
+    };
+    for (uint32_t i = 0; i < per; i += 2) {
+      one(a0, i);
+      if (i + 1 < per) one(a1, i + 1);
+    }
+    sw.finish();
+    S.sbits[ui] = sw.bits;
+    S.part[0][ui] = sw.bits;
+  }
+}
+
 template <int DT>
 __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
                            const uint32_t* codes, const uint8_t* tabs, const GcMeta* meta,
@@ -678,7 +735,11 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
   if (!(slot_cap & 1u)) slot_cap--;
 
   // pass A: unit bits (+ raw planes, + slot encoding of group sg)
-  for (uint32_t u = tid; u < units; u += nthr) {
+  const bool fast_a = sg == 0 && huff == 1u && nb == J.chunk_bytes && nvec % T == 0 &&
+                      nvt % R == 0 && T <= (uint32_t)nthr;
+  if (fast_a)
+    pack_fast_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+  for (uint32_t u = fast_a ? units : tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T;
     uint32_t bits[G];
 #pragma unroll
@@ -718,17 +779,21 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
               sw.put64(x, len);
             }
           } else {
-            for (int q = 0; q < valid; q++) {
-              const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
-              sw.put(cl & 0xFFFFu, cl >> 16);
-            }
+#pragma unroll
+            for (int q = 0; q < V; q++)
+              if (q < valid) {
+                const uint32_t cl = S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))];
+                sw.put(cl & 0xFFFFu, cl >> 16);
+              }
           }
         } else if (huff >> g & 1) {
           if (full) {
 #pragma unroll
             for (int q = 0; q < V / 4; q++) bits[g] += len4(S.codes[g], g4[g][q]);
           } else {
-            for (int q = 0; q < valid; q++) bits[g] += S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu] >> 16;
+#pragma unroll
+            for (int q = 0; q < V; q++)
+              if (q < valid) bits[g] += S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))] >> 16;
           }
         } else if (raw >> g & 1) {
           uint8_t* p = out + P + S.off[g] + v * V;
@@ -737,7 +802,9 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
             else if (V == 4) *reinterpret_cast<uint32_t*>(p) = g4[g][0];
             else *reinterpret_cast<uint4*>(p) = make_uint4(g4[g][0], g4[g][1], g4[g][2], g4[g][3]);
           } else {
-            for (int q = 0; q < valid; q++) p[q] = (uint8_t)(g4[g][q >> 2] >> (8 * (q & 3)));
+#pragma unroll
+            for (int q = 0; q < V; q++)
+              if (q < valid) p[q] = (uint8_t)__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3));
           }
         }
       }
@@ -745,7 +812,9 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     }
     if (sg >= 0) {
       sw.finish();
-      bits[sg] = sw.bits;
+#pragma unroll
+      for (int g = 0; g < G; g++)
+        if (g == sg) bits[g] = sw.bits;
       S.sbits[t * R + k] = sw.bits;
     }
 #pragma unroll
@@ -849,10 +918,12 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
           }
         } else {
           const int valid = (int)(m - v * V);
-          for (int q = 0; q < valid; q++) {
-            const uint32_t cl = S.codes[g][(g4[g][q >> 2] >> (8 * (q & 3))) & 0xFFu];
-            bw[g].put(cl & 0xFFFFu, cl >> 16);
-          }
+#pragma unroll
+          for (int q = 0; q < V; q++)
+            if (q < valid) {
+              const uint32_t cl = S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))];
+              bw[g].put(cl & 0xFFFFu, cl >> 16);
+            }
         }
       }
     }
@@ -971,7 +1042,11 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
     const int hs = hist_smem_bytes(max_groups < 1 ? 4 : (max_groups > 4 ? 4 : max_groups));
     auto kh = pick(uniform_dtype, k_hist<ZIPNN_BF16>, k_hist<ZIPNN_FP16>, k_hist<ZIPNN_FP32>,
                    k_hist<ZIPNN_U8>, k_hist<-1>);
-    if (hs > 48 * 1024) cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, hs);
+    cudaError_t ea = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, hs);
+    if (ea == cudaSuccess)
+      ea = cudaFuncSetAttribute(kh, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
+    if (ea != cudaSuccess) return ea;
     kh<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist);
     unsigned nb = (unsigned)((ngc_total + kBuildWarps - 1) / kBuildWarps);
     k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.codes, s.tabs, s.meta);
@@ -990,6 +1065,9 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
                  k_pack<ZIPNN_U8>, k_pack<-1>);
   const int ps = (int)(kPackSlotWords * 4);
   cudaError_t ea = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  if (ea == cudaSuccess)
+    ea = cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
   if (ea != cudaSuccess) return ea;
   kp<<<(unsigned)(nchunks_total + njobs), kPackThreads, ps, st>>>(r, nchunks_total, s.codes, s.tabs,
                                                                 s.meta, s.offs, s.totals);

@@ -24,7 +24,7 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
@@ -81,12 +81,15 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   if (!out || count <= 0 || !streams || !d_dsts) return ZIPNN_EINVAL;
   *out = nullptr;
   std::vector<Job> jobs((size_t)count);
-  uint64_t chunk = 0;
+  uint64_t chunk = 0, max_chunk = 0;
   int max_groups = 1;
   int uniform = streams[0].dtype;
+  bool lanes256 = true;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
     if (s->dtype != uniform) uniform = -1;
+    if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
+    if (s->lanes % 256) lanes256 = false;
     if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
     const void* base = d_bases ? d_bases[i] : nullptr;
     if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
@@ -132,7 +135,7 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   if (tuning) tu = *tuning;
   e = capture(p, [&](cudaStream_t cs) {
     return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
-                            uniform);
+                            uniform, max_chunk, lanes256);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;

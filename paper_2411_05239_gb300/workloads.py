@@ -52,6 +52,20 @@ def rowscaled_fp32(rows: int = 8192, cols: int = 8192, seed: int = 1, device="cp
 
 
 # ---------------------------------------------------------------------------
+# "Clean" models (Sec. 3.2): parameters held in a wider type than the precision
+# they carry.  FP32 holding BF16 values has its 16 low bits zero (the T5 rows of
+# the byte-grouping size table); FP16 holding BF16 values has the 3 low fraction
+# bits of every normal number zero.  N(0, 0.02) drawn as BF16; seeds 5 and 6;
+# 67,108,864 values (256 MiB FP32, 128 MiB FP16).
+def clean_fp32_from_bf16(n: int = 67_108_864, seed: int = 5, device="cpu") -> torch.Tensor:
+    return gaussian(n, 0.02, seed, torch.bfloat16, device).to(torch.float32)
+
+
+def clean_fp16_from_bf16(n: int = 67_108_864, seed: int = 6, device="cpu") -> torch.Tensor:
+    return gaussian(n, 0.02, seed, torch.bfloat16, device).to(torch.float16)
+
+
+# ---------------------------------------------------------------------------
 # 8B-class decoder-only checkpoint in BF16 (Llama-3.1-8B shapes): 32 layers of
 # q,o 4096x4096, k,v 1024x4096, gate,up 14336x4096, down 4096x14336, two RMSNorm
 # vectors of ones; embedding and head 128256x4096.  Weights N(0, 0.02/sqrt(2l+1))

@@ -44,9 +44,9 @@ def test_host_only_entry_points(lib):
     assert lib.zipnn_version() == 1
     lib.zipnn_default_lanes.restype = ctypes.c_uint32
     lib.zipnn_default_lanes.argtypes = [ctypes.c_int, ctypes.c_size_t]
-    assert lib.zipnn_default_lanes(0, 256 * 1024) == 128
-    assert lib.zipnn_default_lanes(2, 256 * 1024) == 64
-    assert lib.zipnn_default_lanes(0, 4096) == 2
+    assert lib.zipnn_default_lanes(0, 256 * 1024) == 256
+    assert lib.zipnn_default_lanes(2, 256 * 1024) == 128
+    assert lib.zipnn_default_lanes(0, 4096) == 4
     lib.zipnn_compress_bound.restype = ctypes.c_size_t
     lib.zipnn_compress_bound.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t]
     assert lib.zipnn_compress_bound(1 << 20, 0, 1 << 18) == 64 + 4 * 2 * 16 + (1 << 20) + 4 * 2 * 16

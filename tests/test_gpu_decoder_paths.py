@@ -1,0 +1,138 @@
+"""Decoder launch shapes and loops vs the CPU oracle (needs a GB300).
+
+The decoder has a specialised loop for chunks whose exponent group is Huffman
+coded and whose other groups are raw, zero or constant, and a generic loop for
+everything else; it runs with 128- or 256-thread CTAs, one or two sub-streams
+per thread, and W = 10, 11 or 12 bit pair tables (W = 11 resolves 12-bit codes
+inside the table entry).  None of these choices may change a decoded byte
+(lossless, ZipNN Sec. 2.3), and every container must stay byte-identical to the
+oracle's (Sec. 3.1, 3.2 and 5.1 as specified for the container).
+"""
+from __future__ import annotations
+
+import struct
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2411_05239_gb300 import workloads as W
+from paper_2411_05239_gb300 import zipnn as Z
+
+pytestmark = pytest.mark.gpu
+
+
+def u8(t: torch.Tensor) -> np.ndarray:
+    return t.contiguous().view(-1).view(torch.uint8).cpu().numpy()
+
+
+def skewed_exponents_bf16(n: int, seed: int) -> torch.Tensor:
+    """BF16 values whose exponent byte e = 0x7F - k has P(k) ~ 2^-k (k < 40):
+    the length limit of 12 binds, so every chunk holds codes of 11 and 12 bits."""
+    g = np.random.default_rng(seed)
+    k = np.minimum(g.geometric(0.5, size=n) - 1, 39)
+    e = (0x7F - k).astype(np.uint16)
+    frac = g.integers(0, 128, size=n).astype(np.uint16)
+    sign = (g.random(n) < 0.5).astype(np.uint16) << 15
+    bits = sign | (e << 7) | frac
+    return torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16)
+
+
+def max_code_len(stream: bytes) -> int:
+    """Longest code length of any Huffman group-chunk in a container."""
+    P = struct.unpack_from("<Q", stream, 32)[0]
+    G = struct.unpack_from("<I", stream, 24)[0]
+    nch = struct.unpack_from("<I", stream, 28)[0]
+    best = 0
+    for i in range(nch * G):
+        off, size, mode = struct.unpack_from("<QIB", stream, 64 + 16 * i)
+        if mode == 1:
+            bits = stream[P + off: P + off + 12]
+            best = max(best, max(l + 1 for l in range(12) if bits[l]))
+    return best
+
+
+CASES = [
+    ("bf16_gauss", Z.BF16, lambda: W.gaussian(600_001, 0.02, 81)),
+    ("bf16_long_codes", Z.BF16, lambda: skewed_exponents_bf16(524_288 + 77, 82)),
+    ("fp32_clean", Z.FP32, lambda: W.clean_fp32_from_bf16(262_144 + 5, 83)),
+    ("fp32_gauss", Z.FP32, lambda: W.gaussian(262_144, 0.05, 84, torch.float32)),
+    ("fp16_from_bf16", Z.FP16, lambda: W.clean_fp16_from_bf16(300_000, 85)),
+    ("u8_skewed", Z.U8, lambda: torch.from_numpy(
+        np.random.default_rng(86).geometric(0.3, size=1_048_576 + 9).clip(0, 255).astype(np.uint8))),
+]
+
+
+@pytest.mark.parametrize("name,dtype,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("lanes", [128, 256, 512, 768])
+def test_cta_sizes_table_widths_and_lanes(name, dtype, make, lanes):
+    x = make()
+    xs = u8(x)
+    chunk = 262144
+    c = Z.compress(x.cuda(), chunk_bytes=chunk, lanes=lanes, dtype=dtype)
+    want = O.compress(xs, dtype, chunk, lanes)
+    assert c.to_bytes() == want
+    out = torch.empty_like(x, device="cuda")
+    for w in (10, 11, 12):
+        for nt in (128, 256):
+            out.zero_()
+            Z.batch_decompress([c], [out], tune=Z.tuning(threads=nt, lut_bits=w))
+            Z.sync_status()
+            assert np.array_equal(u8(out), xs), (w, nt)
+
+
+def test_long_codes_are_present():
+    """The skewed case really exercises 12-bit codes (the W = 11 long entries)."""
+    x = skewed_exponents_bf16(262_144, 90)
+    assert max_code_len(O.compress(u8(x), Z.BF16, 262144)) == 12
+
+
+@pytest.mark.parametrize("lanes", [256, 512])
+def test_delta_on_fast_loop(lanes):
+    n = 524_288
+    nxt, base = W.delta_pair(n, seed=91, device="cuda")
+    c = Z.compress(nxt, chunk_bytes=262144, lanes=lanes, base=base)
+    assert c.to_bytes() == O.delta(u8(nxt), u8(base), Z.BF16, 262144, lanes)
+    out = torch.empty_like(nxt)
+    for nt in (128, 256):
+        Z.batch_decompress([c], [out], bases=[base], tune=Z.tuning(threads=nt))
+        Z.sync_status()
+        assert torch.equal(out.view(torch.int16), nxt.view(torch.int16))
+
+
+def test_mixed_batch_of_all_layouts():
+    """One persistent launch over tensors that take different loops and dtypes."""
+    xs = [make() for _, _, make in CASES]
+    cs = [Z.compress(x.cuda(), chunk_bytes=131072, lanes=256) for x in xs]
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    Z.batch_decompress(cs, outs)
+    Z.sync_status()
+    for x, o in zip(xs, outs):
+        assert np.array_equal(u8(o), u8(x))
+
+
+def test_wrong_substream_start_reports_ecorrupt_and_context_survives():
+    """A start-bit entry moved by one bit breaks the rule that every sub-stream
+    ends where the next one begins: the chunk is reported corrupt."""
+    x = W.gaussian(262_144 * 4, 0.02, 92)
+    c = Z.compress(x.cuda(), chunk_bytes=262144, lanes=256)
+    s = bytearray(c.to_bytes())
+    P = struct.unpack_from("<Q", s, 32)[0]
+    off, size, mode = struct.unpack_from("<QIB", s, 64 + 16 * (2 * 2))   # chunk 2, group 0
+    assert mode == 1
+    nz = sum(s[P + off: P + off + 12])
+    h = (12 + nz + 3) // 4 * 4
+    p = P + off + h + 4 * 4          # start bit of sub-stream 5
+    struct.pack_into("<I", s, p, struct.unpack_from("<I", s, p)[0] + 1)
+    buf = torch.from_numpy(np.frombuffer(bytes(s), dtype=np.uint8).copy()).cuda()
+    bad = Z.wrap(buf)
+    out = torch.empty_like(x, device="cuda")
+    Z.batch_decompress([bad], [out])
+    with pytest.raises(Z.ZipnnError) as ei:
+        Z.sync_status()
+    assert ei.value.status == -3  # ZIPNN_ECORRUPT
+    # the context still works
+    y = Z.decompress(c)
+    Z.sync_status()
+    assert torch.equal(y.cpu().view(torch.int16), x.view(torch.int16))
