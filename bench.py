@@ -345,26 +345,27 @@ def run_gb300(args):
         Z.sync_status()
         pt_ms = all_max([e0.elapsed_time(e1) / K], world)[0]
 
-    # end to end through host buffers: H2D of the containers (pinned), batched
-    # decode, D2H of the tensors (pinned), every step
-    e2e = None
+    # end to end through host buffers, every step: the load plan copies the
+    # containers from pinned host memory and decodes segment by segment with
+    # copies and decoding overlapped (zipnn_plan_load), then the device status
+    # word is read back (zipnn_sync_status: 4 bytes D2H).  The round-trip
+    # variant also copies every decoded tensor back to pinned host memory.
+    e2e = e2e_rt = None
     if args.e2e_steps > 0:
         h_cont = [torch.empty(c.nbytes, dtype=torch.uint8, pin_memory=True) for c in cs]
         for h, c in zip(h_cont, cs):
             h.copy_(c.device_tensor())
-        h_out = [torch.empty(t.numel(), dtype=torch.bfloat16, pin_memory=True) for t in ts]
-        d_cont = [c.device_tensor() for c in cs]
         torch.cuda.synchronize()
+        load = Z.plan_load(cs, h_cont, outs, segment_bytes=args.e2e_segment_mb << 20, tune=tune)
 
         def e2e_step():
-            for d, h in zip(d_cont, h_cont):
-                d.copy_(h, non_blocking=True)
-            dec_plan.launch(stream)
-            for h, o in zip(h_out, outs):
-                h.copy_(o, non_blocking=True)
-            stream.synchronize()
+            load.launch(stream)
+            Z.sync_status(stream)
 
         e2e_step()
+        for t, o in zip(ts[:3], outs[:3]):
+            if not torch.equal(t.view(torch.int16), o.view(torch.int16)):
+                raise SystemExit("e2e load mismatch")
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -373,14 +374,36 @@ def run_gb300(args):
         torch.cuda.synchronize()
         barrier(world)
         e2e_s = all_max([(time.perf_counter() - t0) / args.e2e_steps], world)[0]
-        ok = all(torch.equal(h.view(torch.int16), t.view(torch.int16).cpu())
-                 for h, t in zip(h_out[:3], ts[:3]))
-        if not ok:
-            raise SystemExit("e2e round trip mismatch")
         e2e = {"value": world * orig / e2e_s / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": comp_bytes, "d2h_bytes_per_step": orig,
+               "h2d_bytes_per_step": comp_bytes, "d2h_bytes_per_step": 4,
                "steps": args.e2e_steps, "ms_per_step": e2e_s * 1e3,
-               "path": "pinned host containers -> H2D -> batched decode plan -> D2H pinned"}
+               "path": "zipnn_plan_load: pinned host containers -> H2D (copy stream) overlapped "
+                       "with per-segment persistent decode into HBM -> zipnn_sync_status (4 B D2H)",
+               "segment_mb": args.e2e_segment_mb}
+        # round trip: the decoded tensors also go back to pinned host memory
+        h_out = [torch.empty(t.numel(), dtype=torch.bfloat16, pin_memory=True) for t in ts]
+
+        def rt_step():
+            load.launch(stream)
+            for h, o in zip(h_out, outs):
+                h.copy_(o, non_blocking=True)
+            Z.sync_status(stream)
+
+        rt_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            rt_step()
+        torch.cuda.synchronize()
+        rt_s = all_max([(time.perf_counter() - t0) / args.e2e_steps], world)[0]
+        if not all(torch.equal(h.view(torch.int16), t.view(torch.int16).cpu())
+                   for h, t in zip(h_out[:3], ts[:3])):
+            raise SystemExit("e2e round trip mismatch")
+        e2e_rt = {"value": world * orig / rt_s / 1e9, "unit": "GB/s",
+                  "h2d_bytes_per_step": comp_bytes, "d2h_bytes_per_step": orig,
+                  "ms_per_step": rt_s * 1e3,
+                  "path": "zipnn_plan_load, then every decoded tensor D2H to pinned memory"}
+        load.close()
         del h_cont, h_out
 
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
@@ -431,6 +454,7 @@ def run_gb300(args):
                               "algorithmic_bytes": alg_comp},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "e2e_roundtrip": e2e_rt,
         "gpu_launches": 5 * K,
         "clocks": clocks,
         "wall_s_timed": mwall,
@@ -448,7 +472,8 @@ def run_gb300(args):
 
 def run_tensors(args):
     """Single-configuration modes: plain 8 MiB BF16 (L2-flushed between steps),
-    256 MiB row-scaled FP32, and the 3.43 GB checkpoint delta (base + next).
+    256 MiB row-scaled FP32, the 3.43 GB checkpoint delta (base + next), and the
+    clean-model tensors (FP32 / FP16 holding BF16 values, Sec. 3.2).
     Same step as the checkpoint mode: graph-captured compress + decode."""
     from paper_2411_05239_gb300 import workloads as W
     from paper_2411_05239_gb300 import zipnn as Z
@@ -462,6 +487,12 @@ def run_tensors(args):
     elif args.workload == "fp32":
         xs = [W.rowscaled_fp32(device="cuda")]
         name = "rowscaled_fp32_256mib"
+    elif args.workload == "clean_fp32":
+        xs = [W.clean_fp32_from_bf16(device="cuda")]
+        name = "clean_fp32_from_bf16_256mib"
+    elif args.workload == "clean_fp16":
+        xs = [W.clean_fp16_from_bf16(device="cuda")]
+        name = "clean_fp16_from_bf16_128mib"
     else:
         n = sum(sp.numel for sp in W.delta_specs())
         nxt, base = W.delta_pair(n, seed=3, device="cuda")
@@ -651,12 +682,15 @@ def main(argv=None):
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick chunk size, lanes, table width, CTAs/SM on a sample first")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-segment-mb", type=int, default=512,
+                    help="container bytes per decode launch in the load plan")
     ap.add_argument("--per-tensor", type=int, default=1)
     ap.add_argument("--cpu-sample-mb", type=int, default=384)
     ap.add_argument("--layers", type=int, default=32, help="decoder layers (32 = 8B class)")
     ap.add_argument("--vocab", type=int, default=128256, help="embedding/head rows")
     ap.add_argument("--workload", default="checkpoint",
-                    choices=["checkpoint", "serve", "plain", "fp32", "delta"])
+                    choices=["checkpoint", "serve", "plain", "fp32", "delta", "clean_fp32",
+                             "clean_fp16"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -667,7 +701,7 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
-    if args.workload in ("plain", "fp32", "delta"):
+    if args.workload in ("plain", "fp32", "delta", "clean_fp32", "clean_fp16"):
         return run_tensors(args)
     return run_gb300(args)
 

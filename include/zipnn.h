@@ -178,6 +178,28 @@ zipnn_status zipnn_batch_compress_into(const void* const* d_srcs, const void* co
                                        size_t workspace_bytes, uint64_t* d_out_nbytes,
                                        void* cuda_stream);
 
+/* Encoder options (zipnn_batch_compress_into_ex).
+ * lanes: sub-streams per Huffman group-chunk, 0 = zipnn_default_lanes.
+ * probe_skip: the skip-ahead probe of ZipNN Sec. 3.2 ("Identifying
+ *   compressibility"): after a group-chunk is decided raw, the same byte group
+ *   of the next probe_skip chunks of the tensor is stored raw without its
+ *   decision counting, then decisions resume; 0 = every group-chunk decided on
+ *   its own (the default).  The containers stay valid version-1 containers.
+ * reserved: must be zero (EINVAL otherwise). */
+typedef struct zipnn_encode_options {
+    uint32_t lanes;
+    uint32_t probe_skip;
+    uint32_t reserved[2];
+} zipnn_encode_options;
+
+/* zipnn_batch_compress_into with encoder options (opts may be NULL: defaults);
+ * arguments, workspace and errors otherwise as zipnn_batch_compress_into. */
+zipnn_status zipnn_batch_compress_into_ex(
+    const void* const* d_srcs, const void* const* d_bases, const size_t* nbytes,
+    const int* dtypes, int count, size_t chunk_bytes, const zipnn_encode_options* opts,
+    void* const* d_outs, const size_t* out_capacities, void* d_workspace,
+    size_t workspace_bytes, uint64_t* d_out_nbytes, void* cuda_stream);
+
 /* Wrap a container that is already in device memory (e.g. copied from a file)
  * as a zipnn_stream: reads and validates its 64-B header (synchronous copy of
  * 64 bytes).  The stream does not own d_data.  ECORRUPT if the header is bad. */
@@ -224,6 +246,20 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
                                  size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
                                  const size_t* out_capacities, uint64_t* d_out_nbytes,
                                  zipnn_plan** out);
+/* zipnn_plan_load (loading form, e.g. a checkpoint kept compressed in host
+ *   memory): every launch copies container i from h_containers[i] (page-locked
+ *   host memory, streams[i].nbytes bytes) into streams[i].data (device, 16-B
+ *   aligned, at least streams[i].nbytes bytes; streams[i] describes the
+ *   container, e.g. from zipnn_stream_wrap of an earlier copy) and decodes it
+ *   into d_dsts[i] (XOR d_bases[i] for delta containers, as
+ *   zipnn_batch_decompress).  Containers are taken in order in segments of
+ *   about segment_bytes (0 = 512 MiB); each segment's persistent decode starts
+ *   as soon as its copies have landed, while the copies of the next segments
+ *   proceed on another stream: one graph, copies and decoding overlapped.
+ *   Pageable host memory cannot be captured and returns ECUDA. */
+zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_containers,
+                             const void* const* d_bases, void* const* d_dsts, int count,
+                             size_t segment_bytes, const zipnn_tuning* tuning, zipnn_plan** out);
 zipnn_status zipnn_plan_launch(zipnn_plan* plan, void* cuda_stream);
 void zipnn_plan_destroy(zipnn_plan* plan);
 

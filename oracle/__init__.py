@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
         L.or_bound.restype = sz
         L.or_compress.argtypes = [ctypes.c_void_p, sz, ctypes.c_int, sz, ctypes.c_uint32,
                                   ctypes.c_void_p, sz, ctypes.POINTER(sz)]
+        L.or_compress_skip.argtypes = [ctypes.c_void_p, sz, ctypes.c_int, sz, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_void_p, sz, ctypes.c_void_p]
         L.or_delta.argtypes = [ctypes.c_void_p, ctypes.c_void_p, sz, ctypes.c_int, sz,
                                ctypes.c_uint32, ctypes.c_void_p, sz, ctypes.POINTER(sz)]
         L.or_decompress.argtypes = [ctypes.c_void_p, sz, ctypes.c_void_p, ctypes.c_void_p, sz]
@@ -129,15 +131,22 @@ def bound(nbytes: int, dtype: int, chunk_bytes: int) -> int:
     return int(lib().or_bound(nbytes, dtype, chunk_bytes))
 
 
-def compress(data, dtype: int, chunk_bytes: int = 256 * 1024, lanes: int | None = None) -> bytes:
+def compress(data, dtype: int, chunk_bytes: int = 256 * 1024, lanes: int | None = None,
+             skip: int = 0) -> bytes:
+    """Container of `data`; skip > 0 applies the skip-ahead probe (Sec. 3.2):
+    after a raw group-chunk the same group of the next `skip` chunks is raw."""
     src = _as_u8(data)
     if lanes is None:
         lanes = default_lanes(dtype, chunk_bytes)
     cap = bound(src.size, dtype, chunk_bytes) + 64
     out = np.zeros(cap, dtype=np.uint8)
     n = ctypes.c_size_t(0)
-    rc = lib().or_compress(_ptr(src), src.size, dtype, chunk_bytes, lanes, _ptr(out), cap,
-                           ctypes.byref(n))
+    if skip:
+        rc = lib().or_compress_skip(_ptr(src), src.size, dtype, chunk_bytes, lanes, skip,
+                                    _ptr(out), cap, ctypes.byref(n))
+    else:
+        rc = lib().or_compress(_ptr(src), src.size, dtype, chunk_bytes, lanes, _ptr(out), cap,
+                               ctypes.byref(n))
     if rc:
         raise OracleError(rc, "compress")
     return out[: n.value].tobytes()

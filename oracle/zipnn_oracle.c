@@ -34,8 +34,11 @@
  *     bits, leaves ordered by (count ascending, symbol descending), leaves
  *     before packages on equal weight; canonical codes as in RFC 1951 3.2.2;
  *     table as code-length counts followed by the symbols (JPEG DHT layout);
- *   - raw-vs-Huffman: exact per group-chunk decision with a 1/64 margin; the
- *     paper's skip-ahead probe is not used;
+ *   - raw-vs-Huffman: exact per group-chunk decision with a 1/64 margin;
+ *     the paper's skip-ahead probe (Sec. 3.2, "Identifying compressibility")
+ *     is an option: after a group-chunk comes out raw, the same group of the
+ *     next `skip` chunks is stored raw without being evaluated, then
+ *     evaluation resumes ("the specific number varies": skip is a parameter);
  *   - symbols of a group-chunk are dealt to T interleaved sub-streams in
  *     vectors of V = 16/element_size symbols; each sub-stream's start bit is
  *     stored so sub-streams decode independently.
@@ -423,7 +426,7 @@ int or_compress_chunk(const uint8_t* src, size_t nb, int dtype, uint32_t lanes,
  *     the payload area, u32 payload size, u8 mode, u8 value, u16 zero;
  *   payloads in (chunk, group) order, each zero-padded to 16 B.            */
 static int compress_impl(const uint8_t* src, size_t nbytes, int dtype, size_t chunk_bytes,
-                         uint32_t lanes, uint32_t flags, uint8_t* out, size_t cap,
+                         uint32_t lanes, uint32_t flags, uint32_t skip, uint8_t* out, size_t cap,
                          size_t* out_size) {
     int rc = check_params(dtype, nbytes, chunk_bytes, lanes);
     if (rc) return rc;
@@ -437,7 +440,9 @@ static int compress_impl(const uint8_t* src, size_t nbytes, int dtype, size_t ch
 
     size_t stride = chunk_bytes / (size_t)es + 1100;
     uint8_t* pay = (uint8_t*)malloc(stride * (size_t)G);
-    if (!pay) return OR_ENOMEM;
+    uint8_t* planes = (uint8_t*)malloc(chunk_bytes + 16);
+    if (!pay || !planes) { free(pay); free(planes); return OR_ENOMEM; }
+    uint32_t skip_left[4] = {0, 0, 0, 0};
     uint64_t cursor = 0;
     for (size_t c = 0; c < nch; c++) {
         size_t off = c * chunk_bytes;
@@ -445,6 +450,24 @@ static int compress_impl(const uint8_t* src, size_t nbytes, int dtype, size_t ch
         int32_t modes[4], values[4];
         uint64_t sizes[4];
         or_compress_chunk(src + off, nb, dtype, lanes, modes, values, sizes, pay, stride);
+        if (skip) {
+            /* skip-ahead probe: a group inside its skip window is stored raw
+             * (its evaluation above is discarded); a group evaluated raw opens
+             * a window over the next `skip` chunks */
+            size_t m = nb / (size_t)es;
+            or_split(dtype, src + off, m, planes);
+            for (int g = 0; g < G; g++) {
+                if (skip_left[g] > 0) {
+                    skip_left[g]--;
+                    modes[g] = OR_RAW;
+                    values[g] = 0;
+                    sizes[g] = m;
+                    memcpy(pay + (size_t)g * stride, planes + (size_t)g * m, m);
+                } else if (modes[g] == OR_RAW) {
+                    skip_left[g] = skip;
+                }
+            }
+        }
         for (int g = 0; g < G; g++) {
             uint8_t* e = out + OR_HDR_BYTES + (c * (size_t)G + (size_t)g) * OR_ENTRY_BYTES;
             put_u64(e, cursor);
@@ -452,13 +475,14 @@ static int compress_impl(const uint8_t* src, size_t nbytes, int dtype, size_t ch
             e[12] = (uint8_t)modes[g];
             e[13] = (uint8_t)values[g];
             size_t padded = (size_t)align_up(sizes[g], 16);
-            if (P + cursor + padded > cap) { free(pay); return OR_ENOMEM; }
+            if (P + cursor + padded > cap) { free(pay); free(planes); return OR_ENOMEM; }
             memset(out + P + cursor, 0, padded);
             memcpy(out + P + cursor, pay + (size_t)g * stride, sizes[g]);
             cursor += padded;
         }
     }
     free(pay);
+    free(planes);
     uint8_t* h = out;
     h[0] = 'Z'; h[1] = 'N'; h[2] = 'N'; h[3] = '1';
     put_u16(h + 4, 1);
@@ -477,7 +501,14 @@ static int compress_impl(const uint8_t* src, size_t nbytes, int dtype, size_t ch
 
 int or_compress(const uint8_t* src, size_t nbytes, int dtype, size_t chunk_bytes, uint32_t lanes,
                 uint8_t* out, size_t cap, size_t* out_size) {
-    return compress_impl(src, nbytes, dtype, chunk_bytes, lanes, 0, out, cap, out_size);
+    return compress_impl(src, nbytes, dtype, chunk_bytes, lanes, 0, 0, out, cap, out_size);
+}
+
+/* Compression with the skip-ahead probe (Sec. 3.2, "Identifying
+ * compressibility"): skip = chunks stored raw after a raw group-chunk. */
+int or_compress_skip(const uint8_t* src, size_t nbytes, int dtype, size_t chunk_bytes,
+                     uint32_t lanes, uint32_t skip, uint8_t* out, size_t cap, size_t* out_size) {
+    return compress_impl(src, nbytes, dtype, chunk_bytes, lanes, 0, skip, out, cap, out_size);
 }
 
 /* Delta (Sec. 4.2): the container of a XOR b, flagged DELTA. */
@@ -486,7 +517,8 @@ int or_delta(const uint8_t* a, const uint8_t* b, size_t nbytes, int dtype, size_
     uint8_t* x = (uint8_t*)malloc(nbytes + 1);
     if (!x) return OR_ENOMEM;
     for (size_t i = 0; i < nbytes; i++) x[i] = (uint8_t)(a[i] ^ b[i]);
-    int rc = compress_impl(x, nbytes, dtype, chunk_bytes, lanes, OR_FLAG_DELTA, out, cap, out_size);
+    int rc = compress_impl(x, nbytes, dtype, chunk_bytes, lanes, OR_FLAG_DELTA, 0, out, cap,
+                           out_size);
     free(x);
     return rc;
 }

@@ -23,7 +23,7 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64);
 }  // namespace zipnn
 
 using namespace zipnn;
@@ -322,16 +322,20 @@ extern "C" size_t zipnn_batch_compress_workspace_size(const size_t* nbytes, cons
   return batch_ws_bytes(bp);
 }
 
-extern "C" zipnn_status zipnn_batch_compress_into(
+extern "C" zipnn_status zipnn_batch_compress_into_ex(
     const void* const* d_srcs, const void* const* d_bases, const size_t* nbytes,
-    const int* dtypes, int count, size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
-    const size_t* out_capacities, void* d_workspace, size_t workspace_bytes,
-    uint64_t* d_out_nbytes, void* cuda_stream) {
+    const int* dtypes, int count, size_t chunk_bytes, const zipnn_encode_options* opts,
+    void* const* d_outs, const size_t* out_capacities, void* d_workspace,
+    size_t workspace_bytes, uint64_t* d_out_nbytes, void* cuda_stream) {
   if (!d_outs) return ZIPNN_EINVAL;
+  const uint32_t lanes = opts ? opts->lanes : 0u;
+  const uint32_t skip = opts ? opts->probe_skip : 0u;
+  if (opts && (opts->reserved[0] || opts->reserved[1])) return ZIPNN_EINVAL;
   BatchPlan bp;
   zipnn_status rc = plan_batch_compress(d_srcs, d_bases, nbytes, dtypes, count, chunk_bytes,
                                         lanes, d_outs, out_capacities, d_out_nbytes, &bp);
   if (rc) return rc;
+  for (Job& J : bp.jobs) J.skip = skip;
   if (!d_workspace || workspace_bytes < batch_ws_bytes(bp)) return ZIPNN_ENOMEM;
   uint32_t* err = err_word();
   if (!err) return ZIPNN_ECUDA;
@@ -349,6 +353,19 @@ extern "C" zipnn_status zipnn_batch_compress_into(
     e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st,
                               bp.uniform);
   return cuda_status(e);
+}
+
+extern "C" zipnn_status zipnn_batch_compress_into(
+    const void* const* d_srcs, const void* const* d_bases, const size_t* nbytes,
+    const int* dtypes, int count, size_t chunk_bytes, uint32_t lanes, void* const* d_outs,
+    const size_t* out_capacities, void* d_workspace, size_t workspace_bytes,
+    uint64_t* d_out_nbytes, void* cuda_stream) {
+  zipnn_encode_options o;
+  memset(&o, 0, sizeof(o));
+  o.lanes = lanes;
+  return zipnn_batch_compress_into_ex(d_srcs, d_bases, nbytes, dtypes, count, chunk_bytes, &o,
+                                      d_outs, out_capacities, d_workspace, workspace_bytes,
+                                      d_out_nbytes, cuda_stream);
 }
 
 static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t nbytes, int dtype,
@@ -448,7 +465,8 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   Job J = decode_job(s, d_base_or_null, d_dst);
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
-                                   nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0);
+                                   nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0,
+                                   stage_frac64(s->dtype, s->flags));
   return cuda_status(e);
 }
 
@@ -462,11 +480,13 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   int max_groups = 1;
   int uniform = streams[0].dtype;
   bool lanes256 = true;
+  int frac64 = 0;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
     if (s->dtype != uniform) uniform = -1;
     if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
     if (s->lanes % 256) lanes256 = false;
+    if (stage_frac64(s->dtype, s->flags) > frac64) frac64 = stage_frac64(s->dtype, s->flags);
     zipnn_status rc = check_stream(s);
     if (rc) return rc;
     const void* base = d_bases ? d_bases[i] : nullptr;
@@ -490,7 +510,7 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
-                         uniform, max_chunk, lanes256);
+                         uniform, max_chunk, lanes256, frac64);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

@@ -38,12 +38,12 @@ namespace zipnn {
 namespace {
 
 constexpr int kDecThreads = 128;  // CTA size of mixed-dtype and W = 10 launches; else 256
-// Shared-memory staging for Huffman payloads: sized for the largest chunk of
-// the launch (an exponent payload of a 16-bit chunk is about a sixth of the
-// chunk), at most kStageBytes; payloads that do not fit are read from global
-// memory instead.
-constexpr uint32_t kStageBytes = 45056;
+// Shared-memory staging for Huffman payloads: sized at launch from the largest
+// chunk and the dtypes of the launch (decode_stage_bytes); payloads that do
+// not fit are read from global memory instead.
 constexpr uint32_t kStageMin = 4096;
+constexpr uint32_t kStageCapPerSm = 227u * 1024u;  // shared memory an SM gives its CTAs
+constexpr uint32_t kStaticReserve = 4096;          // static Smem + the per-CTA reservation
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -889,24 +889,26 @@ DecodeKernel pick_kernel(int dt) {
 
 }  // namespace
 
-// Stage size: room for the payloads of the largest chunk (capped), and always
+// Stage size: room for the payloads of the largest chunk (frac64 / 64 of it,
+// see stage_frac64), at most what lets two CTAs share an SM, and always room
 // for the tables of every Huffman group after the first.
-uint32_t decode_stage_bytes(uint64_t max_chunk, int max_groups, int w) {
-  const uint64_t want = (max_chunk * 11 / 64 + 1024 + 127) & ~127ull;
-  uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > kStageBytes ? kStageBytes : want));
+uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w) {
+  const uint64_t cap = (uint64_t)kStageCapPerSm / 2 - (4u << w) - kStaticReserve;
+  const uint64_t want = (max_chunk * (uint64_t)frac64 / 64 + 1024 + 127) & ~127ull;
+  uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > cap ? cap : want));
   const uint32_t tabs = (uint32_t)(max_groups - 1) * (4u << w) + 256u;
   return st > tabs ? st : tabs;
 }
 
 // Dynamic shared memory of one decode CTA: one table slot + the stage.
-int decode_smem_bytes(int w, uint64_t max_chunk, int max_groups) {
-  return (4 << w) + (int)decode_stage_bytes(max_chunk, max_groups, w);
+int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups) {
+  return (4 << w) + (int)decode_stage_bytes(max_chunk, frac64, max_groups, w);
 }
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256) {
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64) {
   if (nchunks_total == 0) return cudaSuccess;
   JobRef r;
   r.table = h_one ? nullptr : d_jobs;
@@ -917,6 +919,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     uniform_dtype = h_one->dtype;
     max_chunk = h_one->chunk_bytes;
     lanes256 = h_one->lanes % 256 == 0;
+    frac64 = stage_frac64(h_one->dtype, h_one->flags);
   }
   int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 12;
   if (w < 10) w = 10;
@@ -935,8 +938,8 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
   if (max_groups < 1 || max_groups > 4) max_groups = 4;
-  const uint32_t stage = decode_stage_bytes(max_chunk, max_groups, w);
-  const int smem = decode_smem_bytes(w, max_chunk, max_groups);
+  const uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w);
+  const int smem = decode_smem_bytes(w, max_chunk, frac64, max_groups);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // all of the unified L1 / shared array as shared memory, so the CTAs per

@@ -53,6 +53,12 @@ __device__ __forceinline__ int find_job_gc(const JobRef& r, uint64_t gc) {
 
 // Load original vector v (16 bytes) of a chunk, XOR-ed with the base when
 // given; bytes past nb (a partial last vector) read as zero.
+// Ask L2 for the 128-B line holding p, without a register or a wait: loads
+// issued later find it in L2 instead of waiting for DRAM.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ uint4 load_vec(const uint8_t* src, const uint8_t* base, uint64_t v,
                                           uint64_t nb) {
   uint4 a;
@@ -95,6 +101,25 @@ __device__ __forceinline__ void split_vec(int dtype, uint4 a, uint32_t out[4][4]
 // 32 different banks (one wavefront, whatever the symbols), which removes the
 // bank conflicts that bound a plain per-warp histogram.
 
+// Shared-memory add without a result, on a 32-bit shared-window address.
+__device__ __forceinline__ void red_shared_inc(uint32_t saddr) {
+  asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(saddr) : "memory");
+}
+
+// Histogram of a whole chunk of 16-bit elements (no ragged vector): the byte
+// offsets of an element h's counters follow from its bits directly.  Exponent
+// bin e = (h >> 7) & 0xFF sits at e * 128 = h & 0x7F80; the sign + low-fraction
+// bin r = (h >> 8 & 0x80) | (h & 0x7F) sits at 0x8000 + r * 128 =
+// 0x8000 | (h >> 1 & 0x4000) | (h << 7 & 0x3F80).  hl is the shared-window
+// address of lane 0's counter of exponent bin 0 plus 4 * lane.
+__device__ __forceinline__ void hist16_word(uint32_t hl, uint32_t w) {
+  red_shared_inc(hl + (w & 0x7F80u));
+  red_shared_inc(hl + (((w >> 1) & 0x4000u) | (((w << 7) & 0x3F80u) | 0x8000u)));
+  const uint32_t h = w >> 16;
+  red_shared_inc(hl + (h & 0x7F80u));
+  red_shared_inc(hl + (((h >> 1) & 0x4000u) | (((h << 7) & 0x3F80u) | 0x8000u)));
+}
+
 template <int DT>
 __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist) {
   constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
@@ -112,7 +137,38 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   const uint64_t nvec = (nb + 15) / 16;
   const uint64_t m = nb / ES;
   constexpr int U = 4;  // vectors in flight per thread
-  for (uint64_t v0 = tid; v0 < nvec; v0 += (uint64_t)kHistThreads * U) {
+  uint64_t vstart = tid;
+  if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
+    // whole rounds of kHistThreads * U vectors of whole 16-bit elements
+    const uint64_t nfast = nb % 16 ? 0 : nvec / ((uint64_t)kHistThreads * U) * (kHistThreads * U);
+    const uint32_t hls = (uint32_t)__cvta_generic_to_shared(hl);
+    for (uint64_t v0 = tid; v0 < nfast; v0 += (uint64_t)kHistThreads * U) {
+      uint4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t v = v0 + (uint64_t)u * kHistThreads;
+        const uint64_t vp = v + 2ull * kHistThreads * U;  // two rounds ahead
+        if (vp < nfast) {
+          prefetch_l2(reinterpret_cast<const uint4*>(src) + vp);
+          if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + vp);
+        }
+        a[u] = __ldg(reinterpret_cast<const uint4*>(src) + v);
+        if (base) {
+          const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
+          a[u].x ^= b.x; a[u].y ^= b.y; a[u].z ^= b.z; a[u].w ^= b.w;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        hist16_word(hls, a[u].x);
+        hist16_word(hls, a[u].y);
+        hist16_word(hls, a[u].z);
+        hist16_word(hls, a[u].w);
+      }
+    }
+    vstart = nfast + tid;
+  }
+  for (uint64_t v0 = vstart; v0 < nvec; v0 += (uint64_t)kHistThreads * U) {
     uint4 a[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -400,18 +456,42 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
 }
 
 // ---------------------------------------------------------------------------
-// k_scan: one CTA per tensor, exclusive scan of padded payload sizes.
+// k_scan: one CTA per tensor, exclusive scan of padded payload sizes.  With
+// the skip-ahead probe (J.skip > 0, ZipNN Sec. 3.2 "Identifying
+// compressibility") thread g first walks the tensor's chunks in order for
+// group g: after a group-chunk decided raw, the same group of the next J.skip
+// chunks becomes raw (the builder's result for them is discarded), then
+// decisions resume.
 
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(JobRef jr, const GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
+k_scan(JobRef jr, GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
        uint64_t* __restrict__ totals, uint32_t* __restrict__ err) {
   __shared__ uint64_t warp_sums[kScanThreads / 32];
   const int j = blockIdx.x;
   const Job& J = job_at(jr, j);
   const int G = elem_size(J.dtype);
   const uint64_t ngc = (uint64_t)J.n_chunks * G;
+  if (J.skip) {
+    if ((int)threadIdx.x < G) {
+      const int g = threadIdx.x;
+      uint32_t left = 0;
+      for (uint32_t c = 0; c < J.n_chunks; c++) {
+        GcMeta& M = meta[J.gc_begin + (uint64_t)c * G + g];
+        if (left) {
+          left--;
+          const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - (uint64_t)c * J.chunk_bytes);
+          M.mode = kRaw;
+          M.value = 0;
+          M.size = (uint32_t)(nb / G);
+        } else if (M.mode == kRaw) {
+          left = J.skip;
+        }
+      }
+    }
+    __syncthreads();
+  }
   const uint64_t per = (ngc + kScanThreads - 1) / kScanThreads;
   const uint64_t b0 = min(ngc, per * threadIdx.x), b1 = min(ngc, b0 + per);
   uint64_t local = 0;
@@ -468,6 +548,7 @@ k_scan(JobRef jr, const GcMeta* __restrict__ meta, uint64_t* __restrict__ offs,
 constexpr int kPackThreads = 512;
 constexpr int kPackMaxUnits = 1024;
 constexpr uint32_t kPackSlotWords = 20480;  // 80 KiB of unit slots
+constexpr uint32_t kPrefetchAhead = 8;  // pass-A vectors between an L2 prefetch and its load
 
 __device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
   for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
@@ -616,7 +697,8 @@ __device__ __forceinline__ uint32_t len4(const uint32_t* codes, uint32_t w) {
 // Pass A for the dominant chunk layout: group 0 Huffman (slot-encoded), every
 // other group raw, zero or constant (bit g of raw set for raw groups), a whole
 // chunk whose vectors split evenly over the T sub-streams and R parts (per
-// vectors per unit).  No tails: per vector one 16-B load (two in flight), the
+// vectors per unit).  No tails: per vector one 16-B load (two in flight, the
+// line requested from L2 eight vectors earlier), the
 // split, V/4 joined code appends into the unit's slot and one store per raw
 // group.
 template <int DT>
@@ -649,11 +731,16 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
     sw.cap = slot_cap;
     sw.bits = 0;
     uint64_t v = t + (uint64_t)k * per * T;
+    constexpr uint32_t D = 2;  // vectors in flight per thread (L2 prefetches run further ahead)
     uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
     auto one = [&](uint4& a, uint32_t i) {
       uint32_t g4[4][4];
       split_vec(DT, a, g4);
-      if (i + 2 < per) a = ld(v + 2ull * T);
+      if (i + D < per) a = ld(v + (uint64_t)D * T);
+      if (i + kPrefetchAhead < per) {
+        prefetch_l2(reinterpret_cast<const uint4*>(src) + v + (uint64_t)kPrefetchAhead * T);
+        if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + v + (uint64_t)kPrefetchAhead * T);
+      }
 #pragma unroll
       for (int q = 0; q < V / 4; q++) {
         uint32_t len;
@@ -669,7 +756,7 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
       }
       v += T;
     };
-    for (uint32_t i = 0; i < per; i += 2) {
+    for (uint32_t i = 0; i < per; i += D) {
       one(a0, i);
       if (i + 1 < per) one(a1, i + 1);
     }

@@ -24,14 +24,14 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
 using namespace zipnn;
 
 struct zipnn_plan {
-  int kind = 0;                 // 1 = decompress, 2 = compress
+  int kind = 0;                 // 1 = decompress, 2 = compress, 3 = load
   int device = 0;
   void* dmem = nullptr;         // job table + ticket + scratch
   cudaGraph_t graph = nullptr;
@@ -85,11 +85,13 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   int max_groups = 1;
   int uniform = streams[0].dtype;
   bool lanes256 = true;
+  int frac64 = 0;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
     if (s->dtype != uniform) uniform = -1;
     if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
     if (s->lanes % 256) lanes256 = false;
+    if (stage_frac64(s->dtype, s->flags) > frac64) frac64 = stage_frac64(s->dtype, s->flags);
     if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
     const void* base = d_bases ? d_bases[i] : nullptr;
     if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
@@ -135,7 +137,7 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   if (tuning) tu = *tuning;
   e = capture(p, [&](cudaStream_t cs) {
     return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
-                            uniform, max_chunk, lanes256);
+                            uniform, max_chunk, lanes256, frac64);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
@@ -211,6 +213,119 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
       e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs, uniform);
     return e2;
   });
+  if (e != cudaSuccess) return fail(p, e);
+  *out = p;
+  return ZIPNN_OK;
+}
+
+zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_containers,
+                             const void* const* d_bases, void* const* d_dsts, int count,
+                             size_t segment_bytes, const zipnn_tuning* tuning, zipnn_plan** out) {
+  if (!out || count <= 0 || !streams || !h_containers || !d_dsts) return ZIPNN_EINVAL;
+  *out = nullptr;
+  if (segment_bytes == 0) segment_bytes = (size_t)512 << 20;
+  // jobs as in zipnn_plan_decompress, grouped into segments of consecutive
+  // containers holding about segment_bytes each
+  std::vector<Job> jobs((size_t)count);
+  std::vector<int> seg_first;
+  size_t seg_fill = 0;
+  for (int i = 0; i < count; i++) {
+    const zipnn_stream* s = &streams[i];
+    if (!s->data || !aligned16(s->data) || !h_containers[i]) return ZIPNN_EINVAL;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
+    if ((s->orig_nbytes && !d_dsts[i]) || !aligned16(d_dsts[i]) || !aligned16(base))
+      return ZIPNN_EINVAL;
+    if (s->n_groups != (uint32_t)elem_size(s->dtype) || s->dtype < 0 || s->dtype > ZIPNN_U8 ||
+        s->lanes < 1 || s->lanes > ZIPNN_MAX_LANES || s->chunk_bytes < ZIPNN_MIN_CHUNK ||
+        (uint64_t)s->n_chunks != (s->orig_nbytes + s->chunk_bytes - 1) / s->chunk_bytes)
+      return ZIPNN_EINVAL;
+    if (i == 0 || seg_fill >= segment_bytes) {
+      seg_first.push_back(i);
+      seg_fill = 0;
+    }
+    seg_fill += s->nbytes;
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.src = static_cast<const uint8_t*>(s->data);
+    J.base = static_cast<const uint8_t*>(base);
+    J.dst = static_cast<uint8_t*>(d_dsts[i]);
+    J.nbytes = s->orig_nbytes;
+    J.chunk_bytes = s->chunk_bytes;
+    J.lanes = s->lanes;
+    J.n_chunks = s->n_chunks;
+    J.dtype = s->dtype;
+    J.flags = s->flags;
+    J.stream_bytes = s->nbytes;
+    jobs[i] = J;
+  }
+  const int nseg = (int)seg_first.size();
+  seg_first.push_back(count);
+  // chunk numbering restarts in every segment (each has its own table and ticket)
+  for (int k = 0; k < nseg; k++) {
+    uint64_t ch = 0;
+    for (int i = seg_first[k]; i < seg_first[k + 1]; i++) {
+      jobs[i].chunk_begin = ch;
+      ch += jobs[i].n_chunks;
+    }
+  }
+  uint32_t* err = plan_err_word();
+  if (!err) return ZIPNN_ECUDA;
+  zipnn_plan* p = new zipnn_plan();
+  p->kind = 3;
+  p->count = count;
+  cudaGetDevice(&p->device);
+  const size_t tbytes = align_up(sizeof(Job) * (size_t)count, 256);
+  const size_t kbytes = align_up(sizeof(unsigned long long) * (size_t)nseg, 256);
+  cudaError_t e = cudaMalloc(&p->dmem, tbytes + kbytes);
+  if (e != cudaSuccess) return fail(p, e);
+  Job* d_jobs = static_cast<Job*>(p->dmem);
+  auto* tickets = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p->dmem) + tbytes);
+  e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(p, e);
+  zipnn_tuning tu;
+  memset(&tu, 0, sizeof(tu));
+  if (tuning) tu = *tuning;
+  // graph: the copy stream issues the H2D copies segment by segment and marks
+  // each segment's end with an event; the capture stream decodes a segment as
+  // soon as its copies have landed, while the copies of the next ones proceed
+  cudaStream_t sc = nullptr;
+  std::vector<cudaEvent_t> evs((size_t)nseg + 1, nullptr);
+  e = cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking);
+  for (int k = 0; k <= nseg && e == cudaSuccess; k++)
+    e = cudaEventCreateWithFlags(&evs[(size_t)k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = capture(p, [&](cudaStream_t cs) {
+    cudaError_t r = cudaEventRecord(evs[(size_t)nseg], cs);  // fork
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(sc, evs[(size_t)nseg], 0);
+    for (int k = 0; k < nseg && r == cudaSuccess; k++) {
+      const int a = seg_first[k], b = seg_first[k + 1];
+      uint64_t nch = 0, max_chunk = 0;
+      int max_groups = 1, uniform = jobs[a].dtype;
+      bool lanes256 = true;
+      int frac64 = 0;
+      for (int i = a; i < b && r == cudaSuccess; i++) {
+        if (stage_frac64(jobs[i].dtype, jobs[i].flags) > frac64)
+          frac64 = stage_frac64(jobs[i].dtype, jobs[i].flags);
+        r = cudaMemcpyAsync(streams[i].data, h_containers[i], streams[i].nbytes,
+                            cudaMemcpyHostToDevice, sc);
+        nch += jobs[i].n_chunks;
+        if (jobs[i].dtype != uniform) uniform = -1;
+        if (jobs[i].chunk_bytes > max_chunk) max_chunk = jobs[i].chunk_bytes;
+        if ((int)streams[i].n_groups > max_groups) max_groups = (int)streams[i].n_groups;
+        if (jobs[i].lanes % 256) lanes256 = false;
+      }
+      if (r == cudaSuccess) r = cudaEventRecord(evs[(size_t)k], sc);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);
+      if (r == cudaSuccess)
+        r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err, tickets + k,
+                             cs, uniform, max_chunk, lanes256, frac64);
+    }
+    // the last wait above joined the copy stream back into the capture stream
+    return r;
+  });
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (sc) cudaStreamDestroy(sc);
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
   return ZIPNN_OK;

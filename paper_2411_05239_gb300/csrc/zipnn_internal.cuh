@@ -29,6 +29,24 @@ __host__ __device__ inline int elem_size(int dtype) {
 }
 __host__ __device__ inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Decoder stage sizing: the Huffman payload bytes of one chunk to provision
+// for, in 64ths of the chunk.  Model weights: a BF16 exponent group codes to
+// about a third of its half of the chunk (11/64 with margin), an FP16 one (5
+// exponent + 3 fraction bits) to about 70% (24/64), an FP32 one to about a
+// third of its quarter (8/64); U8 streams are unknown (32/64); a BF16 / FP32
+// delta codes two groups, and the stage also holds the second group's table
+// (20/64).  Chunks whose payloads exceed the stage are decoded from global
+// memory instead.
+inline int stage_frac64(int dtype, uint32_t flags) {
+  const bool delta = (flags & 1u) != 0;
+  switch (dtype) {
+    case 0: return delta ? 20 : 11;
+    case 1: return 24;
+    case 2: return delta ? 20 : 8;
+    default: return 32;
+  }
+}
+
 // One tensor of a (possibly batched) call.
 struct Job {
   const uint8_t* src;     // compress: input tensor; decompress: container
@@ -45,7 +63,7 @@ struct Job {
   uint32_t n_chunks;
   int32_t dtype;
   uint32_t flags;
-  uint32_t pad;
+  uint32_t skip;          // compress: skip-ahead probe window (0 = exact decisions)
 };
 
 // Per group-chunk result of the code builder.

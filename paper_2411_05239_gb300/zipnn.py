@@ -32,6 +32,7 @@ EXPORTS = [
     "zipnn_batch_decompress", "zipnn_sync_status", "zipnn_stream_free",
     "zipnn_batch_compress_workspace_size", "zipnn_batch_compress_into",
     "zipnn_plan_decompress", "zipnn_plan_compress", "zipnn_plan_launch", "zipnn_plan_destroy",
+    "zipnn_plan_load", "zipnn_batch_compress_into_ex",
 ]
 
 
@@ -48,6 +49,11 @@ class ZStream(ctypes.Structure):
                 ("lanes", ctypes.c_uint32), ("n_chunks", ctypes.c_uint32),
                 ("n_groups", ctypes.c_uint32), ("owned", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class ZEncodeOptions(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_uint32), ("probe_skip", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class ZTuning(ctypes.Structure):
@@ -96,6 +102,12 @@ def lib() -> ctypes.CDLL:
         "zipnn_plan_compress": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz),
                                  ctypes.POINTER(i32), i32, sz, u32, ctypes.POINTER(vp),
                                  ctypes.POINTER(sz), vp, ctypes.POINTER(vp)], i32),
+        "zipnn_batch_compress_into_ex": ([ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                          ctypes.POINTER(sz), ctypes.POINTER(i32), i32, sz,
+                                          ctypes.POINTER(ZEncodeOptions), ctypes.POINTER(vp),
+                                          ctypes.POINTER(sz), vp, sz, vp, vp], i32),
+        "zipnn_plan_load": ([zsp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                             i32, sz, ctypes.POINTER(ZTuning), ctypes.POINTER(vp)], i32),
         "zipnn_plan_launch": ([vp, vp], i32),
         "zipnn_plan_destroy": ([vp], None),
     }
@@ -325,10 +337,12 @@ class BatchCompressor:
     """Batched compression of a fixed list of CUDA tensors into caller buffers.
 
     Arguments are marshalled once; each call() enqueues the four encoder
-    kernels for all tensors (zipnn_batch_compress_into)."""
+    kernels for all tensors (zipnn_batch_compress_into_ex).  probe_skip > 0
+    applies the skip-ahead probe (Sec. 3.2): after a raw group-chunk the same
+    group of the next probe_skip chunks is stored raw."""
 
     def __init__(self, xs: list[torch.Tensor], chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0,
-                 bases: list[torch.Tensor | None] | None = None):
+                 bases: list[torch.Tensor | None] | None = None, probe_skip: int = 0):
         n = len(xs)
         self.xs = xs
         self.chunk_bytes = chunk_bytes
@@ -349,14 +363,16 @@ class BatchCompressor:
         self._bases = _ptrs(bases) if bases is not None else None
         self._outs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
         self.lanes = lanes
+        self.opts = ZEncodeOptions(lanes, probe_skip, (ctypes.c_uint32 * 2)(0, 0))
         self.n = n
 
     def __call__(self, stream=None) -> None:
-        rc = lib().zipnn_batch_compress_into(self._srcs, self._bases, self._nb, self._dt, self.n,
-                                             self.chunk_bytes, self.lanes, self._outs, self._caps,
-                                             self.ws.data_ptr(), self.ws.numel(),
-                                             self.out_nbytes.data_ptr(), _sp(stream))
-        _check(rc, "zipnn_batch_compress_into")
+        rc = lib().zipnn_batch_compress_into_ex(self._srcs, self._bases, self._nb, self._dt,
+                                                self.n, self.chunk_bytes, ctypes.byref(self.opts),
+                                                self._outs, self._caps, self.ws.data_ptr(),
+                                                self.ws.numel(), self.out_nbytes.data_ptr(),
+                                                _sp(stream))
+        _check(rc, "zipnn_batch_compress_into_ex")
 
     def containers(self) -> list[Compressed]:
         """Wrap the containers written by the last call (synchronises)."""
@@ -398,6 +414,28 @@ def plan_decompress(cs: list[Compressed], outs: list[torch.Tensor],
                                      ctypes.byref(h))
     _check(rc, "zipnn_plan_decompress")
     return Plan(h.value, [cs, outs, bases])
+
+
+def plan_load(cs: list[Compressed], h_containers: list[torch.Tensor], outs: list[torch.Tensor],
+              bases: list[torch.Tensor | None] | None = None, segment_bytes: int = 0,
+              tune: ZTuning | None = None) -> Plan:
+    """Load plan: every launch copies the containers from pinned host buffers
+    (h_containers[i], uint8, c.nbytes bytes) into the device containers cs[i]
+    and decodes them into outs, segment by segment, copies and decoding
+    overlapped, as one CUDA graph."""
+    n = len(cs)
+    for c, h in zip(cs, h_containers):
+        if h.device.type != "cpu" or not h.is_pinned() or h.numel() * h.element_size() < c.nbytes:
+            raise ValueError("plan_load: host containers must be pinned CPU tensors of c.nbytes bytes")
+    arr = (ZStream * n)(*[c.zs for c in cs])
+    hp = (ctypes.c_void_p * n)(*[hc.data_ptr() for hc in h_containers])
+    dsts = _ptrs(outs)
+    bp = _ptrs(bases) if bases is not None else None
+    h = ctypes.c_void_p()
+    rc = lib().zipnn_plan_load(arr, hp, bp, dsts, n, segment_bytes,
+                               ctypes.byref(tune) if tune else None, ctypes.byref(h))
+    _check(rc, "zipnn_plan_load")
+    return Plan(h.value, [cs, h_containers, outs, bases])
 
 
 def plan_compress(bc: BatchCompressor) -> Plan:

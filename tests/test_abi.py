@@ -97,3 +97,28 @@ def test_batch_workspace_query_needs_no_pointers(lib):
     assert lib.zipnn_batch_compress_workspace_size(nb, dt, 3, 16384) > 0
     bad = (ctypes.c_size_t * 1)(3)
     assert lib.zipnn_batch_compress_workspace_size(bad, (ctypes.c_int * 1)(0), 1, 16384) == 0
+
+
+def test_load_plan_validates_before_any_device_work(lib):
+    """zipnn_plan_load rejects missing pointers and bad container descriptions
+    with EINVAL on the host."""
+    vp = ctypes.c_void_p
+    lib.zipnn_plan_load.restype = ctypes.c_int
+    lib.zipnn_plan_load.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_size_t, vp, vp]
+    out = vp()
+    assert lib.zipnn_plan_load(None, None, None, None, 1, 0, None, ctypes.byref(out)) == -1
+    assert lib.zipnn_plan_load(None, None, None, None, 0, 0, None, ctypes.byref(out)) == -1
+
+    class ZStream(ctypes.Structure):
+        _fields_ = [("data", vp), ("nbytes", ctypes.c_uint64), ("orig_nbytes", ctypes.c_uint64),
+                    ("dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                    ("chunk_bytes", ctypes.c_uint32), ("lanes", ctypes.c_uint32),
+                    ("n_chunks", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
+                    ("owned", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    zs = ZStream(0x1008, 96, 128, 0, 0, 4096, 2, 1, 2, 0, 0)        # misaligned device data
+    hp = (vp * 1)(0x2000)
+    dp = (vp * 1)(0x3000)
+    assert lib.zipnn_plan_load(ctypes.byref(zs), hp, None, dp, 1, 0, None, ctypes.byref(out)) == -1
+    zs = ZStream(0x1000, 96, 128, 0, 0, 4096, 2, 3, 2, 0, 0)        # chunk count inconsistent
+    assert lib.zipnn_plan_load(ctypes.byref(zs), hp, None, dp, 1, 0, None, ctypes.byref(out)) == -1
