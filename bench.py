@@ -472,8 +472,9 @@ def run_gb300(args):
 
 def run_tensors(args):
     """Single-configuration modes: plain 8 MiB BF16 (L2-flushed between steps),
-    256 MiB row-scaled FP32, the 3.43 GB checkpoint delta (base + next), and the
-    clean-model tensors (FP32 / FP16 holding BF16 values, Sec. 3.2).
+    256 MiB row-scaled FP32, 256 MiB N(0, 0.02) FP16, the 3.43 GB checkpoint
+    delta (base + next), and the clean-model tensors (FP32 / FP16 holding BF16
+    values, Sec. 3.2).
     Same step as the checkpoint mode: graph-captured compress + decode."""
     from paper_2411_05239_gb300 import workloads as W
     from paper_2411_05239_gb300 import zipnn as Z
@@ -487,6 +488,9 @@ def run_tensors(args):
     elif args.workload == "fp32":
         xs = [W.rowscaled_fp32(device="cuda")]
         name = "rowscaled_fp32_256mib"
+    elif args.workload == "fp16":
+        xs = [W.gaussian(134_217_728, 0.02, 9, torch.float16, device="cuda")]
+        name = "gaussian_fp16_256mib"
     elif args.workload == "clean_fp32":
         xs = [W.clean_fp32_from_bf16(device="cuda")]
         name = "clean_fp32_from_bf16_256mib"
@@ -574,7 +578,7 @@ def run_serve(args):
     from paper_2411_05239_gb300 import zipnn as Z
 
     torch.cuda.set_device(0)
-    trace = W.request_trace(n=args.serve_requests, seed=4)
+    trace = W.request_trace(n=args.serve_requests, seed=4, rate=args.serve_rate)
     maxb = max(r.nbytes for r in trace)
     pools = {}
     for k, (dt, tdt) in enumerate(W.TORCH_DTYPE.items()):
@@ -654,7 +658,7 @@ def run_serve(args):
     line = {
         "metric": METRIC, "value": done_bytes / (t_last - t_first) / 1e9, "unit": "GB/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "served_stream", "requests": len(trace), "rate_per_s": 200,
+        "config": {"workload": "served_stream", "requests": len(trace), "rate_per_s": args.serve_rate,
                    "budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
                    "offered_gb": total / 1e9},
         "served": {"p50_ms": pct(served, 0.5), "p99_ms": pct(served, 0.99),
@@ -689,11 +693,13 @@ def main(argv=None):
     ap.add_argument("--layers", type=int, default=32, help="decoder layers (32 = 8B class)")
     ap.add_argument("--vocab", type=int, default=128256, help="embedding/head rows")
     ap.add_argument("--workload", default="checkpoint",
-                    choices=["checkpoint", "serve", "plain", "fp32", "delta", "clean_fp32",
-                             "clean_fp16"])
+                    choices=["checkpoint", "serve", "plain", "fp32", "fp16", "delta",
+                             "clean_fp32", "clean_fp16"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="request arrivals per second (the served-stream workload: 200)")
     ap.add_argument("--ref-sample-mb", type=int, default=48)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
@@ -701,7 +707,7 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
-    if args.workload in ("plain", "fp32", "delta", "clean_fp32", "clean_fp16"):
+    if args.workload in ("plain", "fp32", "fp16", "delta", "clean_fp32", "clean_fp16"):
         return run_tensors(args)
     return run_gb300(args)
 

@@ -9,11 +9,13 @@
 // batch: its compress requests run as one batched compression (4 kernels for
 // all of them) and its decompress requests as one persistent batched decode,
 // on the slot's stream.  New requests keep being admitted into other slots
-// while earlier batches run, so their work overlaps on the device.  A host
-// callback on the stream stamps the completion time; outputs stay resident
-// (and charged) until the caller releases them.
+// while earlier batches run, so their work overlaps on the device.  A waiter
+// thread per slot blocks on an event recorded after the batch and stamps the
+// completion time; outputs stay resident (and charged) until the caller
+// releases them.
 #include <chrono>
 #include <condition_variable>
+#include <memory>
 #include <cstdint>
 #include <cstring>
 #include <deque>
@@ -99,6 +101,14 @@ struct Slot {
   cudaStream_t st = nullptr;
   Batch* batch = nullptr;
   uint64_t* h_sizes = nullptr;  // pinned, mapped: container sizes of the slot's batch
+  // completion: the scheduler records `ev` after the batch and hands the batch
+  // to this slot's waiter thread, which blocks on the event (lower latency than
+  // a stream host callback) and then queues the batch as finished
+  cudaEvent_t ev = nullptr;
+  Batch* launched = nullptr;
+  bool quit = false;
+  std::unique_ptr<std::condition_variable> wcv;
+  std::thread waiter;
 };
 
 struct Batch {
@@ -122,7 +132,7 @@ struct zipnn_server {
   std::vector<Slot> slots;
   std::deque<Req*> pending;
   std::map<uint64_t, Req*> live;
-  std::deque<Batch*> finished;  // pushed by stream callbacks
+  std::deque<Batch*> finished;  // pushed by the slot waiters
   std::deque<zipnn_completion> done;
   std::mutex mu;
   std::condition_variable cv;
@@ -153,19 +163,27 @@ uint64_t in_bytes(const zipnn_request& r) {
   return r.op == ZIPNN_OP_COMPRESS ? r.input_bytes : r.container.nbytes;
 }
 
-void CUDART_CB on_batch_done(void* p) {
-  Batch* b = static_cast<Batch*>(p);
-  b->t_done = now_s();
-  zipnn_server* s = b->srv;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
+// Waiter of slot si: waits for each batch launched on the slot to complete.
+void slot_waiter(zipnn_server* s, int si) {
+  cudaSetDevice(s->device);
+  Slot& sl = s->slots[(size_t)si];
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    sl.wcv->wait(lk, [&] { return sl.launched != nullptr || sl.quit; });
+    if (!sl.launched) break;  // quit with nothing in flight
+    Batch* b = sl.launched;
+    sl.launched = nullptr;
+    lk.unlock();
+    cudaEventSynchronize(sl.ev);
+    b->t_done = now_s();
+    lk.lock();
     s->finished.push_back(b);
+    s->cv.notify_all();
   }
-  s->cv.notify_all();
 }
 
 // Launch one batch on slot `si` (called without the lock; the batch belongs to
-// the scheduler until its stream callback fires).
+// the scheduler until the slot's waiter has seen it complete).
 void launch_batch(zipnn_server* s, int si, Batch* b) {
   cudaStream_t st = s->slots[si].st;
   std::vector<const void*> csrc, cbase;
@@ -202,7 +220,13 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
     rc = zipnn_batch_decompress(dstr.data(), dbase.data(), ddst.data(), (int)dstr.size(), nullptr,
                                 st);
   b->launch_status = rc;
-  cudaLaunchHostFunc(st, on_batch_done, b);
+  Slot& sl = s->slots[(size_t)si];
+  cudaEventRecord(sl.ev, st);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    sl.launched = b;
+  }
+  sl.wcv->notify_one();
 }
 
 void finish_batch(zipnn_server* s, Batch* b) {
@@ -347,7 +371,7 @@ void scheduler(zipnn_server* s) {
         s->inflight += b->reqs.size();
         s->stats.batches++;
         if (b->reqs.size() > s->stats.max_batch) s->stats.max_batch = b->reqs.size();
-        // launch without the lock: submitters and the stream callbacks stay free
+        // launch without the lock: submitters and the slot waiters stay free
         lk.unlock();
         launch_batch(s, free_slot, b);
         lk.lock();
@@ -379,10 +403,13 @@ zipnn_status zipnn_server_create(uint64_t budget_bytes, int slots, zipnn_server*
   s->slots.resize((size_t)slots);
   for (auto& sl : s->slots) {
     cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
-    if (cudaHostAlloc(reinterpret_cast<void**>(&sl.h_sizes), sizeof(uint64_t) * kMaxBatch,
-                      cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    sl.wcv.reset(new std::condition_variable());
+    if (!sl.ev || cudaHostAlloc(reinterpret_cast<void**>(&sl.h_sizes), sizeof(uint64_t) * kMaxBatch,
+                                cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
       for (auto& s2 : s->slots) {
         if (s2.h_sizes) cudaFreeHost(s2.h_sizes);
+        if (s2.ev) cudaEventDestroy(s2.ev);
         if (s2.st) cudaStreamDestroy(s2.st);
       }
       cudaFree(s->arena_base);
@@ -390,6 +417,8 @@ zipnn_status zipnn_server_create(uint64_t budget_bytes, int slots, zipnn_server*
       return ZIPNN_ENOMEM;
     }
   }
+  for (size_t i = 0; i < s->slots.size(); i++)
+    s->slots[i].waiter = std::thread(slot_waiter, s, (int)i);
   s->sched = std::thread(scheduler, s);
   *out = s;
   return ZIPNN_OK;
@@ -481,9 +510,18 @@ void zipnn_server_destroy(zipnn_server* s) {
     s->stop = true;
   }
   s->cv.notify_all();
-  if (s->sched.joinable()) s->sched.join();
+  if (s->sched.joinable()) s->sched.join();  // returns once no batch is in flight
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& sl : s->slots) sl.quit = true;
+  }
+  for (auto& sl : s->slots) {
+    sl.wcv->notify_all();
+    if (sl.waiter.joinable()) sl.waiter.join();
+  }
   for (auto& sl : s->slots) {
     cudaStreamSynchronize(sl.st);
+    cudaEventDestroy(sl.ev);
     cudaStreamDestroy(sl.st);
     cudaFreeHost(sl.h_sizes);
   }
