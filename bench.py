@@ -374,8 +374,20 @@ def run_gb300(args):
         torch.cuda.synchronize()
         barrier(world)
         e2e_s = all_max([(time.perf_counter() - t0) / args.e2e_steps], world)[0]
+        # the box's pinned H2D bandwidth, for reading the load path against it
+        probe = h_cont[0][: 1 << 30]
+        dprobe = torch.empty(probe.numel(), dtype=torch.uint8, device=dev)
+        dprobe.copy_(probe, non_blocking=True)
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        for _ in range(3):
+            dprobe.copy_(probe, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * probe.numel() / (time.perf_counter() - tp) / 1e9
+        del dprobe
         e2e = {"value": world * orig / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": comp_bytes, "d2h_bytes_per_step": 4,
+               "pinned_h2d_gbs": h2d_gbs,
                "steps": args.e2e_steps, "ms_per_step": e2e_s * 1e3,
                "path": "zipnn_plan_load: pinned host containers -> H2D (copy stream) overlapped "
                        "with per-segment persistent decode into HBM -> zipnn_sync_status (4 B D2H)",

@@ -70,6 +70,7 @@
 #define OR_HUFF  1
 #define OR_ZERO  2
 #define OR_CONST 3
+#define OR_SPARSE 4
 
 #define OR_MAXLEN     12      /* code length limit */
 #define OR_HDR_BYTES  64
@@ -326,12 +327,68 @@ size_t or_bound(size_t nbytes, int dtype, size_t chunk_bytes) {
  * streams stored raw):
  *   no symbol, or only the symbol 0x00   -> ZERO   (no payload)
  *   a single distinct non-zero symbol     -> CONST  (the byte in the entry)
- *   else Huffman size h = align4(12+nz) + 4(T-1) + 4*ceil(bits/32):
- *        HUFF if h + floor(m/64) < m, else RAW (payload = the m bytes).
+ *   else two coded candidates:
+ *     HUFF: a code for the histogram of all m symbols; size
+ *           h = align4(12+nz) + 4(T-1) + 4*ceil(bits/32);
+ *     SPARSE (only if some vector is all zero): a code for the histogram of
+ *           the symbols outside all-zero vectors; size
+ *           s = align4(12+nz') + 4*ceil(nv/32) + 4(T-1) + 4*ceil(bits'/32)
+ *           (the second term is a bitmap of the vectors holding a non-zero
+ *           symbol, bit v%32 of little-endian word v/32);
+ *   a candidate qualifies when its size + floor(m/64) < m; SPARSE is taken
+ *   when it qualifies and is smaller than a qualifying HUFF, HUFF when it
+ *   qualifies, else RAW (payload = the m bytes).
+ * SPARSE stands in for the paper's switch to Zstd on delta chunks that are
+ * mostly zeros (Sec. 4.2, "Auto Detection"): Huffman alone cannot code a
+ * symbol in less than one bit.
  * Sub-stream t (0 <= t < T) holds the vectors v = t, t+T, ... of V symbols
- * each (symbol i is in vector i / V); its start bit is stored for t >= 1.
+ * each (symbol i is in vector i / V; SPARSE leaves out the all-zero vectors);
+ * its start bit is stored for t >= 1.
  * Returns the payload size written to out (capacity >= m + 1100 bytes).     */
 typedef struct { int mode; int value; size_t size; } or_group_result;
+
+/* table bytes: BITS[12] then the symbols ordered by (length, symbol) */
+static size_t write_table(const uint8_t* len, uint8_t* out) {
+    int k = 12;
+    for (int l = 1; l <= OR_MAXLEN; l++) {
+        int cnt = 0;
+        for (int s = 0; s < 256; s++)
+            if (len[s] == l) { out[k++] = (uint8_t)s; cnt++; }
+        out[l - 1] = (uint8_t)cnt;
+    }
+    return (size_t)k;
+}
+
+/* is vector v (symbols v*V .. min(m, v*V+V)-1) all zero? */
+static int vector_is_zero(const uint8_t* sym, size_t m, uint32_t V, size_t v) {
+    for (size_t i = v * V; i < m && i < (v + 1) * V; i++)
+        if (sym[i]) return 0;
+    return 1;
+}
+
+/* sub-stream start table at offs and MSB-first words at bs; with skip_zero,
+ * all-zero vectors contribute no codes */
+static void write_streams(const uint8_t* sym, size_t m, uint32_t T, uint32_t V,
+                          const uint32_t* code, const uint8_t* len, int skip_zero,
+                          size_t nwords, uint8_t* offs, uint8_t* bs) {
+    uint32_t* words = (uint32_t*)calloc(nwords + 1, sizeof(uint32_t));
+    size_t nv = (m + V - 1) / V;
+    uint64_t pos = 0;
+    for (uint32_t t = 0; t < T; t++) {
+        if (t > 0) put_u32(offs + 4u * (t - 1u), (uint32_t)pos);
+        for (size_t v = t; v < nv; v += T) {
+            if (skip_zero && vector_is_zero(sym, m, V, v)) continue;
+            for (uint32_t j = 0; j < V; j++) {
+                size_t i = v * V + j;
+                if (i >= m) break;
+                put_bits(words, pos, code[sym[i]], len[sym[i]]);
+                pos += len[sym[i]];
+            }
+        }
+    }
+    for (size_t w = 0; w < nwords; w++) put_u32(bs + 4 * w, words[w]);
+    free(words);
+}
 
 static or_group_result encode_group(const uint8_t* sym, size_t m, uint32_t T, uint32_t V,
                                    uint8_t* out) {
@@ -344,6 +401,7 @@ static or_group_result encode_group(const uint8_t* sym, size_t m, uint32_t T, ui
     if (nz == 0 || (nz == 1 && last == 0)) { r.mode = OR_ZERO; return r; }
     if (nz == 1) { r.mode = OR_CONST; r.value = last; return r; }
 
+    /* HUFF candidate */
     uint8_t len[256];
     uint32_t code[256];
     or_code_lengths(hist, len);
@@ -352,43 +410,61 @@ static or_group_result encode_group(const uint8_t* sym, size_t m, uint32_t T, ui
     for (int s = 0; s < 256; s++) bits += (uint64_t)hist[s] * len[s];
     size_t h = (size_t)align_up(12u + (unsigned)nz, 4);
     size_t nwords = (size_t)((bits + 31) / 32);
-    size_t hsize = h + 4u * (T - 1u) + 4u * nwords;
-    if (!(hsize + (m >> 6) < m)) {
+    size_t s_huff = h + 4u * (T - 1u) + 4u * nwords;
+    int huff_ok = s_huff + (m >> 6) < m;
+
+    /* SPARSE candidate: the zeros of all-zero vectors leave the histogram */
+    size_t nv = (m + V - 1) / V, zsyms = 0, zvec = 0;
+    for (size_t v = 0; v < nv; v++)
+        if (vector_is_zero(sym, m, V, v)) {
+            zvec++;
+            zsyms += (v * V + V <= m) ? V : m - v * V;
+        }
+    int sparse_ok = 0;
+    uint32_t hist2[256];
+    uint8_t len2[256];
+    uint32_t code2[256];
+    size_t h2 = 0, nbw = (nv + 31) / 32, nwords2 = 0, s_sparse = 0;
+    if (zvec > 0) {
+        memcpy(hist2, hist, sizeof(hist2));
+        hist2[0] -= (uint32_t)zsyms;
+        int nz2 = 0;
+        for (int s = 0; s < 256; s++) nz2 += hist2[s] > 0;
+        if (nz2 >= 2) {
+            or_code_lengths(hist2, len2);
+            or_canonical_codes(len2, code2);
+            uint64_t bits2 = 0;
+            for (int s = 0; s < 256; s++) bits2 += (uint64_t)hist2[s] * len2[s];
+            h2 = (size_t)align_up(12u + (unsigned)nz2, 4);
+            nwords2 = (size_t)((bits2 + 31) / 32);
+            s_sparse = h2 + 4u * nbw + 4u * (T - 1u) + 4u * nwords2;
+            sparse_ok = s_sparse + (m >> 6) < m;
+        }
+    }
+
+    if (sparse_ok && (!huff_ok || s_sparse < s_huff)) {
+        memset(out, 0, s_sparse);
+        write_table(len2, out);
+        uint8_t* bitmap = out + h2;
+        for (size_t v = 0; v < nv; v++)
+            if (!vector_is_zero(sym, m, V, v)) bitmap[v / 8] |= (uint8_t)(1u << (v % 8));
+        write_streams(sym, m, T, V, code2, len2, 1, nwords2, out + h2 + 4u * nbw,
+                      out + h2 + 4u * nbw + 4u * (T - 1u));
+        r.mode = OR_SPARSE;
+        r.size = s_sparse;
+        return r;
+    }
+    if (!huff_ok) {
         r.mode = OR_RAW;
         r.size = m;
         memcpy(out, sym, m);
         return r;
     }
-
-    /* table: counts per length, then symbols ordered by (length, symbol) */
-    memset(out, 0, hsize);
-    int k = 12;
-    for (int l = 1; l <= OR_MAXLEN; l++) {
-        int cnt = 0;
-        for (int s = 0; s < 256; s++)
-            if (len[s] == l) { out[k++] = (uint8_t)s; cnt++; }
-        out[l - 1] = (uint8_t)cnt;
-    }
-    uint8_t* offs = out + h;
-    uint32_t* words = (uint32_t*)calloc(nwords + 1, sizeof(uint32_t));
-    size_t nv = (m + V - 1) / V;
-    uint64_t pos = 0;
-    for (uint32_t t = 0; t < T; t++) {
-        if (t > 0) put_u32(offs + 4u * (t - 1u), (uint32_t)pos);
-        for (size_t v = t; v < nv; v += T) {
-            for (uint32_t j = 0; j < V; j++) {
-                size_t i = v * V + j;
-                if (i >= m) break;
-                put_bits(words, pos, code[sym[i]], len[sym[i]]);
-                pos += len[sym[i]];
-            }
-        }
-    }
-    uint8_t* bs = out + h + 4u * (T - 1u);
-    for (size_t w = 0; w < nwords; w++) put_u32(bs + 4 * w, words[w]);
-    free(words);
+    memset(out, 0, s_huff);
+    write_table(len, out);
+    write_streams(sym, m, T, V, code, len, 0, nwords, out + h, out + h + 4u * (T - 1u));
     r.mode = OR_HUFF;
-    r.size = hsize;
+    r.size = s_huff;
     return r;
 }
 
@@ -528,7 +604,7 @@ int or_delta(const uint8_t* a, const uint8_t* b, size_t nbytes, int dtype, size_
  * rule: after reading l bits the value c is a code of length l iff
  * first[l] <= c < first[l] + count[l].                                       */
 static int decode_group(const uint8_t* p, size_t size, size_t m, uint32_t T, uint32_t V,
-                        uint8_t* sym) {
+                        int sparse, uint8_t* sym) {
     if (size < 12) return OR_ECORRUPT;
     uint32_t count[OR_MAXLEN + 1] = {0};
     int nz = 0;
@@ -538,7 +614,13 @@ static int decode_group(const uint8_t* p, size_t size, size_t m, uint32_t T, uin
     for (int l = 1; l <= OR_MAXLEN; l++) kraft += (uint64_t)count[l] << (OR_MAXLEN - l);
     if (kraft > (1u << OR_MAXLEN)) return OR_ECORRUPT;
     size_t h = (size_t)align_up(12u + (unsigned)nz, 4);
+    size_t nv = (m + V - 1) / V;
+    const uint8_t* bitmap = p + h;                 /* SPARSE: one bit per vector */
+    if (sparse) h += 4u * ((nv + 31) / 32);
     if (size < h + 4u * (T - 1u) || (size - h - 4u * (T - 1u)) % 4) return OR_ECORRUPT;
+    if (sparse)
+        for (size_t v = nv; v < (nv + 31) / 32 * 32; v++)
+            if (bitmap[v / 8] >> (v % 8) & 1u) return OR_ECORRUPT;   /* bits past nv */
     const uint8_t* symbols = p + 12;
     uint8_t seen[256] = {0};
     for (int k = 0; k < nz; k++) {
@@ -556,12 +638,15 @@ static int decode_group(const uint8_t* p, size_t size, size_t m, uint32_t T, uin
     const uint8_t* offs = p + h;
     const uint8_t* bs = p + h + 4u * (T - 1u);
     uint64_t total_bits = (uint64_t)(size - h - 4u * (T - 1u)) * 8u;
-    size_t nv = (m + V - 1) / V;
     uint64_t pos = 0;
     for (uint32_t t = 0; t < T; t++) {
         uint64_t start = t ? get_u32(offs + 4u * (t - 1u)) : 0;
         if (start != pos) return OR_ECORRUPT;      /* sub-streams are contiguous */
         for (size_t v = t; v < nv; v += T) {
+            if (sparse && !(bitmap[v / 8] >> (v % 8) & 1u)) {   /* all-zero vector */
+                for (size_t i = v * V; i < m && i < (v + 1) * V; i++) sym[i] = 0;
+                continue;
+            }
             for (uint32_t j = 0; j < V; j++) {
                 size_t i = v * V + j;
                 if (i >= m) break;
@@ -656,9 +741,9 @@ int or_decompress(const uint8_t* s, size_t n, const uint8_t* base, uint8_t* dst,
             } else if (mode == OR_RAW) {
                 if (size != m || value) { free(planes); return OR_ECORRUPT; }
                 memcpy(dstp, p, m);
-            } else if (mode == OR_HUFF) {
+            } else if (mode == OR_HUFF || mode == OR_SPARSE) {
                 if (value) { free(planes); return OR_ECORRUPT; }
-                rc = decode_group(p, size, m, T, V, dstp);
+                rc = decode_group(p, size, m, T, V, mode == OR_SPARSE, dstp);
                 if (rc) { free(planes); return rc; }
             } else {
                 free(planes);

@@ -1,10 +1,11 @@
 """A second, pure-Python reader of the container, written from the format
 specification alone (test helper; shares nothing with oracle/ or the CUDA path).
 
-It parses the header, the chunk map and every payload, decodes HUFF sub-streams
-with a dictionary of (length, code) -> symbol built from the code-length counts,
-and reassembles elements from their byte groups (ZipNN Sec. 3.1, Sec. 3.2,
-Sec. 5.1).  Slow; only for small inputs.
+It parses the header, the chunk map and every payload, decodes HUFF (and
+SPARSE: the same, after a bitmap of the vectors that hold a non-zero symbol)
+sub-streams with a dictionary of (length, code) -> symbol built from the
+code-length counts, and reassembles elements from their byte groups (ZipNN
+Sec. 3.1, Sec. 3.2, Sec. 5.1).  Slow; only for small inputs.
 """
 from __future__ import annotations
 
@@ -27,11 +28,18 @@ def parse(stream: bytes) -> dict:
                 chunks=nch, payload=P, total=total, entries=entries)
 
 
-def _decode_huff(p: bytes, m: int, T: int, V: int) -> bytes:
+def _decode_huff(p: bytes, m: int, T: int, V: int, sparse: bool = False) -> bytes:
     counts = list(p[:12])
     nz = sum(counts)
     syms = p[12:12 + nz]
     h = (12 + nz + 3) // 4 * 4
+    nv = (m + V - 1) // V
+    nonzero = [True] * nv
+    if sparse:
+        nbw = (nv + 31) // 32
+        bm = int.from_bytes(p[h:h + 4 * nbw], "little")
+        nonzero = [bool(bm >> v & 1) for v in range(nv)]
+        h += 4 * nbw
     starts = [0] + [struct.unpack_from("<I", p, h + 4 * k)[0] for k in range(T - 1)]
     bs = p[h + 4 * (T - 1):]
     # canonical assignment: lengths ascending, symbols in table order
@@ -46,10 +54,11 @@ def _decode_huff(p: bytes, m: int, T: int, V: int) -> bytes:
     bits = "".join(format(struct.unpack_from("<I", bs, 4 * w)[0], "032b")
                    for w in range(len(bs) // 4))
     out = bytearray(m)
-    nv = (m + V - 1) // V
     for t in range(T):
         pos = starts[t]
         for v in range(t, nv, T):
+            if not nonzero[v]:
+                continue                       # all-zero vector: no codes
             for j in range(V):
                 i = v * V + j
                 if i >= m:
@@ -95,8 +104,12 @@ def decode(stream: bytes, base: bytes | None = None) -> bytes:
                 planes.append(_decode_huff(p, m, h["lanes"], V))
             elif mode == 2:
                 planes.append(bytes(m))
-            else:
+            elif mode == 3:
                 planes.append(bytes([value]) * m)
+            elif mode == 4:
+                planes.append(_decode_huff(p, m, h["lanes"], V, sparse=True))
+            else:
+                raise ValueError(f"unknown mode {mode}")
         out += _merge(h["dtype"], planes, m)
     if h["flags"] & 1:
         out = bytearray(a ^ b for a, b in zip(out, base))

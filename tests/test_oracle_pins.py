@@ -288,10 +288,11 @@ def _load_golden(name):
     return fields, bytes.fromhex("".join(stream))
 
 
-@pytest.mark.parametrize("name", ["bf16_two_symbols.txt", "fp32_four_groups.txt"])
+@pytest.mark.parametrize("name", ["bf16_two_symbols.txt", "fp32_four_groups.txt",
+                                  "u8_sparse_vectors.txt"])
 def test_golden_containers(name):
     f, want = _load_golden(name)
-    data = np.frombuffer(bytes.fromhex(f["input"]), dtype=np.uint8)
+    data = np.frombuffer(bytes.fromhex(f["input"].replace(" ", "")), dtype=np.uint8)
     got = O.compress(data, int(f["dtype"]), int(f["chunk_bytes"]), int(f["lanes"]))
     assert got.hex() == want.hex()
     assert np.array_equal(O.decompress(want), data)
