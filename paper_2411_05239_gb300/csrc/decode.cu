@@ -123,6 +123,7 @@ struct ChunkInfo {
   uint64_t payload[4];      // byte offset of the payload within the container
   uint64_t bs[4];           // bitstream offset within the payload (HUFF)
   uint64_t offs[4];         // start-bit table offset within the payload (HUFF)
+  uint64_t bmo[4];          // vector bitmap offset within the payload (SPARSE)
   uint32_t staged[4];       // stage offset of the payload, or ~0 if read from global
   uint32_t stage_bytes;
   uint32_t bad;
@@ -134,6 +135,10 @@ struct Smem {
   uint32_t* lut_ptr[4];  // pair table of each Huffman group
   unsigned long long chunk;
 };
+
+// Groups carried as Huffman sub-streams: HUFF, and SPARSE (the same after a
+// bitmap of the vectors that hold a non-zero symbol).
+__device__ __forceinline__ bool coded_mode(uint32_t m) { return m == kHuff || m == kSparse; }
 
 __device__ __forceinline__ uint8_t tab_byte(const GroupTab& t, int i) {
   return (uint8_t)(t.words[i >> 2] >> (8 * (i & 3)));
@@ -303,8 +308,8 @@ struct Staging {
 // sub-streams, which gives the scheduler instruction-level parallelism); each
 // vector is merged with the raw / constant groups and stored.
 template <int DT, int W, class BR, bool STAGED, int NS>
-__device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
-                                            uint32_t* err) {
+__device__ __noinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
+                                         uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
@@ -318,6 +323,7 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
   uint32_t mode[G], cval[G], nwords[G], offs[G], bsoff[G];
   const uint8_t* rawp[G];
   const uint8_t* pay[G];
+  const uint32_t* bmp[G];   // SPARSE: bitmap of the vectors holding a non-zero symbol
   uint32_t lut[G];  // shared-window addresses of the pair tables
 #pragma unroll
   for (int g = 0; g < G; g++) {
@@ -329,6 +335,7 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
     offs[g] = (uint32_t)CI.offs[g];
     bsoff[g] = (uint32_t)CI.bs[g];
     lut[g] = smem_u32(S.lut_ptr[g]);
+    bmp[g] = reinterpret_cast<const uint32_t*>(pay[g] + (uint32_t)CI.bmo[g]);
   }
   uint32_t bad = 0;
   for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
@@ -342,7 +349,7 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
       const uint32_t t = act[j] ? tt[j] : 0u;
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        if (mode[g] != kHuff) continue;
+        if (mode[g] != kHuff && mode[g] != kSparse) continue;
         uint32_t start = 0;
         if (t) start = STAGED ? *reinterpret_cast<const uint32_t*>(pay[g] + offs[g] + 4u * (t - 1))
                               : rd_u32(pay[g] + offs[g] + 4u * (t - 1));
@@ -396,16 +403,29 @@ __device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, S
       }
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        if (mode[g] == kHuff) {
+        if (mode[g] == kHuff || mode[g] == kSparse) {
           const GroupTab& tb = S.tab[g];
           const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+          // SPARSE: a vector whose bit is clear is all zero and has no codes
+          bool coded[NS];
+#pragma unroll
+          for (int j = 0; j < NS; j++) {
+            coded[j] = true;
+            if (mode[g] == kSparse && live[j]) {
+              const uint32_t wi = vv[j] >> 5;
+              const uint32_t word = STAGED ? bmp[g][wi] : __ldg(bmp[g] + wi);
+              coded[j] = (word >> (vv[j] & 31u)) & 1u;
+            }
+          }
 #pragma unroll
           for (int q = 0; q < V / 4; q++) {
             uint32_t a[NS], b[NS];
 #pragma unroll
-            for (int j = 0; j < NS; j++) a[j] = two_symbols<W>(br[j][g], lut[g], tb, syms, bad);
+            for (int j = 0; j < NS; j++)
+              a[j] = coded[j] ? two_symbols<W>(br[j][g], lut[g], tb, syms, bad) : 0u;
 #pragma unroll
-            for (int j = 0; j < NS; j++) b[j] = two_symbols<W>(br[j][g], lut[g], tb, syms, bad);
+            for (int j = 0; j < NS; j++)
+              b[j] = coded[j] ? two_symbols<W>(br[j][g], lut[g], tb, syms, bad) : 0u;
 #pragma unroll
             for (int j = 0; j < NS; j++) gw[j][g][q] = a[j] | (b[j] << 16);
           }
@@ -629,10 +649,10 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     const uint32_t size = e.z, mode = e.w & 0xFFu, value = (e.w >> 8) & 0xFFu;
     uint32_t bad = (e.w >> 16) != 0;
     const uint64_t avail = J.stream_bytes > P ? J.stream_bytes - P : 0;
-    if (mode > kConst || po > avail || align_up(size, 16) > avail - po || (po & 15)) bad = 1;
+    if (mode > kSparse || po > avail || align_up(size, 16) > avail - po || (po & 15)) bad = 1;
     if (mode == kRaw && size != m) bad = 1;
     if ((mode == kZero || mode == kConst) && size != 0) bad = 1;
-    if (mode == kHuff && size < 12) bad = 1;
+    if ((mode == kHuff || mode == kSparse) && size < 12) bad = 1;
     CI.mode[tid] = bad ? kZero : mode;
     CI.value[tid] = value;
     CI.size[tid] = size;
@@ -648,7 +668,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   if (tid == 0) {
     uint32_t nhuff = 0, pay_total = 0;
     for (int g = 0; g < G; g++)
-      if (CI.mode[g] == kHuff) {
+      if (coded_mode(CI.mode[g])) {
         nhuff++;
         pay_total += (uint32_t)align_up(CI.size[g], 16);
       }
@@ -658,7 +678,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     for (int g = 0; g < G; g++) {
       CI.staged[g] = 0xFFFFFFFFu;
       S.lut_ptr[g] = lut0;
-      if (CI.mode[g] != kHuff) continue;
+      if (!coded_mode(CI.mode[g])) continue;
       if (stage_payloads) {
         CI.staged[g] = used;
         used += (uint32_t)align_up(CI.size[g], 16);
@@ -668,7 +688,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     CI.stage_bytes = used;
     uint32_t lo = (used + 32 + 127) & ~127u;
     for (int g = 0; g < G; g++)
-      if (CI.mode[g] == kHuff && S.lut_ptr[g] == nullptr) {
+      if (coded_mode(CI.mode[g]) && S.lut_ptr[g] == nullptr) {
         if (lo + kLutBytes > stg.cap) {  // cannot happen with the launch's sizing; fail closed
           CI.bad = 1;
           lo = 0;
@@ -688,14 +708,14 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   // 3a. table bytes of every Huffman group (word loads, clamped to the payload)
 #pragma unroll
   for (int g = 0; g < G; g++) {
-    if (CI.mode[g] != kHuff) continue;
+    if (!coded_mode(CI.mode[g])) continue;
     const uint8_t* p = cont + CI.payload[g];
     for (int i = tid; i < 68; i += nthr)
       S.tab[g].words[i] = (4u * i + 4u <= CI.size[g]) ? rd_u32(p + 4 * i) : 0u;
   }
   __syncthreads();
   // 3b. canonical limits (thread g), validation
-  if (tid < G && CI.mode[tid] == kHuff) {
+  if (tid < G && coded_mode(CI.mode[tid])) {
     GroupTab& t = S.tab[tid];
     uint32_t nz = 0, kraft = 0, code = 0, idx = 0, prevc = 0;
     t.lim[0] = 0;
@@ -712,14 +732,18 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     }
     t.lim[kMaxLen + 1] = 0xFFFFFFFFu;
     const uint64_t h = align_up(12 + nz, 4);
+    // SPARSE: the vector bitmap (one bit per 16-byte vector of the chunk)
+    // sits between the table and the start-bit table
+    const uint64_t bmb = CI.mode[tid] == kSparse ? 4ull * ((nb + 511) / 512) : 0ull;
     const uint64_t size = CI.size[tid];
-    if (nz < 2 || nz > 256 || kraft > (uint32_t)kLutSize || size < h + 4ull * (T - 1) ||
-        (size - h - 4ull * (T - 1)) % 4) {
+    const uint64_t hdr = h + bmb + 4ull * (T - 1);
+    if (nz < 2 || nz > 256 || kraft > (uint32_t)kLutSize || size < hdr || (size - hdr) % 4) {
       atomicOr(&CI.bad, 1u);
     } else {
-      CI.offs[tid] = h;
-      CI.bs[tid] = h + 4ull * (T - 1);
-      CI.nwords[tid] = (uint32_t)((size - h - 4ull * (T - 1)) / 4);
+      CI.bmo[tid] = h;
+      CI.offs[tid] = h + bmb;
+      CI.bs[tid] = hdr;
+      CI.nwords[tid] = (uint32_t)((size - hdr) / 4);
     }
   }
   __syncthreads();
@@ -731,7 +755,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     bool ok = CI.mode[0] == kHuff && CI.staged[0] != 0xFFFFFFFFu && nb == J.chunk_bytes &&
               ((uint32_t)(nb / 16) % T) == 0;
 #pragma unroll
-    for (int g = 1; g < G; g++) ok = ok && CI.mode[g] != kHuff;
+    for (int g = 1; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
     if (ok) fast = (T % (2u * nthr) == 0) ? 2 : ((T % (uint32_t)nthr == 0) ? 1 : 0);
   }
   const bool rot = fast != 0 && DT != ZIPNN_U8;
@@ -742,7 +766,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   if (!bad_tab) {
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      if (CI.mode[g] != kHuff) continue;
+      if (!coded_mode(CI.mode[g])) continue;
       const GroupTab& t = S.tab[g];
       const uint8_t* syms = reinterpret_cast<const uint8_t*>(t.words) + 12;
       uint32_t limw[W + 1];

@@ -121,7 +121,8 @@ __device__ __forceinline__ void hist16_word(uint32_t hl, uint32_t w) {
 }
 
 template <int DT>
-__device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist) {
+__device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist,
+                           uint32_t* __restrict__ zsyms) {
   constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
   constexpr int V = 16 / (DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2));
   constexpr int ES = 16 / V;
@@ -131,8 +132,12 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   const uint8_t* src = J.src + off;
   const uint8_t* base = J.base ? J.base + off : nullptr;
 
-  for (int i = tid; i < G * 256 * 32; i += kHistThreads) sh[i] = 0;
+  uint32_t* zcnt = sh + G * 256 * 32;  // per group: symbols inside all-zero vectors
+  for (int i = tid; i < G * 256 * 32 + G; i += kHistThreads) sh[i] = 0;
   __syncthreads();
+  uint32_t zc[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) zc[g] = 0;
   uint32_t* hl = sh + lane;
   const uint64_t nvec = (nb + 15) / 16;
   const uint64_t m = nb / ES;
@@ -164,6 +169,9 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
         hist16_word(hls, a[u].y);
         hist16_word(hls, a[u].z);
         hist16_word(hls, a[u].w);
+        const uint32_t any = a[u].x | a[u].y | a[u].z | a[u].w;
+        if (!(any & 0x7F807F80u)) zc[0] += 8;       // 8 zero exponent bytes
+        if (!(any & 0x807F807Fu)) zc[1 % G] += 8;   // 8 zero sign + fraction bytes
       }
     }
     vstart = nfast + tid;
@@ -182,6 +190,13 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
       uint32_t g[4][4];
       split_vec(DT, a[u], g);
       const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
+#pragma unroll
+      for (int gg = 0; gg < G; gg++) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int q = 0; q < V / 4; q++) any |= g[gg][q];
+        if (!any) zc[gg] += (uint32_t)valid;   // bytes past the tail were loaded as zero
+      }
       if (valid == V) {
 #pragma unroll
         for (int gg = 0; gg < G; gg++)
@@ -198,7 +213,14 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
       }
     }
   }
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    uint32_t z = zc[g];
+    for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    if (lane == 0 && z) atomicAdd(&zcnt[g], z);
+  }
   __syncthreads();
+  if (tid < G) zsyms[J.gc_begin + c * G + tid] = zcnt[tid];
   // bin totals: thread b sums the 32 lane counters of bin b (rotated start so
   // the 32 threads of a warp read 32 different banks)
   for (int b = tid; b < G * 256; b += kHistThreads) {
@@ -210,25 +232,26 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
 }
 
 template <int DTS>
-__global__ void __launch_bounds__(kHistThreads) k_hist(JobRef jr, uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(kHistThreads)
+k_hist(JobRef jr, uint32_t* __restrict__ hist, uint32_t* __restrict__ zsyms) {
   extern __shared__ uint32_t hsm[];
   const uint64_t chunk = blockIdx.x;
   const int j = find_job_chunk(jr, chunk);
   const Job& J = job_at(jr, j);
   const uint64_t c = chunk - J.chunk_begin;
   if (DTS >= 0) {
-    hist_chunk<(DTS < 0 ? 0 : DTS)>(J, c, hsm, hist);
+    hist_chunk<(DTS < 0 ? 0 : DTS)>(J, c, hsm, hist, zsyms);
     return;
   }
   switch (J.dtype) {
-    case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, hist); break;
-    case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, hist); break;
-    case ZIPNN_FP32: hist_chunk<ZIPNN_FP32>(J, c, hsm, hist); break;
-    default: hist_chunk<ZIPNN_U8>(J, c, hsm, hist); break;
+    case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, hist, zsyms); break;
+    case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, hist, zsyms); break;
+    case ZIPNN_FP32: hist_chunk<ZIPNN_FP32>(J, c, hsm, hist, zsyms); break;
+    default: hist_chunk<ZIPNN_U8>(J, c, hsm, hist, zsyms); break;
   }
 }
 
-static int hist_smem_bytes(int max_groups) { return max_groups * 256 * 32 * 4; }
+static int hist_smem_bytes(int max_groups) { return max_groups * (256 * 32 + 1) * 4; }
 
 // ---------------------------------------------------------------------------
 // k_build: one warp per group-chunk.
@@ -260,74 +283,26 @@ __device__ __forceinline__ int lower_bound_u32(const uint32_t* a, int n, uint32_
   return lo;
 }
 
-__global__ void __launch_bounds__(kBuildWarps * 32)
-k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
-        uint32_t* __restrict__ codes, uint8_t* __restrict__ tabs, GcMeta* __restrict__ meta) {
-  __shared__ BuildSmem smem[kBuildWarps];
-  const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5;
-  const uint64_t gc = (uint64_t)blockIdx.x * kBuildWarps + wid;
-  if (gc >= ngc_total) return;
-  BuildSmem& S = smem[wid];
+// Shannon bound: any prefix code spends >= sum c log2(n / c) bits on counts c
+// summing to n.  True when even that many bits (plus `fixed` bytes) cannot
+// qualify against the raw size m, or, with have_best, cannot beat `best`.
+__device__ bool bound_rules_out(const uint32_t cnt[8], uint32_t n, uint64_t fixed, uint32_t m,
+                                bool have_best, uint64_t best) {
+  float part = 0.f;
+  const float lm = log2f((float)n);
+  for (int k = 0; k < 8; k++)
+    if (cnt[k]) part += (float)cnt[k] * (lm - log2f((float)cnt[k]));
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  const float lower = part * (1.0f - 1e-4f) - 64.0f;
+  if (!(lower > 0.f)) return false;
+  const uint64_t lb_bits = (uint64_t)lower;
+  const uint64_t lb_size = fixed + 4ull * ((lb_bits + 31) / 32);
+  return lb_size + (m >> 6) >= m || (have_best && lb_size >= best);
+}
 
-  const int j = find_job_gc(jr, gc);
-  const Job& J = job_at(jr, j);
-  const int es = elem_size(J.dtype), G = es;
-  const uint64_t local = gc - J.gc_begin;
-  const uint64_t c = local / G;
-  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
-  const uint32_t m = (uint32_t)(nb / es);
-  const uint32_t T = J.lanes;
-
-  // counts of symbols s = lane + 32 k
-  uint32_t cnt[8];
-  uint32_t nz = 0;
-  for (int k = 0; k < 8; k++) {
-    cnt[k] = hist[gc * 256 + lane + 32 * k];
-    nz += __popc(__ballot_sync(0xffffffffu, cnt[k] > 0));
-  }
-  uint32_t* mycodes = codes + gc * 256;
-  for (int k = 0; k < 8; k++) mycodes[lane + 32 * k] = 0;
-
-  GcMeta res;
-  res.nz = nz;
-  res.value = 0;
-  res.size = 0;
-  if (nz <= 1) {
-    uint32_t sym = 0;
-    for (int k = 0; k < 8; k++) {
-      uint32_t b = __ballot_sync(0xffffffffu, cnt[k] > 0);
-      if (b) sym = 32 * k + (__ffs(b) - 1);
-    }
-    res.mode = (nz == 0 || sym == 0) ? kZero : kConst;
-    res.value = (res.mode == kConst) ? sym : 0;
-    if (lane == 0) meta[gc] = res;
-    return;
-  }
-
-  const uint32_t h = (uint32_t)align_up(12 + nz, 4);
-  const uint64_t fixed = (uint64_t)h + 4ull * (T - 1);
-  // Shannon bound: any prefix code spends >= sum c log2(m / c) bits.  If even
-  // that many bits cannot beat the raw size, the decision is RAW.
-  {
-    float part = 0.f;
-    const float lm = log2f((float)m);
-    for (int k = 0; k < 8; k++)
-      if (cnt[k]) part += (float)cnt[k] * (lm - log2f((float)cnt[k]));
-    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    float lower = part * (1.0f - 1e-4f) - 64.0f;
-    if (lower > 0.f) {
-      uint64_t lb_bits = (uint64_t)lower;
-      uint64_t lb_size = fixed + 4ull * ((lb_bits + 31) / 32);
-      if (lb_size + (m >> 6) >= m) {
-        res.mode = kRaw;
-        res.size = m;
-        if (lane == 0) meta[gc] = res;
-        return;
-      }
-    }
-  }
-
+// Code lengths limited to kMaxLen bits for the counts cnt[k] of symbols
+// lane + 32 k (nz >= 2 of them non-zero), by package-merge; into S.lens.
+__device__ void pm_lengths(BuildSmem& S, const uint32_t cnt[8], uint32_t nz, int lane) {
   // --- sort the leaves by key = count << 8 | (255 - symbol) (ascending):
   // compact the non-zero symbols (ballot prefix), then rank each key among
   // the nz compacted keys (keys are distinct: the symbol part differs)
@@ -411,23 +386,122 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
     if (!cnt[k]) S.lens[lane + 32 * k] = 0;
   __syncwarp();
 
-  // --- bit count and mode decision
-  uint32_t bits = 0;
-  uint8_t mylen[8];
+}
+
+__global__ void __launch_bounds__(kBuildWarps * 32)
+k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
+        const uint32_t* __restrict__ zsyms, uint32_t* __restrict__ codes,
+        uint8_t* __restrict__ tabs, GcMeta* __restrict__ meta) {
+  __shared__ BuildSmem smem[kBuildWarps];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const uint64_t gc = (uint64_t)blockIdx.x * kBuildWarps + wid;
+  if (gc >= ngc_total) return;
+  BuildSmem& S = smem[wid];
+
+  const int j = find_job_gc(jr, gc);
+  const Job& J = job_at(jr, j);
+  const int es = elem_size(J.dtype), G = es;
+  const uint64_t local = gc - J.gc_begin;
+  const uint64_t c = local / G;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
+  const uint32_t m = (uint32_t)(nb / es);
+  const uint32_t T = J.lanes;
+
+  // counts of symbols s = lane + 32 k
+  uint32_t cnt[8];
+  uint32_t nz = 0;
   for (int k = 0; k < 8; k++) {
-    mylen[k] = S.lens[lane + 32 * k];
-    bits += cnt[k] * mylen[k];
+    cnt[k] = hist[gc * 256 + lane + 32 * k];
+    nz += __popc(__ballot_sync(0xffffffffu, cnt[k] > 0));
   }
-  for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-  const uint64_t hsize = fixed + 4ull * ((bits + 31) / 32);
-  if (!(hsize + (m >> 6) < m)) {
+  uint32_t* mycodes = codes + gc * 256;
+  for (int k = 0; k < 8; k++) mycodes[lane + 32 * k] = 0;
+
+  GcMeta res;
+  res.nz = nz;
+  res.value = 0;
+  res.size = 0;
+  if (nz <= 1) {
+    uint32_t sym = 0;
+    for (int k = 0; k < 8; k++) {
+      uint32_t b = __ballot_sync(0xffffffffu, cnt[k] > 0);
+      if (b) sym = 32 * k + (__ffs(b) - 1);
+    }
+    res.mode = (nz == 0 || sym == 0) ? kZero : kConst;
+    res.value = (res.mode == kConst) ? sym : 0;
+    if (lane == 0) meta[gc] = res;
+    return;
+  }
+
+  const uint32_t V = 16u / (uint32_t)es, nv = (m + V - 1) / V;
+  const uint32_t zs = zsyms[gc];
+
+  // HUFF candidate: a code for all m symbols (skipped when the Shannon bound
+  // already shows it cannot qualify)
+  const uint32_t h = (uint32_t)align_up(12 + nz, 4);
+  const uint64_t fixed = (uint64_t)h + 4ull * (T - 1);
+  bool huff_ok = false;
+  uint64_t hsize = 0;
+  uint8_t lenH[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (!bound_rules_out(cnt, m, fixed, m, false, 0)) {
+    pm_lengths(S, cnt, nz, lane);
+    uint32_t bits = 0;
+    for (int k = 0; k < 8; k++) {
+      lenH[k] = S.lens[lane + 32 * k];
+      bits += cnt[k] * lenH[k];
+    }
+    for (int o = 16; o; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    hsize = fixed + 4ull * ((bits + 31) / 32);
+    huff_ok = hsize + (m >> 6) < m;
+    __syncwarp();
+  }
+
+  // SPARSE candidate: a code for the symbols outside all-zero vectors (the
+  // zeros of those vectors leave the histogram) plus a bitmap of the vectors
+  bool sparse_ok = false;
+  uint64_t ssize = 0;
+  uint32_t nz2 = 0;
+  uint8_t lenS[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (zs > 0) {
+    uint32_t cnt2[8];
+    for (int k = 0; k < 8; k++) cnt2[k] = cnt[k];
+    if (lane == 0) cnt2[0] -= zs;                    // symbol 0 is lane 0, k = 0
+    for (int k = 0; k < 8; k++) nz2 += __popc(__ballot_sync(0xffffffffu, cnt2[k] > 0));
+    if (nz2 >= 2) {
+      const uint64_t fixed2 = align_up(12 + nz2, 4) + 4ull * ((nv + 31) / 32) + 4ull * (T - 1);
+      if (!bound_rules_out(cnt2, m - zs, fixed2, m, huff_ok, hsize)) {
+        pm_lengths(S, cnt2, nz2, lane);
+        uint32_t bits2 = 0;
+        for (int k = 0; k < 8; k++) {
+          lenS[k] = S.lens[lane + 32 * k];
+          bits2 += cnt2[k] * lenS[k];
+        }
+        for (int o = 16; o; o >>= 1) bits2 += __shfl_xor_sync(0xffffffffu, bits2, o);
+        ssize = fixed2 + 4ull * ((bits2 + 31) / 32);
+        sparse_ok = ssize + (m >> 6) < m;
+        __syncwarp();
+      }
+    }
+  }
+
+  // --- mode decision (SPARSE only when strictly smaller than a qualifying HUFF)
+  uint8_t mylen[8];
+  if (sparse_ok && (!huff_ok || ssize < hsize)) {
+    res.mode = kSparse;
+    res.size = (uint32_t)ssize;
+    res.nz = nz2;
+    for (int k = 0; k < 8; k++) mylen[k] = lenS[k];
+  } else if (huff_ok) {
+    res.mode = kHuff;
+    res.size = (uint32_t)hsize;
+    for (int k = 0; k < 8; k++) mylen[k] = lenH[k];
+  } else {
     res.mode = kRaw;
     res.size = m;
     if (lane == 0) meta[gc] = res;
     return;
   }
-  res.mode = kHuff;
-  res.size = (uint32_t)hsize;
 
   // --- canonical codes (RFC 1951 Sec. 3.2.2) and the table bytes
   uint32_t count[kMaxLen + 1];
@@ -799,16 +873,28 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     e[15] = 0;
   }
   __syncthreads();
-  uint32_t huff = 0, raw = 0;
+  uint32_t huff = 0, raw = 0, sparse = 0;  // huff: every coded group (HUFF or SPARSE)
 #pragma unroll
   for (int g = 0; g < G; g++) {
-    if (S.meta[g].mode == kHuff) huff |= 1u << g;
+    if (S.meta[g].mode == kHuff || S.meta[g].mode == kSparse) huff |= 1u << g;
+    if (S.meta[g].mode == kSparse) sparse |= 1u << g;
     if (S.meta[g].mode == kRaw) raw |= 1u << g;
   }
 #pragma unroll
   for (int g = 0; g < G; g++)
     if (huff >> g & 1)
       for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
+  // SPARSE groups: the vector bitmap (bit v % 32 of word v / 32) is built in
+  // pass A from the vectors it loads anyway; start from zero
+  const uint32_t bmw = (uint32_t)((nvec + 31) / 32);
+  uint32_t* bmap[4] = {nullptr, nullptr, nullptr, nullptr};
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if (sparse >> g & 1u) {
+      bmap[g] = reinterpret_cast<uint32_t*>(out + P + S.off[g] +
+                                            align_up(12 + S.meta[g].nz, 4));
+      for (uint32_t w = tid; w < bmw; w += nthr) bmap[g][w] = 0;
+    }
   __syncthreads();
 
   // The first Huffman group is encoded once, in pass A, into per-unit slots in
@@ -822,8 +908,8 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
   if (!(slot_cap & 1u)) slot_cap--;
 
   // pass A: unit bits (+ raw planes, + slot encoding of group sg)
-  const bool fast_a = sg == 0 && huff == 1u && nb == J.chunk_bytes && nvec % T == 0 &&
-                      nvt % R == 0 && T <= (uint32_t)nthr;
+  const bool fast_a = sg == 0 && huff == 1u && sparse == 0 && nb == J.chunk_bytes &&
+                      nvec % T == 0 && nvt % R == 0 && T <= (uint32_t)nthr;
   if (fast_a)
     pack_fast_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
   for (uint32_t u = fast_a ? units : tid; u < units; u += nthr) {
@@ -857,6 +943,21 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
       const int valid = full ? V : (int)(m - v * V);
 #pragma unroll
       for (int g = 0; g < G; g++) {
+        if (sparse >> g & 1u) {  // SPARSE: bitmap bit; all-zero vectors carry no codes
+          uint32_t any = 0;
+#pragma unroll
+          for (int q = 0; q < V / 4; q++) any |= g4[g][q];
+          if (T % 32 == 0) {
+            // the active lanes hold consecutive vectors from a multiple of 32
+            // (lane 0 first): one ballot is one bitmap word
+            const uint32_t act = __activemask();
+            const uint32_t word = __ballot_sync(act, any != 0);
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(act) - 1)) bmap[g][v >> 5] = word;
+          } else if (any) {
+            atomicOr(&bmap[g][v >> 5], 1u << (v & 31));
+          }
+          if (!any) continue;
+        }
         if (g == sg) {
           if (full) {
 #pragma unroll
@@ -927,14 +1028,16 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     const uint32_t h = (uint32_t)align_up(12 + nz, 4);
     const uint8_t* tab = tabs + (gc0 + g) * kTabBytes;
     for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
-    uint32_t* po = reinterpret_cast<uint32_t*>(p + h);
+    const uint32_t nbm = (sparse >> g & 1u) ? bmw : 0u;  // bitmap words (written in pass A)
+    uint32_t* po = reinterpret_cast<uint32_t*>(p + h + 4 * nbm);
     for (uint32_t t = 1 + tid; t < T; t += nthr) po[t - 1] = S.part[g][t * R];
     uint32_t* words = po + (T - 1);
-    const uint32_t capw = (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * (T - 1)) / 4;
+    const uint32_t capw =
+        (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * nbm - 4ull * (T - 1)) / 4;
     for (uint32_t w = tid; w < capw; w += nthr) words[w] = 0;
     if (tid == 0) {
       S.capw[g] = capw;
-      S.hsz[g] = h + 4 * (T - 1);
+      S.hsz[g] = h + 4 * nbm + 4 * (T - 1);
     }
   }
   __syncthreads();
@@ -996,6 +1099,12 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
 #pragma unroll
       for (int g = 0; g < G; g++) {
         if (!emit[g]) continue;
+        if (sparse >> g & 1u) {  // SPARSE: all-zero vectors carry no codes
+          uint32_t any = 0;
+#pragma unroll
+          for (int q = 0; q < V / 4; q++) any |= g4[g][q];
+          if (!any) continue;
+        }
         if (full) {
 #pragma unroll
           for (int q = 0; q < V / 4; q++) {
@@ -1079,6 +1188,7 @@ size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njob
   b += align_up(ngc_total * sizeof(GcMeta), 256);   // meta
   b += align_up(ngc_total * 8, 256);                // offs
   b += align_up((uint64_t)njobs * 8, 256);          // totals
+  b += align_up(ngc_total * 4, 256);                // zsyms
   return b + 256;
 }
 
@@ -1091,7 +1201,8 @@ void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total
   s->tabs = p; p += align_up(ngc_total * kTabBytes, 256);
   s->meta = reinterpret_cast<GcMeta*>(p); p += align_up(ngc_total * sizeof(GcMeta), 256);
   s->offs = reinterpret_cast<uint64_t*>(p); p += align_up(ngc_total * 8, 256);
-  s->totals = reinterpret_cast<uint64_t*>(p);
+  s->totals = reinterpret_cast<uint64_t*>(p); p += align_up((uint64_t)njobs * 8, 256);
+  s->zsyms = reinterpret_cast<uint32_t*>(p);
 }
 
 static JobRef make_ref(const Job* d_jobs, int njobs, const Job* h_one) {
@@ -1134,9 +1245,10 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
       ea = cudaFuncSetAttribute(kh, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 cudaSharedmemCarveoutMaxShared);
     if (ea != cudaSuccess) return ea;
-    kh<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist);
+    kh<<<(unsigned)nchunks_total, kHistThreads, hs, st>>>(r, s.hist, s.zsyms);
     unsigned nb = (unsigned)((ngc_total + kBuildWarps - 1) / kBuildWarps);
-    k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.codes, s.tabs, s.meta);
+    k_build<<<nb, kBuildWarps * 32, 0, st>>>(r, ngc_total, s.hist, s.zsyms, s.codes, s.tabs,
+                                             s.meta);
   }
   k_scan<<<njobs, kScanThreads, 0, st>>>(r, s.meta, s.offs, s.totals, d_err);
   return cudaGetLastError();

@@ -22,7 +22,7 @@ constexpr int kHdrBytes = 64;
 constexpr int kEntryBytes = 16;
 constexpr int kTabBytes = 272;        // 12 counts + up to 256 symbols, padded
 
-enum Mode : uint32_t { kRaw = 0, kHuff = 1, kZero = 2, kConst = 3 };
+enum Mode : uint32_t { kRaw = 0, kHuff = 1, kZero = 2, kConst = 3, kSparse = 4 };
 
 __host__ __device__ inline int elem_size(int dtype) {
   return dtype == ZIPNN_FP32 ? 4 : (dtype == ZIPNN_U8 ? 1 : 2);
@@ -147,6 +147,7 @@ struct EncodeScratch {
   GcMeta* meta;        // [ngc]
   uint64_t* offs;      // [ngc] payload offsets
   uint64_t* totals;    // [njobs]
+  uint32_t* zsyms;     // [ngc] symbols inside all-zero vectors (SPARSE candidate)
 };
 size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njobs);
 void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total, int njobs,
