@@ -759,10 +759,14 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     if (ok) fast = (T % (2u * nthr) == 0) ? 2 : ((T % (uint32_t)nthr == 0) ? 1 : 0);
   }
   const bool rot = fast != 0 && DT != ZIPNN_U8;
-  // 3c. pair tables.  For window w (W bits) the first code has length
-  // l1 = 1 + #{l <= W : lim_W[l] <= w}; the second code is found the same way
-  // in the remaining W - l1 bits (zero-filled), and kept only if it fits.  With
-  // W = 11 a first code of 12 bits is resolved in the entry by its last bit.
+  // 3c. pair tables, in two passes.  Pass 1: for window w (W bits) the first
+  // code has length l1 = 1 + #{l <= W : lim_W[l] <= w}; with W = 11 a first
+  // code of 12 bits is resolved in the entry by its last bit.  Pass 2: the
+  // second code is the first code of window (w << l1) & (2^W - 1) (the
+  // remaining W - l1 bits, zero-filled), kept when it fits in them.  Pass 2
+  // reads entries that other threads are turning into pairs; a pair keeps the
+  // first code's symbol and length where pass 2 reads them, so either value
+  // serves.
   if (!bad_tab) {
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -785,14 +789,6 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
         if (l1 <= (uint32_t)W) {
           const uint32_t r1 = t.index[l1] + ((uint32_t)w >> (W - l1)) - t.first[l1];
           ent = sym(r1) | (l1 << 16) | (l1 << 27);
-          const uint32_t rest = ((uint32_t)w << l1) & (kLut - 1);
-          uint32_t l2 = 1;
-#pragma unroll
-          for (int q = 1; q <= W; q++) l2 += (limw[q] <= rest);
-          if (l1 + l2 <= (uint32_t)W) {
-            const uint32_t r2 = t.index[l2] + (rest >> (W - l2)) - t.first[l2];
-            ent = (ent & 0x07FFFFFFu) | (sym(r2) << 8) | ((l1 + l2) << 27) | kPair;
-          }
         } else if (W == 11) {
           // first code of 12 bits: w is its prefix, the next bit selects
           ent = kLong | (12u << 16) | (12u << 27);
@@ -806,6 +802,22 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
           }
         }
         sts32(L + 4u * (uint32_t)w, ent);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      if (!coded_mode(CI.mode[g])) continue;
+      const uint32_t L = smem_u32(S.lut_ptr[g]);
+      for (int w = tid; w < kLut; w += nthr) {
+        const uint32_t e = lds32(L + 4u * (uint32_t)w);
+        const uint32_t l1 = (e >> 16) & 15u;
+        if (l1 == 0 || l1 >= (uint32_t)W) continue;  // invalid, long, or no room left
+        const uint32_t e2 = lds32(L + 4u * (((uint32_t)w << l1) & (kLut - 1)));
+        const uint32_t l2 = (e2 >> 16) & 15u;
+        if (l2 == 0 || l1 + l2 > (uint32_t)W) continue;
+        sts32(L + 4u * (uint32_t)w,
+              (e & 0x000F00FFu) | ((e2 & 0xFFu) << 8) | ((l1 + l2) << 27) | kPair);
       }
     }
   }

@@ -147,6 +147,12 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
     // whole rounds of kHistThreads * U vectors of whole 16-bit elements
     const uint64_t nfast = nb % 16 ? 0 : nvec / ((uint64_t)kHistThreads * U) * (kHistThreads * U);
     const uint32_t hls = (uint32_t)__cvta_generic_to_shared(hl);
+    // the second round, up to where the in-loop prefetches start
+    for (uint64_t vp = tid + (uint64_t)kHistThreads * U; vp < nfast && vp < 2ull * kHistThreads * U;
+         vp += kHistThreads) {
+      prefetch_l2(reinterpret_cast<const uint4*>(src) + vp);
+      if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + vp);
+    }
     for (uint64_t v0 = tid; v0 < nfast; v0 += (uint64_t)kHistThreads * U) {
       uint4 a[U];
 #pragma unroll
@@ -750,6 +756,41 @@ struct SlotWriter {
   }
 };
 
+// Slot writer of the specialised pass A: the pending bits sit left-aligned
+// in one 32-bit word; an append of n <= 32 bits places them with one 64-bit
+// shift and stores a word when 32 bits are complete.  Same bits, counts and
+// overflow rule as SlotWriter.
+struct SlotWriter32 {
+  uint32_t* slot;
+  uint32_t cur, nb, wi, cap, bits;
+  __device__ __forceinline__ void put(uint32_t x, uint32_t n) {  // 1 <= n <= 32, x < 2^n
+    const uint32_t total = nb + n;                                // <= 63
+    const uint64_t X = (uint64_t)x << (64 - total);
+    const uint32_t hi = cur | (uint32_t)(X >> 32);
+    bits += n;
+    if (total >= 32) {
+      if (wi < cap) slot[wi] = hi;
+      wi++;
+      cur = (uint32_t)X;
+      nb = total - 32;
+    } else {
+      cur = hi;
+      nb = total;
+    }
+  }
+  __device__ __forceinline__ void put48(uint64_t x, uint32_t n) {  // n <= 48
+    if (n > 32) {
+      put((uint32_t)(x >> 32), n - 32);
+      put((uint32_t)x, 32);
+    } else {
+      put((uint32_t)x, n);
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    if (nb > 0 && wi < cap) slot[wi] = cur;
+  }
+};
+
 // Codes of 4 consecutive symbols (bytes of w) joined MSB-first: <= 48 bits.
 __device__ __forceinline__ uint64_t join4(const uint32_t* codes, uint32_t w, uint32_t& len) {
   uint32_t e0 = codes[__byte_perm(w, 0, 0x4440)], e1 = codes[__byte_perm(w, 0, 0x4441)];
@@ -797,15 +838,20 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
   };
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T, ui = t * R + k;
-    SlotWriter sw;
+    SlotWriter32 sw;
     sw.slot = slots + (size_t)ui * slot_cap;
-    sw.acc = 0;
-    sw.nacc = 0;
+    sw.cur = 0;
+    sw.nb = 0;
     sw.wi = 0;
     sw.cap = slot_cap;
     sw.bits = 0;
     uint64_t v = t + (uint64_t)k * per * T;
     constexpr uint32_t D = 2;  // vectors in flight per thread (L2 prefetches run further ahead)
+    // the unit's first vectors, up to where the in-loop prefetches start
+    for (uint32_t i = D; i < kPrefetchAhead && i < per; i++) {
+      prefetch_l2(reinterpret_cast<const uint4*>(src) + v + (uint64_t)i * T);
+      if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + v + (uint64_t)i * T);
+    }
     uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
     auto one = [&](uint4& a, uint32_t i) {
       uint32_t g4[4][4];
@@ -815,11 +861,24 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
         prefetch_l2(reinterpret_cast<const uint4*>(src) + v + (uint64_t)kPrefetchAhead * T);
         if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + v + (uint64_t)kPrefetchAhead * T);
       }
-#pragma unroll
-      for (int q = 0; q < V / 4; q++) {
+      if constexpr (V / 4 == 1) {
         uint32_t len;
-        const uint64_t x = join4(codes0, g4[0][q], len);
-        sw.put64(x, len);
+        const uint64_t x = join4(codes0, g4[0][0], len);
+        sw.put48(x, len);
+      } else {
+        // two joined quads at a time: one append when they fit in 32 bits
+#pragma unroll
+        for (int q = 0; q < V / 4; q += 2) {
+          uint32_t l0, l1;
+          const uint64_t x0 = join4(codes0, g4[0][q], l0);
+          const uint64_t x1 = join4(codes0, g4[0][q + 1], l1);
+          if (l0 + l1 <= 32) {
+            sw.put(((uint32_t)x0 << l1) | (uint32_t)x1, l0 + l1);
+          } else {
+            sw.put48(x0, l0);
+            sw.put48(x1, l1);
+          }
+        }
       }
 #pragma unroll
       for (int g = 1; g < G; g++) {
