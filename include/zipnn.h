@@ -103,8 +103,9 @@ int zipnn_version(void);
 const char* zipnn_strerror(int status);
 
 /* Sub-streams per Huffman group-chunk used when a call takes no lanes value:
- * chunk_bytes / (element size * 512), clamped to [1, 1024] (sub-streams of
- * about 512 symbols; 256 lanes for BF16 / FP16 at 256 KiB). */
+ * chunk_bytes / 1024, clamped to [1, 1024]: one sub-stream per 64 vectors of
+ * 16 bytes (256 lanes at 256 KiB for every dtype, so that a 256-thread decoder
+ * CTA owns one sub-stream per thread). */
 uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes);
 
 /* Upper bound on the container size for nbytes of the given dtype and chunk

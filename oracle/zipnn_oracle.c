@@ -112,11 +112,12 @@ int or_elem_size(int dtype) {
 }
 int or_n_groups(int dtype) { return or_elem_size(dtype); }
 
-/* default interleave width: sub-streams of about 512 symbols */
+/* default interleave width: one sub-stream per 1 KiB of original data (64
+ * vectors of 16 bytes) */
 uint32_t or_default_lanes(int dtype, uint32_t chunk_bytes) {
     int es = or_elem_size(dtype);
     if (es == 0) return 0;
-    uint32_t t = chunk_bytes / ((uint32_t)es * 512u);
+    uint32_t t = chunk_bytes / 1024u;
     if (t < 1) t = 1;
     if (t > OR_MAX_LANES) t = OR_MAX_LANES;
     return t;

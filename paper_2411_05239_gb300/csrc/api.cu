@@ -116,8 +116,8 @@ zipnn_status cuda_status(cudaError_t e) {
 }
 
 uint32_t lanes_default(int dtype, size_t chunk_bytes) {
-  const int es = elem_size(dtype);
-  uint64_t t = chunk_bytes / ((uint64_t)es * 512u);
+  (void)dtype;                       // the same for every dtype
+  uint64_t t = chunk_bytes / 1024u;  // one sub-stream per 64 vectors of 16 bytes
   if (t < 1) t = 1;
   if (t > ZIPNN_MAX_LANES) t = ZIPNN_MAX_LANES;
   return (uint32_t)t;

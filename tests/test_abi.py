@@ -45,7 +45,8 @@ def test_host_only_entry_points(lib):
     lib.zipnn_default_lanes.restype = ctypes.c_uint32
     lib.zipnn_default_lanes.argtypes = [ctypes.c_int, ctypes.c_size_t]
     assert lib.zipnn_default_lanes(0, 256 * 1024) == 256
-    assert lib.zipnn_default_lanes(2, 256 * 1024) == 128
+    assert lib.zipnn_default_lanes(2, 256 * 1024) == 256
+    assert lib.zipnn_default_lanes(3, 256 * 1024) == 256
     assert lib.zipnn_default_lanes(0, 4096) == 4
     lib.zipnn_compress_bound.restype = ctypes.c_size_t
     lib.zipnn_compress_bound.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t]
