@@ -198,6 +198,28 @@ def time_oracle(sample: np.ndarray, chunk: int, dtype: int | None = None,
             "ratio": len(s) / sample.size}
 
 
+def time_oracle_threads(sample: np.ndarray, chunk: int, threads: int) -> dict:
+    """The oracle chunk-parallel over host threads: each thread compresses then
+    decompresses its own chunk-aligned slice of `sample` (the C calls release
+    the GIL).  Wall time of the slowest thread per phase."""
+    import concurrent.futures as cf
+    import oracle as O
+    n = sample.size // chunk
+    per = -(-n // threads)
+    slices = [sample[i * per * chunk:min(n, (i + 1) * per) * chunk] for i in range(threads)]
+    slices = [s for s in slices if s.size]
+    with cf.ThreadPoolExecutor(len(slices)) as ex:
+        t0 = time.perf_counter()
+        conts = list(ex.map(lambda s: O.compress(s, O.BF16, chunk), slices))
+        t1 = time.perf_counter()
+        outs = list(ex.map(O.decompress, conts))
+        t2 = time.perf_counter()
+    assert all(np.array_equal(o, s) for o, s in zip(outs, slices))
+    nb = sum(s.size for s in slices)
+    return {"compress_gbs": nb / (t1 - t0) / 1e9, "decompress_gbs": nb / (t2 - t1) / 1e9,
+            "threads": len(slices), "bytes": nb}
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
     """The oracle (plain single-threaded C, as it stands) on host cores."""
@@ -419,7 +441,7 @@ def run_gb300(args):
         del h_cont, h_out
 
     # CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
-    cpu = None
+    cpu = cpu_n = None
     if rank == 0 and world == 1 and args.cpu_sample_mb > 0:
         sample = oracle_sample(ts, args.chunk, args.cpu_sample_mb << 20)
         r = time_oracle(sample, args.chunk)
@@ -428,6 +450,10 @@ def run_gb300(args):
                "compress_gbs": r["bytes"] / r["compress_s"] / 1e9,
                "sample": (f"{r['bytes'] >> 20} MiB: evenly spaced {args.chunk >> 10} KiB chunks "
                           "of the checkpoint; oracle compress then decompress, 1 thread")}
+        rn = time_oracle_threads(sample, args.chunk, os.cpu_count() or 1)
+        cpu_n = {"value": rn["decompress_gbs"], "unit": "GB/s", "cores": rn["threads"],
+                 "kind": "oracle, chunk-parallel over host threads",
+                 "compress_gbs": rn["compress_gbs"], "sample": "the same sample, sliced"}
 
     dec_s, comp_s = md / 1e3, mc / 1e3
     value = world * orig / dec_s / 1e9
@@ -465,6 +491,7 @@ def run_gb300(args):
                               "unit": "GB/s", "frac": alg_comp / comp_s / 1e9 / hbm_peak,
                               "algorithmic_bytes": alg_comp},
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_n,
         "e2e": e2e,
         "e2e_roundtrip": e2e_rt,
         "gpu_launches": 5 * K,

@@ -23,7 +23,8 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
+                             bool has_delta);
 }  // namespace zipnn
 
 using namespace zipnn;
@@ -466,7 +467,8 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   Job J = decode_job(s, d_base_or_null, d_dst);
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
                                    nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0,
-                                   stage_frac64(s->dtype, s->flags));
+                                   stage_frac64(s->dtype, s->flags),
+                                   (s->flags & ZIPNN_FLAG_DELTA) != 0);
   return cuda_status(e);
 }
 
@@ -479,10 +481,11 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   uint64_t chunk = 0, max_chunk = 0;
   int max_groups = 1;
   int uniform = streams[0].dtype;
-  bool lanes256 = true;
+  bool lanes256 = true, has_delta = false;
   int frac64 = 0;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
+    if (s->flags & ZIPNN_FLAG_DELTA) has_delta = true;
     if (s->dtype != uniform) uniform = -1;
     if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
     if (s->lanes % 256) lanes256 = false;
@@ -510,7 +513,7 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
-                         uniform, max_chunk, lanes256, frac64);
+                         uniform, max_chunk, lanes256, frac64, has_delta);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

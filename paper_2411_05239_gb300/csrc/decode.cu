@@ -308,8 +308,8 @@ struct Staging {
 // sub-streams, which gives the scheduler instruction-level parallelism); each
 // vector is merged with the raw / constant groups and stored.
 template <int DT, int W, class BR, bool STAGED, int NS>
-__device__ __noinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
-                                         uint32_t* err) {
+__device__ __forceinline__ void decode_loop(const Job& J, uint64_t c, Smem& S, Staging& stg,
+                                            uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
@@ -621,11 +621,224 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   if (bad) atomicOr(err, 1u);
 }
 
+// A staged coded group (HUFF or SPARSE) and the reader of one of its
+// sub-streams, as the fast loop sees them.
+struct FastGroup {
+  const uint32_t* words;   // bitstream (shared memory)
+  const uint32_t* starts;  // start bits of sub-streams 1..T-1
+  const uint32_t* bm;      // SPARSE: bitmap of the vectors holding a non-zero symbol
+  uint32_t nbits, wlim, lut;
+  bool sparse;
+};
+struct FastReader {
+  uint32_t w0, w1, pos, idx;
+};
+
+// Two symbols of reader r (one pair lookup, refill clamped to the payload).
+template <int W>
+__device__ __forceinline__ uint32_t fast_pair(const FastGroup& F, FastReader& r, const GroupTab& tb,
+                                              uint32_t& bad) {
+  const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+  const uint32_t e = pair_at<W>(__funnelshift_l(r.w1, r.w0, r.pos), F.lut, tb, syms, bad);
+  r.pos += e >> 27;
+  if (r.pos >= 32u) {
+    r.pos -= 32u;
+    r.w0 = r.w1;
+    r.w1 = F.words[min(r.idx, F.wlim)];
+    r.idx++;
+  }
+  return e;
+}
+
+// Fast loop for the other layouts of deltas, clean and pruned models: group 0
+// coded (HUFF or SPARSE) and staged; with NC = 2 (16-bit dtypes)
+// group 1 coded and staged too, else every group after the first raw, zero or
+// constant; a whole chunk whose nvec vectors split evenly over the T
+// sub-streams, and T a multiple of NS * nthr.  Thread t decodes sub-streams
+// t, t + nthr, ... (NS in lockstep, interleaved for instruction-level
+// parallelism); every vector is 16 B of output: V/2 pair lookups per coded
+// group (none for an all-zero vector of a SPARSE group), one load per raw
+// group (two vectors ahead), bit-select merge with the rotated exponent
+// symbols, a 16-B store.  No per-vector mode tests and no tails inside the
+// loop.  Each sub-stream must end exactly where the next one starts (the last
+// one within the bitstream); a mismatch flags the chunk as corrupt.
+template <int DT, int W, int NS, int NC>
+__device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, const Smem& S,
+                                            const Staging& stg, uint32_t* err) {
+  constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
+  constexpr int RW = DT == ZIPNN_FP32 ? 3 : (DT == ZIPNN_U8 ? 1 : 2);
+  static_assert(NC == 1 || (NC == 2 && G == 2), "two coded groups: 16-bit dtypes only");
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const ChunkInfo& CI = S.ci;
+  const uint64_t off0 = c * J.chunk_bytes;
+  const uint32_t T = J.lanes;
+  const uint32_t nper = (J.chunk_bytes / 16u) / T;
+  FastGroup F[NC];
+#pragma unroll
+  for (int g = 0; g < NC; g++) {
+    const uint8_t* pay = stg.base + CI.staged[g];
+    F[g].words = reinterpret_cast<const uint32_t*>(pay + (uint32_t)CI.bs[g]);
+    F[g].starts = reinterpret_cast<const uint32_t*>(pay + (uint32_t)CI.offs[g]);
+    F[g].bm = reinterpret_cast<const uint32_t*>(pay + (uint32_t)CI.bmo[g]);
+    F[g].sparse = CI.mode[g] == kSparse;
+    F[g].nbits = CI.nwords[g] * 32u;
+    F[g].wlim = CI.nwords[g] + 1u;
+    F[g].lut = smem_u32(S.lut_ptr[g]);
+  }
+  const uint8_t* rawp[G];
+  uint32_t cw[G], rawm = 0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    rawp[g] = J.src + CI.payload[g];
+    cw[g] = CI.value[g] * 0x01010101u;  // ZERO groups carry value 0
+    if (g >= NC && CI.mode[g] == kRaw) rawm |= 1u << g;
+  }
+  uint4* dst = reinterpret_cast<uint4*>(J.dst + off0);
+  const uint4* base = J.base ? reinterpret_cast<const uint4*>(J.base + off0) : nullptr;
+  uint32_t bad = 0;
+  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
+    FastReader R[NC][NS];
+    uint32_t vt[NS];
+    uint32_t ra[NS][RW], rb[NS][RW];  // raw words of vectors k (even) and k + 1
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+      const uint32_t t = t0 + j * nthr;
+      vt[j] = t;
+#pragma unroll
+      for (int g = 0; g < NC; g++) {
+        uint32_t start = t ? F[g].starts[t - 1] : 0u;
+        if (start > F[g].nbits) {
+          bad = 1;
+          start = F[g].nbits;
+        }
+        FastReader& r = R[g][j];
+        r.idx = start >> 5;
+        r.pos = start & 31u;
+        r.w0 = F[g].words[min(r.idx, F[g].wlim)];
+        r.w1 = F[g].words[min(r.idx + 1u, F[g].wlim)];
+        r.idx += 2;
+      }
+      if constexpr (NC == 1) {
+        load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
+        if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
+      }
+    }
+    // vector k of every sub-stream; rr holds its raw words and receives those
+    // of vector k + 2
+    auto vec = [&](uint32_t k, uint32_t (&rr)[NS][RW]) {
+      uint32_t ex[NC][NS][V / 4];
+#pragma unroll
+      for (int g = 0; g < NC; g++) {
+        bool coded[NS];
+#pragma unroll
+        for (int j = 0; j < NS; j++) coded[j] = true;
+        if (F[g].sparse) {  // uniform per chunk
+#pragma unroll
+          for (int j = 0; j < NS; j++) {
+            const uint32_t v = vt[j] + k * T;
+            coded[j] = (F[g].bm[v >> 5] >> (v & 31u)) & 1u;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < V / 4; q++) {
+          uint32_t h[2][NS];
+#pragma unroll
+          for (int p = 0; p < 2; p++) {
+#pragma unroll
+            for (int j = 0; j < NS; j++) {
+              if (F[g].sparse)
+                h[p][j] = coded[j] ? fast_pair<W>(F[g], R[g][j], S.tab[g], bad) : 0u;
+              else
+                h[p][j] = fast_pair<W>(F[g], R[g][j], S.tab[g], bad);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NS; j++) ex[g][j][q] = __byte_perm(h[0][j], h[1][j], 0x5410);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+        const uint32_t v = vt[j] + k * T;
+        uint32_t x[4];
+        if constexpr (NC == 2) {
+          merge16r(ex[0][j][0], ex[1][j][0], x[0], x[1]);
+          merge16r(ex[0][j][1], ex[1][j][1], x[2], x[3]);
+        } else if constexpr (DT == ZIPNN_FP32) {
+          merge32r(ex[0][j][0], rr[j][0], rr[j][1], rr[j][2], x);
+        } else if constexpr (DT == ZIPNN_U8) {
+          x[0] = ex[0][j][0]; x[1] = ex[0][j][1]; x[2] = ex[0][j][2]; x[3] = ex[0][j][3];
+        } else {
+          merge16r(ex[0][j][0], rr[j][0], x[0], x[1]);
+          merge16r(ex[0][j][1 % (V / 4)], rr[j][1 % RW], x[2], x[3]);
+        }
+        if constexpr (NC == 1)
+          if (k + 2 < nper) load_raw_vec<DT>(rawp, rawm, cw, v + 2 * T, rr[j]);
+        if (base) {
+          const uint4 bb = __ldg(base + v);
+          x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
+        }
+        dst[v] = make_uint4(x[0], x[1], x[2], x[3]);
+      }
+    };
+    for (uint32_t k = 0; k < nper; k += 2) {
+      vec(k, ra);
+      if (k + 1 < nper) vec(k + 1, rb);
+    }
+    // every sub-stream ends where the next begins
+#pragma unroll
+    for (int g = 0; g < NC; g++)
+#pragma unroll
+      for (int j = 0; j < NS; j++) {
+        const FastReader& r = R[g][j];
+        const uint32_t end = (r.idx - 2u) * 32u + r.pos;
+        if (vt[j] + 1u < T) bad |= end != F[g].starts[vt[j]];
+        else bad |= end > F[g].nbits;
+      }
+  }
+  if (bad) atomicOr(err, 1u);
+}
+
+// The generic loop out of line (kernels without the general fast loops).
+template <int DT, int W, class BR, bool STAGED, int NS>
+__device__ __noinline__ void decode_loop_ool(const Job& J, uint64_t c, Smem& S, Staging& stg,
+                                             uint32_t* err) {
+  decode_loop<DT, W, BR, STAGED, NS>(J, c, S, stg, err);
+}
+
+// Every layout but the Huffman loop of model weights, behind one out-of-line
+// call (one call site keeps the register allocation of the kernel's hot path
+// as it is): the general fast loop (SPARSE group 0, or two coded groups), else
+// the generic loop over staged or global payloads.
+template <int DT, int W>
+__device__ __noinline__ void decode_other(const Job& J, uint64_t c, Smem& S, Staging& stg,
+                                          uint32_t* err, int fast, int fast_nc) {
+  constexpr int G = Traits<DT>::G;
+  const uint32_t T = J.lanes;
+  const int nthr = blockDim.x;
+  if constexpr (W >= 11) {
+    if (fast_nc == 2) {
+      if constexpr (G == 2) {
+        if (fast == 2) return decode_fast_coded<DT, W, 2, 2>(J, c, S, stg, err);
+        if (fast == 1) return decode_fast_coded<DT, W, 1, 2>(J, c, S, stg, err);
+      }
+    } else {
+      if (fast == 2) return decode_fast_coded<DT, W, 2, 1>(J, c, S, stg, err);
+      if (fast == 1) return decode_fast_coded<DT, W, 1, 1>(J, c, S, stg, err);
+    }
+  }
+  if (S.ci.stage_bytes) {
+    if (T >= 2u * nthr) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, stg, err);
+    else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, stg, err);
+  } else {
+    decode_loop<DT, W, BitReader, false, 1>(J, c, S, stg, err);
+  }
+}
+
 // Decode one chunk of a tensor of dtype DT with W-bit pair tables.  Returns
 // false if a bulk copy never completed (the caller must stop using the stage).
 // Shared memory: one table slot (lut0) for the first Huffman group; tables of
 // further Huffman groups and the staged payloads share the stage.
-template <int DT, int W>
+template <int DT, int W, bool GEN>
 __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, Staging& stg,
                              uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V, ES = 16 / V;
@@ -750,15 +963,23 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   const bool bad_tab = CI.bad != 0;
   // fast loop (decode_fast) when the chunk has its layout; symbols are then
   // stored rotated in the table
-  int fast = 0;
+  // fast = sub-streams per thread of a fast loop (0: generic loop), fast_nc =
+  // coded groups in front (2: both groups of a 16-bit delta or clean model)
+  int fast = 0, fast_nc = 1;
   if constexpr (W >= 11) {
-    bool ok = CI.mode[0] == kHuff && CI.staged[0] != 0xFFFFFFFFu && nb == J.chunk_bytes &&
-              ((uint32_t)(nb / 16) % T) == 0;
+    // without GEN only the Huffman loop of model weights is a fast loop
+    bool ok = (GEN ? coded_mode(CI.mode[0]) : CI.mode[0] == kHuff) && CI.staged[0] != 0xFFFFFFFFu &&
+              nb == J.chunk_bytes && ((uint32_t)(nb / 16) % T) == 0;
+    if (GEN && G == 2 && coded_mode(CI.mode[1 % G])) {
+      fast_nc = 2;
+      ok = ok && CI.staged[1 % G] != 0xFFFFFFFFu;
+    }
 #pragma unroll
-    for (int g = 1; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
+    for (int g = fast_nc; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
     if (ok) fast = (T % (2u * nthr) == 0) ? 2 : ((T % (uint32_t)nthr == 0) ? 1 : 0);
   }
-  const bool rot = fast != 0 && DT != ZIPNN_U8;
+  // exponent symbols are stored rotated for the fast loops' merge
+  const bool rot0 = fast != 0 && DT != ZIPNN_U8;
   // 3c. pair tables, in two passes.  Pass 1: for window w (W bits) the first
   // code has length l1 = 1 + #{l <= W : lim_W[l] <= w}; with W = 11 a first
   // code of 12 bits is resolved in the entry by its last bit.  Pass 2: the
@@ -776,6 +997,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
       uint32_t limw[W + 1];
 #pragma unroll
       for (int l = 1; l <= W; l++) limw[l] = t.lim[l] >> (kMaxLen - W);
+      const bool rot = rot0 && g == 0;
       auto sym = [&](uint32_t r) -> uint32_t {
         const uint32_t v = syms[r & 255];
         return rot ? (((v >> 1) | (v << 7)) & 0xFFu) : v;
@@ -838,28 +1060,36 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     if (tid == 0) atomicOr(err, 1u);
     return true;
   }
-  // 4. decode + merge (two sub-streams per thread when the chunk has enough)
+  // 4. decode + merge: the Huffman loop of model weights inline, the rest out
+  // of line.  Kernels for launches with deltas (GEN) add the general fast
+  // loops; merely linking them into a kernel costs the inline Huffman loop a
+  // third of its speed (register allocation), so the other kernels keep the
+  // generic loop alone behind their out-of-line calls.
   if constexpr (W >= 11) {
-    if (fast == 2) {
-      decode_fast<DT, W, 2>(J, c, S, stg, err);
-      return true;
-    }
-    if (fast == 1) {
-      decode_fast<DT, W, 1>(J, c, S, stg, err);
-      return true;
+    if (fast_nc == 1 && CI.mode[0] == kHuff) {
+      if (fast == 2) {
+        decode_fast<DT, W, 2>(J, c, S, stg, err);
+        return true;
+      }
+      if (fast == 1) {
+        decode_fast<DT, W, 1>(J, c, S, stg, err);
+        return true;
+      }
     }
   }
-  if (CI.stage_bytes) {
-    if (T >= 2u * nthr) decode_loop<DT, W, SmemBitReader, true, 2>(J, c, S, stg, err);
-    else decode_loop<DT, W, SmemBitReader, true, 1>(J, c, S, stg, err);
+  if constexpr (GEN) {
+    decode_other<DT, W>(J, c, S, stg, err, fast, fast_nc);
+  } else if (CI.stage_bytes) {
+    if (T >= 2u * nthr) decode_loop_ool<DT, W, SmemBitReader, true, 2>(J, c, S, stg, err);
+    else decode_loop_ool<DT, W, SmemBitReader, true, 1>(J, c, S, stg, err);
   } else {
-    decode_loop<DT, W, BitReader, false, 1>(J, c, S, stg, err);
+    decode_loop_ool<DT, W, BitReader, false, 1>(J, c, S, stg, err);
   }
   return true;
 }
 
 // DTS: the dtype of every job in the launch, or -1 for a mixed batch.
-template <int DTS, int W, int NT>
+template <int DTS, int W, int NT, bool GEN>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
          unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap) {
@@ -895,13 +1125,13 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     const uint64_t c = chunk - J.chunk_begin;
     bool ok;
     if (DTS >= 0) {
-      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W>(J, c, S, lut0, stg, err);
+      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN>(J, c, S, lut0, stg, err);
     } else {
       switch (J.dtype) {
-        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W>(J, c, S, lut0, stg, err); break;
-        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W>(J, c, S, lut0, stg, err); break;
-        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W>(J, c, S, lut0, stg, err); break;
-        default: ok = decode_chunk<ZIPNN_U8, W>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W, GEN>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W, GEN>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W, GEN>(J, c, S, lut0, stg, err); break;
+        default: ok = decode_chunk<ZIPNN_U8, W, GEN>(J, c, S, lut0, stg, err); break;
       }
     }
     if (!ok) return;  // a bulk copy timed out: leave the stage alone
@@ -913,13 +1143,24 @@ using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, 
                              uint32_t);
 
 template <int W, int NT>
-DecodeKernel pick_kernel(int dt) {
+DecodeKernel pick_kernel(int dt, bool gen) {
+  // kernels with the general fast loops (deltas: two coded 16-bit groups)
+  if constexpr (W >= 11) {
+    if (gen) {
+      switch (dt) {
+        case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W, NT, true>;
+        case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W, NT, true>;
+        case ZIPNN_FP32: case ZIPNN_U8: break;
+        default: return k_decode<-1, W, kDecThreads, true>;
+      }
+    }
+  }
   switch (dt) {
-    case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W, NT>;
-    case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W, NT>;
-    case ZIPNN_FP32: return k_decode<ZIPNN_FP32, W, NT>;
-    case ZIPNN_U8: return k_decode<ZIPNN_U8, W, NT>;
-    default: return k_decode<-1, W, kDecThreads>;  // mixed batches: 128 threads
+    case ZIPNN_BF16: return k_decode<ZIPNN_BF16, W, NT, false>;
+    case ZIPNN_FP16: return k_decode<ZIPNN_FP16, W, NT, false>;
+    case ZIPNN_FP32: return k_decode<ZIPNN_FP32, W, NT, false>;
+    case ZIPNN_U8: return k_decode<ZIPNN_U8, W, NT, false>;
+    default: return k_decode<-1, W, kDecThreads, false>;  // mixed batches: 128 threads
   }
 }
 
@@ -944,7 +1185,8 @@ int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups) {
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64) {
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
+                             bool has_delta) {
   if (nchunks_total == 0) return cudaSuccess;
   JobRef r;
   r.table = h_one ? nullptr : d_jobs;
@@ -956,6 +1198,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     max_chunk = h_one->chunk_bytes;
     lanes256 = h_one->lanes % 256 == 0;
     frac64 = stage_frac64(h_one->dtype, h_one->flags);
+    has_delta = (h_one->flags & ZIPNN_FLAG_DELTA) != 0;
   }
   int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 12;
   if (w < 10) w = 10;
@@ -966,11 +1209,12 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   const int want = (tuning && tuning->threads) ? tuning->threads : 256;
   const int threads =
       (want == 256 && w >= 11 && uniform_dtype >= 0 && lanes256) ? 256 : kDecThreads;
-  DecodeKernel kern = w == 10    ? pick_kernel<10, kDecThreads>(uniform_dtype)
-                      : w == 11  ? (threads == 256 ? pick_kernel<11, 256>(uniform_dtype)
-                                                   : pick_kernel<11, kDecThreads>(uniform_dtype))
-                                 : (threads == 256 ? pick_kernel<12, 256>(uniform_dtype)
-                                                   : pick_kernel<12, kDecThreads>(uniform_dtype));
+  DecodeKernel kern =
+      w == 10   ? pick_kernel<10, kDecThreads>(uniform_dtype, false)
+      : w == 11 ? (threads == 256 ? pick_kernel<11, 256>(uniform_dtype, has_delta)
+                                  : pick_kernel<11, kDecThreads>(uniform_dtype, has_delta))
+                : (threads == 256 ? pick_kernel<12, 256>(uniform_dtype, has_delta)
+                                  : pick_kernel<12, kDecThreads>(uniform_dtype, has_delta));
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
   if (max_groups < 1 || max_groups > 4) max_groups = 4;

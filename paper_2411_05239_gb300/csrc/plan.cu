@@ -24,7 +24,8 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64);
+                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
+                             bool has_delta);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
@@ -84,10 +85,11 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   uint64_t chunk = 0, max_chunk = 0;
   int max_groups = 1;
   int uniform = streams[0].dtype;
-  bool lanes256 = true;
+  bool lanes256 = true, has_delta = false;
   int frac64 = 0;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
+    if (s->flags & ZIPNN_FLAG_DELTA) has_delta = true;
     if (s->dtype != uniform) uniform = -1;
     if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
     if (s->lanes % 256) lanes256 = false;
@@ -137,7 +139,7 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   if (tuning) tu = *tuning;
   e = capture(p, [&](cudaStream_t cs) {
     return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
-                            uniform, max_chunk, lanes256, frac64);
+                            uniform, max_chunk, lanes256, frac64, has_delta);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
@@ -301,9 +303,10 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       const int a = seg_first[k], b = seg_first[k + 1];
       uint64_t nch = 0, max_chunk = 0;
       int max_groups = 1, uniform = jobs[a].dtype;
-      bool lanes256 = true;
+      bool lanes256 = true, has_delta = false;
       int frac64 = 0;
       for (int i = a; i < b && r == cudaSuccess; i++) {
+        if (jobs[i].flags & ZIPNN_FLAG_DELTA) has_delta = true;
         if (stage_frac64(jobs[i].dtype, jobs[i].flags) > frac64)
           frac64 = stage_frac64(jobs[i].dtype, jobs[i].flags);
         r = cudaMemcpyAsync(streams[i].data, h_containers[i], streams[i].nbytes,
@@ -318,7 +321,7 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);
       if (r == cudaSuccess)
         r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err, tickets + k,
-                             cs, uniform, max_chunk, lanes256, frac64);
+                             cs, uniform, max_chunk, lanes256, frac64, has_delta);
     }
     // the last wait above joined the copy stream back into the capture stream
     return r;

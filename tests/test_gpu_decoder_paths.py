@@ -136,3 +136,41 @@ def test_wrong_substream_start_reports_ecorrupt_and_context_survives():
     y = Z.decompress(c)
     Z.sync_status()
     assert torch.equal(y.cpu().view(torch.int16), x.view(torch.int16))
+
+
+def pruned_bf16(n: int, seed: int) -> torch.Tensor:
+    """BF16 weights with 90% of their 16-byte vectors zero: SPARSE groups."""
+    g = np.random.default_rng(seed)
+    w = (g.standard_normal(n) * 0.02).astype(np.float32)
+    keep = np.repeat(g.random((n + 7) // 8) < 0.1, 8)[:n]
+    return torch.from_numpy(np.where(keep, w, 0).astype(np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("with_delta", [False, True])
+@pytest.mark.parametrize("mixed_dtypes", [False, True])
+def test_batches_with_and_without_deltas(with_delta, mixed_dtypes):
+    """A launch that holds a delta runs the kernels with the general fast loops
+    (two coded groups, SPARSE bitmaps); every other stream of that launch must
+    decode through them as well, and without a delta the same streams take the
+    Huffman loop of model weights and the generic loop."""
+    xs = [W.gaussian(700_000, 0.02, 93), pruned_bf16(600_000, 94),
+          skewed_exponents_bf16(524_288, 95)]
+    if mixed_dtypes:
+        xs += [W.clean_fp16_from_bf16(300_000, 96), W.clean_fp32_from_bf16(262_144, 97)]
+    cs = [Z.compress(x.cuda()) for x in xs]
+    for c, x in zip(cs, xs):
+        assert c.to_bytes() == O.compress(u8(x), Z.dtype_code(x, None), Z.DEFAULT_CHUNK)
+    bases = [None] * len(xs)
+    if with_delta:
+        nxt, base = W.delta_pair(900_001, seed=98, device="cuda")
+        c = Z.compress(nxt, base=base)
+        assert c.to_bytes() == O.delta(u8(nxt), u8(base), Z.BF16, Z.DEFAULT_CHUNK)
+        xs, cs, bases = xs + [nxt], cs + [c], bases + [base]
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    for nt in (128, 256):
+        for o in outs:
+            o.zero_()
+        Z.batch_decompress(cs, outs, bases=bases, tune=Z.tuning(threads=nt))
+        Z.sync_status()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(u8(o), u8(x)), nt
