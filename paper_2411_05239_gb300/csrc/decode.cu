@@ -45,6 +45,7 @@ constexpr uint32_t kStageMin = 4096;
 constexpr uint32_t kStageCapPerSm = 227u * 1024u;  // shared memory an SM gives its CTAs
 constexpr uint32_t kStaticReserve = 4096;          // static Smem + the per-CTA reservation
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kPfBudget = 16ull << 20;  // L2 bytes the fast loops' prefetches may hold
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -296,6 +297,8 @@ __device__ __forceinline__ void merge16r(uint32_t er, uint32_t r, uint32_t& w0, 
 struct Staging {
   uint8_t* base;       // shared-memory stage
   uint32_t cap;        // its size in bytes
+  uint32_t pf_bytes;   // L2 prefetch window of the fast loops per CTA (bytes)
+  uint32_t ring;       // shared-memory address of the raw-word rings (kRingBytes per thread)
   uint64_t* bar;       // its mbarrier
   uint32_t parity;     // phase to wait for next
   uint32_t extra_tx;   // fault injection: bytes expected but never sent (0 normally)
@@ -504,20 +507,101 @@ __device__ __forceinline__ void load_raw_vec(const uint8_t* const* rawp, uint32_
   }
 }
 
+// Bulk prefetch into L2 (asynchronous, no registers, no completion to wait
+// for), in pieces of at most 32 KiB; p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const uint8_t* p, uint64_t bytes) {
+  for (uint64_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t n = (uint32_t)(bytes - o < 32768u ? bytes - o : 32768u);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(n) : "memory");
+  }
+}
+
+// The fast loops read the raw groups (and a delta's base) straight from
+// global memory, each thread two vectors ahead: too few bytes in flight per SM
+// to cover DRAM latency.  Step k of a fast loop consumes vectors [kT, (k+1)T)
+// of the chunk, i.e. a contiguous slice of T * 16/G bytes of every raw group
+// and T * 16 bytes of the base, so one thread of the CTA keeps the slices of
+// the next D steps in flight as bulk L2 prefetches.  D = the CTA's share of an
+// L2 budget (pf_bytes) over the bytes of one step, at least 2, at most the
+// whole chunk.  Only when one pass over the sub-streams covers every lane
+// (T == NS * nthr), so that all threads sweep the slices together.
+template <int G>
+__device__ __forceinline__ uint32_t pf_steps(uint32_t rawm, bool has_base, uint32_t T,
+                                             uint32_t nper, uint32_t pf_bytes) {
+  const uint32_t per_step = ((uint32_t)__popc(rawm) * (16u / G) + (has_base ? 16u : 0u)) * T;
+  if (per_step == 0) return 0;
+  const uint32_t d = pf_bytes / per_step;
+  return d < 2u ? 2u : (d > nper ? nper : d);
+}
+template <int G>
+__device__ __forceinline__ void prefetch_steps(const uint8_t* const (&rawp)[G], uint32_t rawm,
+                                               const uint8_t* base, uint32_t T, uint32_t k0,
+                                               uint32_t k1) {
+  if (k1 <= k0) return;
+  const uint64_t gb = (uint64_t)T * (16u / G);  // bytes of one raw group per step
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if ((rawm >> g) & 1u) bulk_prefetch_l2(rawp[g] + k0 * gb, (k1 - k0) * gb);
+  if (base) bulk_prefetch_l2(base + (uint64_t)k0 * T * 16u, (uint64_t)(k1 - k0) * T * 16u);
+}
+
+// Per-thread asynchronous copies global -> shared (no registers held while in
+// flight); groups complete in the order they were committed.  The ring is
+// touched only by these volatile statements, whose order the compiler keeps.
+__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+__device__ __forceinline__ uint2 lds64(uint32_t saddr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds32v(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+
+// Raw-word ring of the FP32 fast loop: kRingBytes of shared memory per thread
+// hold the three raw groups' words of the next RD steps of its NS sub-streams
+// (4-B pieces), so that RD steps of loads are in flight per thread without
+// holding registers.  The 16-bit loops keep their raw words in registers, two
+// steps ahead: there the ring's shared memory costs a CTA per SM (W = 12) and
+// the loop lost more than it gained.
+constexpr uint32_t kRingBytes = 64;
+template <int NS>
+struct RawRing {
+  static constexpr uint32_t per = kRingBytes / (NS * 3u * 4u);
+  static constexpr uint32_t RD = per >= 8 ? 8u : (per >= 4 ? 4u : 2u);  // steps in the ring
+};
+
 // Fast loop for the dominant chunk layout: group 0 Huffman and staged, every
 // other group raw, zero or constant, a whole chunk whose nvec vectors split evenly over the T
 // sub-streams, and T a multiple of NS * nthr.  Thread t decodes sub-streams
 // t, t + nthr, ... (NS in lockstep, interleaved for instruction-level
-// parallelism); every vector is 16 B of output: V/2 pair lookups, one raw
-// load per raw group (prefetched two vectors ahead), bit-select merge with the
-// rotated exponent symbols, a 16-B store.  No mode tests and no tails inside
-// the loop.  Each sub-stream must end exactly where the next one starts (the
-// last one within the bitstream); a mismatch flags the chunk as corrupt.
+// parallelism); every vector is 16 B of output: V/2 pair lookups, the raw
+// groups' words (16-bit: loaded two steps ahead into alternating register
+// sets; FP32: from the thread's ring, copied RD steps ahead), bit-select merge
+// with the rotated exponent symbols, a 16-B store.  No mode tests and no tails
+// inside the loop.  Each sub-stream must end exactly where the next one starts
+// (the last one within the bitstream); a mismatch flags the chunk as corrupt.
 template <int DT, int W, int NS>
 __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem& S,
                                             const Staging& stg, uint32_t* err) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
   constexpr int RW = DT == ZIPNN_FP32 ? 3 : (DT == ZIPNN_U8 ? 1 : 2);
+  constexpr bool RING = DT == ZIPNN_FP32;
+  constexpr uint32_t RD = RawRing<NS>::RD;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const ChunkInfo& CI = S.ci;
   const uint64_t off0 = c * J.chunk_bytes;
@@ -540,10 +624,39 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   }
   uint4* dst = reinterpret_cast<uint4*>(J.dst + off0);
   const uint4* base = J.base ? reinterpret_cast<const uint4*>(J.base + off0) : nullptr;
+  const uint8_t* base8 = J.base ? J.base + off0 : nullptr;
+  // FP32 ring: this thread's piece q of sub-stream j in slot sl is at
+  // ring + ((sl * NS + j) * 3 + q) * rstride
+  const uint32_t ring = stg.ring + (uint32_t)tid * 4u;
+  const uint32_t rstride = (uint32_t)nthr * 4u;
   uint32_t bad = 0;
+  // L2 prefetch window; steps [0, D) were requested when the chunk was set up.
+  // Lane 0 of warp (k / 2) mod (warps) requests steps k + D and k + D + 1.
+  // FP32 only: in the 16-bit kernels the extra live registers cost the loop
+  // more than the later prefetches gain (the first window stays).
+  const bool pfl = DT == ZIPNN_FP32 && (tid & 31) == 0 && T == (uint32_t)(NS * nthr);
+  const uint32_t wid = (uint32_t)tid >> 5, wmask = ((uint32_t)nthr >> 5) - 1u;
+  const uint32_t D = pfl ? pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes) : 0u;
   for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
     uint32_t w0[NS], w1[NS], pos[NS], idx[NS], vt[NS];
-    uint32_t ra[NS][RW], rb[NS][RW];  // raw words of vectors k (even) and k + 1
+    uint32_t ra[NS][RW], rb[NS][RW];  // 16-bit: raw words of vectors k (even) and k + 1
+    // FP32: raw words of step k into ring slot k mod RD (always one commit
+    // group per step, empty past the end, so that step k has landed when at
+    // most RD - 1 groups are pending)
+    auto issue = [&](uint32_t k) {
+      if (k < nper) {
+        const uint32_t sl = (k & (RD - 1u)) * NS;
+#pragma unroll
+        for (int j = 0; j < NS; j++) {
+          const uint32_t v = vt[j] + k * T;
+#pragma unroll
+          for (int q = 0; q < 3; q++)
+            if ((rawm >> (q + 1)) & 1u)
+              cp_async4(ring + ((sl + j) * 3u + q) * rstride, rawp[q + 1] + 4ull * v);
+        }
+      }
+      cp_async_commit();
+    };
 #pragma unroll
     for (int j = 0; j < NS; j++) {
       const uint32_t t = t0 + j * nthr;
@@ -558,11 +671,17 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
       w0[j] = words[min(idx[j], wlim)];
       w1[j] = words[min(idx[j] + 1u, wlim)];
       idx[j] += 2;
-      load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
-      if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
+      if constexpr (!RING) {
+        load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
+        if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
+      }
     }
-    // vector k of every sub-stream; rr holds its raw words and receives those
-    // of vector k + 2
+    if constexpr (RING) {
+#pragma unroll
+      for (uint32_t k = 0; k < RD; k++) issue(k);
+    }
+    // vector k of every sub-stream; 16-bit: rr holds its raw words and
+    // receives those of vector k + 2
     auto vec = [&](uint32_t k, uint32_t (&rr)[NS][RW]) {
       uint32_t ex[NS][V / 4];
 #pragma unroll
@@ -586,6 +705,17 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
 #pragma unroll
         for (int j = 0; j < NS; j++) ex[j][q] = __byte_perm(h[0][j], h[1][j], 0x5410);
       }
+      if constexpr (RING) {
+        // this thread's copies of step k have landed
+        cp_async_wait<RD - 1>();
+        const uint32_t sl = (k & (RD - 1u)) * NS;
+#pragma unroll
+        for (int j = 0; j < NS; j++)
+#pragma unroll
+          for (int q = 0; q < 3; q++)
+            rr[j][q] = ((rawm >> (q + 1)) & 1u) ? lds32v(ring + ((sl + j) * 3u + q) * rstride)
+                                               : cw[q + 1];
+      }
 #pragma unroll
       for (int j = 0; j < NS; j++) {
         const uint32_t v = vt[j] + k * T;
@@ -598,18 +728,24 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
           merge16r(ex[j][0], rr[j][0], x[0], x[1]);
           merge16r(ex[j][1 % (V / 4)], rr[j][1 % RW], x[2], x[3]);
         }
-        if (k + 2 < nper) load_raw_vec<DT>(rawp, rawm, cw, v + 2 * T, rr[j]);
+        if constexpr (!RING)
+          if (k + 2 < nper) load_raw_vec<DT>(rawp, rawm, cw, v + 2 * T, rr[j]);
         if (base) {
           const uint4 bb = __ldg(base + v);
           x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
         }
         dst[v] = make_uint4(x[0], x[1], x[2], x[3]);
       }
+      // FP32: the slot is free again (its words were consumed above)
+      if constexpr (RING) issue(k + RD);
     };
     for (uint32_t k = 0; k < nper; k += 2) {
+      if (DT == ZIPNN_FP32 && pfl && ((k >> 1) & wmask) == wid && k + D < nper)
+        prefetch_steps<G>(rawp, rawm, base8, T, k + D, min(k + D + 2u, nper));
       vec(k, ra);
       if (k + 1 < nper) vec(k + 1, rb);
     }
+    if constexpr (RING) cp_async_wait<0>();
     // every sub-stream ends where the next begins
 #pragma unroll
     for (int j = 0; j < NS; j++) {
@@ -695,7 +831,13 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
   }
   uint4* dst = reinterpret_cast<uint4*>(J.dst + off0);
   const uint4* base = J.base ? reinterpret_cast<const uint4*>(J.base + off0) : nullptr;
+  const uint8_t* base8 = J.base ? J.base + off0 : nullptr;
   uint32_t bad = 0;
+  // L2 prefetch window; steps [0, D) were requested when the chunk was set up.
+  // Lane 0 of warp (k / 2) mod (warps) requests steps k + D and k + D + 1.
+  const bool pfl = (tid & 31) == 0 && T == (uint32_t)(NS * nthr);
+  const uint32_t wid = (uint32_t)tid >> 5, wmask = ((uint32_t)nthr >> 5) - 1u;
+  const uint32_t D = pfl ? pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes) : 0u;
   for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
     FastReader R[NC][NS];
     uint32_t vt[NS];
@@ -781,6 +923,8 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
       }
     };
     for (uint32_t k = 0; k < nper; k += 2) {
+      if (pfl && ((k >> 1) & wmask) == wid && k + D < nper)
+        prefetch_steps<G>(rawp, rawm, base8, T, k + D, min(k + D + 2u, nper));
       vec(k, ra);
       if (k + 1 < nper) vec(k + 1, rb);
     }
@@ -980,6 +1124,21 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   }
   // exponent symbols are stored rotated for the fast loops' merge
   const bool rot0 = fast != 0 && DT != ZIPNN_U8;
+  // the fast loop's first L2 prefetch window, in flight while the tables are
+  // built (same raw groups and window as the loop computes)
+  if (fast != 0 && tid == 0 && T == (uint32_t)(fast * nthr)) {
+    const uint8_t* rawp[G];
+    uint32_t rawm = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      rawp[g] = J.src + CI.payload[g];
+      if (g >= fast_nc && CI.mode[g] == kRaw) rawm |= 1u << g;
+    }
+    const uint8_t* base8 = J.base ? J.base + c * J.chunk_bytes : nullptr;
+    const uint32_t nper = (J.chunk_bytes / 16u) / T;
+    prefetch_steps<G>(rawp, rawm, base8, T, 0u,
+                      pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes));
+  }
   // 3c. pair tables, in two passes.  Pass 1: for window w (W bits) the first
   // code has length l1 = 1 + #{l <= W : lim_W[l] <= w}; with W = 11 a first
   // code of 12 bits is resolved in the entry by its last bit.  Pass 2: the
@@ -1089,10 +1248,14 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
 }
 
 // DTS: the dtype of every job in the launch, or -1 for a mixed batch.
+// 256-thread CTAs: three per SM (80 registers) for the model-weight kernels;
+// two (128 registers) for the GEN kernels, whose delta loops decode two coded
+// groups and spill at 80.
 template <int DTS, int W, int NT, bool GEN>
-__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1)
+__global__ void __launch_bounds__(NT, NT == 256 ? (GEN ? 2 : 3) : 1)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
-         unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap) {
+         unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap,
+         uint32_t pf_bytes) {
   extern __shared__ __align__(128) uint8_t dsm[];  // [table slot 0] | stage
   __shared__ Smem S;
   __shared__ uint64_t bar;
@@ -1100,6 +1263,8 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   Staging stg;
   stg.base = dsm + (4u << W);
   stg.cap = stage_cap;
+  stg.pf_bytes = pf_bytes;
+  stg.ring = smem_u32(dsm + (4u << W) + stage_cap);
   stg.bar = &bar;
   stg.parity = 0;
   // debug flag 1 (tests only): expect 16 bytes more than the bulk copies send,
@@ -1140,7 +1305,7 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
 }
 
 using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, uint32_t,
-                             uint32_t);
+                             uint32_t, uint32_t);
 
 template <int W, int NT>
 DecodeKernel pick_kernel(int dt, bool gen) {
@@ -1169,17 +1334,19 @@ DecodeKernel pick_kernel(int dt, bool gen) {
 // Stage size: room for the payloads of the largest chunk (frac64 / 64 of it,
 // see stage_frac64), at most what lets two CTAs share an SM, and always room
 // for the tables of every Huffman group after the first.
-uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w) {
-  const uint64_t cap = (uint64_t)kStageCapPerSm / 2 - (4u << w) - kStaticReserve;
+uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w,
+                            uint32_t ring) {
+  const uint64_t cap = (uint64_t)kStageCapPerSm / 2 - (4u << w) - kStaticReserve - ring;
   const uint64_t want = (max_chunk * (uint64_t)frac64 / 64 + 1024 + 127) & ~127ull;
   uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > cap ? cap : want));
   const uint32_t tabs = (uint32_t)(max_groups - 1) * (4u << w) + 256u;
   return st > tabs ? st : tabs;
 }
 
-// Dynamic shared memory of one decode CTA: one table slot + the stage.
-int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups) {
-  return (4 << w) + (int)decode_stage_bytes(max_chunk, frac64, max_groups, w);
+// Dynamic shared memory of one decode CTA: one table slot, the stage and the
+// fast loops' raw-word rings.
+int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups, uint32_t ring) {
+  return (4 << w) + (int)decode_stage_bytes(max_chunk, frac64, max_groups, w, ring) + (int)ring;
 }
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
@@ -1218,8 +1385,11 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
   if (max_groups < 1 || max_groups > 4) max_groups = 4;
-  const uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w);
-  const int smem = decode_smem_bytes(w, max_chunk, frac64, max_groups);
+  // raw-word rings: launches that can hold FP32 chunks
+  const uint32_t ring =
+      (uniform_dtype == ZIPNN_FP32 || uniform_dtype < 0) ? kRingBytes * (uint32_t)threads : 0u;
+  const uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w, ring);
+  const int smem = decode_smem_bytes(w, max_chunk, frac64, max_groups, ring);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // all of the unified L1 / shared array as shared memory, so the CTAs per
@@ -1241,7 +1411,11 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     if (e != cudaSuccess) return e;
   }
   const uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
-  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, dbg, stage);
+  // the fast loops' L2 prefetch budget, shared by the CTAs that run at once
+  uint64_t pf = kPfBudget / grid;
+  if (pf > (64u << 20)) pf = 64u << 20;
+  kern<<<(unsigned)grid, threads, smem, st>>>(r, nchunks_total, d_err, d_ticket, dbg, stage,
+                                              (uint32_t)pf);
   return cudaGetLastError();
 }
 
