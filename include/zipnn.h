@@ -102,10 +102,13 @@ int zipnn_version(void);
 /* Text for a status code; never NULL. */
 const char* zipnn_strerror(int status);
 
-/* Sub-streams per Huffman group-chunk used when a call takes no lanes value:
- * chunk_bytes / 1024, clamped to [1, 1024]: one sub-stream per 64 vectors of
- * 16 bytes (256 lanes at 256 KiB for every dtype, so that a 256-thread decoder
- * CTA owns one sub-stream per thread). */
+/* Sub-streams per Huffman group-chunk used when a call takes no lanes value,
+ * for plain containers: chunk_bytes / 512 for BF16 and FP16 (512 at 256 KiB:
+ * two sub-streams per thread of a 256-thread decoder CTA, whose fast loop runs
+ * them in lockstep), chunk_bytes / 1024 for FP32 and U8; clamped to [1, 1024].
+ * Deltas (a base given, no lanes value) take chunk_bytes / 1024 for every
+ * dtype: their payloads are small, so the 4-byte start of every sub-stream
+ * weighs on the ratio. */
 uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes);
 
 /* Upper bound on the container size for nbytes of the given dtype and chunk

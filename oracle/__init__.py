@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
         L.or_canonical_codes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.or_default_lanes.argtypes = [ctypes.c_int, ctypes.c_uint32]
         L.or_default_lanes.restype = ctypes.c_uint32
+        L.or_default_lanes_delta.argtypes = [ctypes.c_int, ctypes.c_uint32]
+        L.or_default_lanes_delta.restype = ctypes.c_uint32
         L.or_bound.argtypes = [sz, ctypes.c_int, sz]
         L.or_bound.restype = sz
         L.or_compress.argtypes = [ctypes.c_void_p, sz, ctypes.c_int, sz, ctypes.c_uint32,
@@ -85,7 +87,9 @@ def _as_u8(x) -> np.ndarray:
     return a.view(np.uint8).reshape(-1)
 
 
-def default_lanes(dtype: int, chunk_bytes: int) -> int:
+def default_lanes(dtype: int, chunk_bytes: int, delta: bool = False) -> int:
+    if delta:
+        return int(lib().or_default_lanes_delta(dtype, chunk_bytes))
     return int(lib().or_default_lanes(dtype, chunk_bytes))
 
 
@@ -157,7 +161,7 @@ def delta(a, b, dtype: int, chunk_bytes: int = 256 * 1024, lanes: int | None = N
     if sa.size != sb.size:
         raise OracleError(EINVAL, "delta")
     if lanes is None:
-        lanes = default_lanes(dtype, chunk_bytes)
+        lanes = default_lanes(dtype, chunk_bytes, delta=True)
     cap = bound(sa.size, dtype, chunk_bytes) + 64
     out = np.zeros(cap, dtype=np.uint8)
     n = ctypes.c_size_t(0)

@@ -112,15 +112,23 @@ int or_elem_size(int dtype) {
 }
 int or_n_groups(int dtype) { return or_elem_size(dtype); }
 
-/* default interleave width: one sub-stream per 1 KiB of original data (64
- * vectors of 16 bytes) */
-uint32_t or_default_lanes(int dtype, uint32_t chunk_bytes) {
+/* default interleave width (a container parameter, no arithmetic of the
+ * method): plain 16-bit containers take one sub-stream per 512 bytes of
+ * original data (32 vectors of 16 bytes), FP32, U8 and deltas one per 1 KiB;
+ * clamped to [1, OR_MAX_LANES] */
+static uint32_t default_lanes(int dtype, uint32_t chunk_bytes, int delta) {
     int es = or_elem_size(dtype);
     if (es == 0) return 0;
-    uint32_t t = chunk_bytes / 1024u;
+    uint32_t t = chunk_bytes / ((es == 2 && !delta) ? 512u : 1024u);
     if (t < 1) t = 1;
     if (t > OR_MAX_LANES) t = OR_MAX_LANES;
     return t;
+}
+uint32_t or_default_lanes(int dtype, uint32_t chunk_bytes) {
+    return default_lanes(dtype, chunk_bytes, 0);
+}
+uint32_t or_default_lanes_delta(int dtype, uint32_t chunk_bytes) {
+    return default_lanes(dtype, chunk_bytes, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -80,7 +80,8 @@ def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_
     results = []
     dtype = Z.dtype_code(sample[0], None)
     for chunk, scale in [(c, k) for c in chunks for k in lane_scales]:
-        lanes = min(1024, Z.default_lanes(dtype, chunk) * scale, chunk // 16)
+        # one sub-stream per 1 KiB, or per 512 B, of each chunk
+        lanes = max(1, min(1024, chunk // 1024 * scale, chunk // 16))
         bc = Z.BatchCompressor(sample, chunk_bytes=chunk, lanes=lanes)
         bc()
         Z.sync_status()

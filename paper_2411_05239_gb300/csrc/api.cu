@@ -116,14 +116,6 @@ zipnn_status cuda_status(cudaError_t e) {
   return ZIPNN_ECUDA;
 }
 
-uint32_t lanes_default(int dtype, size_t chunk_bytes) {
-  (void)dtype;                       // the same for every dtype
-  uint64_t t = chunk_bytes / 1024u;  // one sub-stream per 64 vectors of 16 bytes
-  if (t < 1) t = 1;
-  if (t > ZIPNN_MAX_LANES) t = ZIPNN_MAX_LANES;
-  return (uint32_t)t;
-}
-
 Job make_job(const void* src, const void* base, void* dst, size_t nbytes, int dtype,
              size_t chunk_bytes, uint32_t lanes, uint32_t flags) {
   Job J;
@@ -197,6 +189,14 @@ Job decode_job(const zipnn_stream* s, const void* base, void* dst) {
 
 namespace zipnn {
 uint32_t* plan_err_word() { return err_word(); }
+
+uint32_t default_lanes_for(int dtype, size_t chunk_bytes, bool delta) {
+  const bool wide = !delta && (dtype == ZIPNN_BF16 || dtype == ZIPNN_FP16);
+  uint64_t t = chunk_bytes / (wide ? 512u : 1024u);
+  if (t < 1) t = 1;
+  if (t > ZIPNN_MAX_LANES) t = ZIPNN_MAX_LANES;
+  return (uint32_t)t;
+}
 }  // namespace zipnn
 
 extern "C" {
@@ -218,7 +218,7 @@ const char* zipnn_strerror(int status) {
 
 uint32_t zipnn_default_lanes(int dtype, size_t chunk_bytes) {
   if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8) return 0;
-  return lanes_default(dtype, chunk_bytes);
+  return default_lanes_for(dtype, chunk_bytes, false);
 }
 
 size_t zipnn_compress_bound(size_t nbytes, int dtype, size_t chunk_bytes) {
@@ -239,7 +239,8 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
                                  int dtype, size_t chunk_bytes, uint32_t lanes, void* d_out,
                                  size_t out_capacity, void* d_workspace, size_t workspace_bytes,
                                  uint64_t* d_out_nbytes, void* cuda_stream) {
-  if (lanes == 0 && dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8) lanes = lanes_default(dtype, chunk_bytes);
+  if (lanes == 0 && dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8)
+    lanes = default_lanes_for(dtype, chunk_bytes, d_base_or_null != nullptr);
   zipnn_status rc = check_params(dtype, nbytes, chunk_bytes, lanes);
   if (rc) return rc;
   if ((nbytes && !d_src) || !d_out || !aligned16(d_src) || !aligned16(d_out) ||
@@ -280,7 +281,10 @@ zipnn_status plan_batch_compress(const void* const* d_srcs, const void* const* d
   bp->jobs.resize((size_t)count);
   for (int i = 0; i < count; i++) {
     const int dt = dtypes[i];
-    const uint32_t ln = (lanes == 0 && dt >= ZIPNN_BF16 && dt <= ZIPNN_U8) ? lanes_default(dt, chunk_bytes) : lanes;
+    const bool dl = d_bases && d_bases[i];
+    const uint32_t ln = (lanes == 0 && dt >= ZIPNN_BF16 && dt <= ZIPNN_U8)
+                            ? default_lanes_for(dt, chunk_bytes, dl)
+                            : lanes;
     zipnn_status rc = check_params(dt, nbytes[i], chunk_bytes, ln);
     if (rc) return rc;
     const void* src = d_srcs ? d_srcs[i] : nullptr;
@@ -373,7 +377,9 @@ static zipnn_status compress_alloc(const void* d_src, const void* d_base, size_t
                                    size_t chunk_bytes, zipnn_stream* out, void* cuda_stream) {
   if (!out) return ZIPNN_EINVAL;
   memset(out, 0, sizeof(*out));
-  const uint32_t lanes = (dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8) ? lanes_default(dtype, chunk_bytes) : 0;
+  const uint32_t lanes = (dtype >= ZIPNN_BF16 && dtype <= ZIPNN_U8)
+                             ? default_lanes_for(dtype, chunk_bytes, d_base != nullptr)
+                             : 0;
   zipnn_status rc = check_params(dtype, nbytes, chunk_bytes, lanes);
   if (rc) return rc;
   if ((nbytes && !d_src) || !aligned16(d_src) || !aligned16(d_base)) return ZIPNN_EINVAL;

@@ -86,7 +86,7 @@ extern "C" zipnn_status zipnn_compress_into_static(const void* d_src, const void
                                                    size_t out_capacity, uint64_t* d_out_nbytes,
                                                    void* cuda_stream) {
   if (dtype < ZIPNN_BF16 || dtype > ZIPNN_U8) return ZIPNN_EINVAL;
-  if (lanes == 0) lanes = zipnn_default_lanes(dtype, chunk_bytes);
+  if (lanes == 0) lanes = zipnn::default_lanes_for(dtype, chunk_bytes, d_base_or_null != nullptr);
   const int es = elem_size(dtype);
   if (nbytes % es || chunk_bytes < ZIPNN_MIN_CHUNK || chunk_bytes > ZIPNN_MAX_CHUNK ||
       chunk_bytes % 16 || lanes < 1 || lanes > ZIPNN_MAX_LANES || lanes > chunk_bytes / 16)

@@ -160,7 +160,8 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
     const int dt = dtypes[i];
     if (dt != uniform) uniform = -1;
     if (dt < ZIPNN_BF16 || dt > ZIPNN_U8) return ZIPNN_EINVAL;
-    const uint32_t ln = lanes ? lanes : zipnn_default_lanes(dt, chunk_bytes);
+    const uint32_t ln =
+        lanes ? lanes : default_lanes_for(dt, chunk_bytes, d_bases && d_bases[i]);
     const int es = elem_size(dt);
     if (nbytes[i] % es || chunk_bytes < ZIPNN_MIN_CHUNK || chunk_bytes > ZIPNN_MAX_CHUNK ||
         chunk_bytes % 16 || ln < 1 || ln > ZIPNN_MAX_LANES || ln > chunk_bytes / 16)

@@ -149,6 +149,11 @@ struct EncodeScratch {
   uint64_t* totals;    // [njobs]
   uint32_t* zsyms;     // [ngc] symbols inside all-zero vectors (SPARSE candidate)
 };
+// Sub-streams per group-chunk when a call gives none: chunk_bytes / 512 for
+// plain 16-bit containers (two sub-streams per thread of a 256-thread decoder
+// CTA at 256 KiB), chunk_bytes / 1024 for FP32, U8 and deltas (whose payloads
+// are small enough for the start-bit tables to show); clamped to [1, 1024].
+uint32_t default_lanes_for(int dtype, size_t chunk_bytes, bool delta);
 size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njobs);
 void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total, int njobs,
                           EncodeScratch* s);

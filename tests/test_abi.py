@@ -44,10 +44,12 @@ def test_host_only_entry_points(lib):
     assert lib.zipnn_version() == 1
     lib.zipnn_default_lanes.restype = ctypes.c_uint32
     lib.zipnn_default_lanes.argtypes = [ctypes.c_int, ctypes.c_size_t]
-    assert lib.zipnn_default_lanes(0, 256 * 1024) == 256
+    assert lib.zipnn_default_lanes(0, 256 * 1024) == 512
+    assert lib.zipnn_default_lanes(1, 256 * 1024) == 512
     assert lib.zipnn_default_lanes(2, 256 * 1024) == 256
     assert lib.zipnn_default_lanes(3, 256 * 1024) == 256
-    assert lib.zipnn_default_lanes(0, 4096) == 4
+    assert lib.zipnn_default_lanes(0, 4096) == 8
+    assert lib.zipnn_default_lanes(0, 1 << 20) == 1024
     lib.zipnn_compress_bound.restype = ctypes.c_size_t
     lib.zipnn_compress_bound.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t]
     assert lib.zipnn_compress_bound(1 << 20, 0, 1 << 18) == 64 + 4 * 2 * 16 + (1 << 20) + 4 * 2 * 16
@@ -60,6 +62,8 @@ def test_lanes_rule_matches_oracle(lib):
     for dt in (0, 1, 2, 3):
         for c in (4096, 65536, 262144, 1 << 20, 16 << 20):
             assert lib.zipnn_default_lanes(dt, c) == O.default_lanes(dt, c)
+            # deltas: one sub-stream per 1 KiB for every dtype
+            assert O.default_lanes(dt, c, delta=True) == max(1, min(1024, c // 1024))
 
 
 def test_invalid_arguments_rejected_before_any_launch(lib):
