@@ -1140,35 +1140,45 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
                       pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes));
   }
   // 3c. pair tables, in two passes.  Pass 1: for window w (W bits) the first
-  // code has length l1 = 1 + #{l <= W : lim_W[l] <= w}; with W = 11 a first
-  // code of 12 bits is resolved in the entry by its last bit.  Pass 2: the
-  // second code is the first code of window (w << l1) & (2^W - 1) (the
-  // remaining W - l1 bits, zero-filled), kept when it fits in them.  Pass 2
-  // reads entries that other threads are turning into pairs; a pair keeps the
-  // first code's symbol and length where pass 2 reads them, so either value
-  // serves.
+  // code has length l1 = the least l <= W with w < lim_W[l] (W + 1 if none);
+  // with W = 11 a first code of 12 bits is resolved in the entry by its last
+  // bit.  Each warp fills a contiguous block of the table, lane j the entries
+  // j, j + 32, ... of it (conflict-free stores); along a lane w increases and
+  // l1 with it, so l1 advances from the previous entry's, with its limit and
+  // index[l1] - first[l1] held in registers.  Pass 2: the second code is the
+  // first code of window (w << l1) & (2^W - 1) (the remaining W - l1 bits,
+  // zero-filled), kept when it fits in them.  Pass 2 reads entries that other
+  // threads are turning into pairs; a pair keeps the first code's symbol and
+  // length where pass 2 reads them, so either value serves.
   if (!bad_tab) {
+    const uint32_t per_w = (uint32_t)kLut / ((uint32_t)nthr >> 5);
+    const uint32_t wb = ((uint32_t)tid >> 5) * per_w;
 #pragma unroll
     for (int g = 0; g < G; g++) {
       if (!coded_mode(CI.mode[g])) continue;
       const GroupTab& t = S.tab[g];
       const uint8_t* syms = reinterpret_cast<const uint8_t*>(t.words) + 12;
-      uint32_t limw[W + 1];
-#pragma unroll
-      for (int l = 1; l <= W; l++) limw[l] = t.lim[l] >> (kMaxLen - W);
       const bool rot = rot0 && g == 0;
       auto sym = [&](uint32_t r) -> uint32_t {
         const uint32_t v = syms[r & 255];
         return rot ? (((v >> 1) | (v << 7)) & 0xFFu) : v;
       };
+      auto lim_of = [&](uint32_t l) -> uint32_t {
+        return l <= (uint32_t)W ? (t.lim[l] >> (kMaxLen - W)) : 0xFFFFFFFFu;
+      };
       const uint32_t L = smem_u32(S.lut_ptr[g]);
-      for (int w = tid; w < kLut; w += nthr) {
-        uint32_t l1 = 1;
-#pragma unroll
-        for (int q = 1; q <= W; q++) l1 += (limw[q] <= (uint32_t)w);
+      uint32_t l1 = 1, lcur = lim_of(1), basel = t.index[1] - t.first[1];
+      for (uint32_t w = wb + ((uint32_t)tid & 31u); w < wb + per_w; w += 32) {
+        if (w >= lcur) {
+          do {
+            l1++;
+            lcur = lim_of(l1);
+          } while (w >= lcur);
+          basel = l1 <= (uint32_t)W ? t.index[l1] - t.first[l1] : 0u;
+        }
         uint32_t ent = 0;
         if (l1 <= (uint32_t)W) {
-          const uint32_t r1 = t.index[l1] + ((uint32_t)w >> (W - l1)) - t.first[l1];
+          const uint32_t r1 = basel + (w >> (W - l1));
           ent = sym(r1) | (l1 << 16) | (l1 << 27);
         } else if (W == 11) {
           // first code of 12 bits: w is its prefix, the next bit selects
@@ -1182,7 +1192,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
               ent |= kBadLong0 << nb;
           }
         }
-        sts32(L + 4u * (uint32_t)w, ent);
+        sts32(L + 4u * w, ent);
       }
     }
     __syncthreads();
