@@ -262,6 +262,88 @@ void finish_batch(zipnn_server* s, Batch* b) {
   delete b;
 }
 
+// Admission (the caller holds the lock): pending requests, in arrival order,
+// into a batch on a free slot while the budget allows.  Returns the batch, its
+// slot claimed and its requests counted in flight, ready for launch_batch
+// without the lock; nullptr when no slot is free, nothing is pending or the
+// head request does not fit now.  *never_fits: nothing is running or held and
+// the head request still does not fit (it never will).
+Batch* admit(zipnn_server* s, bool* never_fits) {
+  *never_fits = false;
+  int free_slot = -1;
+  for (int i = 0; i < (int)s->slots.size(); i++)
+    if (!s->slots[i].batch) { free_slot = i; break; }
+  if (free_slot < 0 || s->pending.empty()) return nullptr;
+  Batch* b = new Batch();
+  b->srv = s;
+  b->slot = free_slot;
+  std::vector<size_t> nbs;
+  std::vector<int> dts;
+  uint64_t chunk = 0;
+  while (!s->pending.empty() && b->reqs.size() < (size_t)kMaxBatch) {
+    Req* q = s->pending.front();
+    if (q->r.op == ZIPNN_OP_COMPRESS && chunk &&
+        (q->r.chunk_bytes ? q->r.chunk_bytes : ZIPNN_DEFAULT_CHUNK) != chunk)
+      break;  // a batch's compress requests share one chunk size
+    const uint64_t in = in_bytes(q->r), outn = out_bytes_needed(q->r);
+    if (s->charged + in + s->arena.used() + outn > s->budget) break;
+    uint64_t oo;
+    if (!s->arena.alloc(outn, &oo)) break;
+    q->out_off = oo;
+    q->out_size = outn;
+    s->charged += in;
+    q->in_charge = in;
+    q->t_admit = now_s();
+    s->pending.pop_front();
+    b->reqs.push_back(q);
+    if (q->r.op == ZIPNN_OP_COMPRESS) {
+      nbs.push_back(q->r.input_bytes);
+      dts.push_back(q->r.dtype);
+      chunk = q->r.chunk_bytes ? q->r.chunk_bytes : ZIPNN_DEFAULT_CHUNK;
+    }
+  }
+  // batch workspace for the compress requests
+  bool ok = true;
+  if (!nbs.empty()) {
+    const uint64_t ws =
+        zipnn_batch_compress_workspace_size(nbs.data(), dts.data(), (int)nbs.size(), chunk);
+    uint64_t wo = 0;
+    if (ws && s->charged + s->arena.used() + ws <= s->budget && s->arena.alloc(ws, &wo)) {
+      b->ws_off = wo;
+      b->ws_size = ws;
+    } else {
+      ok = false;
+    }
+  }
+  if (!ok) {
+    // not enough room for the scratch: hand the compress requests back
+    std::vector<Req*> keep;
+    for (auto it = b->reqs.rbegin(); it != b->reqs.rend(); ++it) {
+      Req* q = *it;
+      if (q->r.op == ZIPNN_OP_COMPRESS) {
+        s->arena.release(q->out_off, q->out_size);
+        s->charged -= q->in_charge;
+        q->in_charge = 0;
+        s->pending.push_front(q);
+      } else {
+        keep.push_back(q);
+      }
+    }
+    b->reqs.assign(keep.rbegin(), keep.rend());
+  }
+  if (b->reqs.empty()) {
+    delete b;
+    *never_fits = s->inflight == 0 && s->arena.used() == 0 && s->charged == 0;
+    return nullptr;
+  }
+  b->h_sizes = s->slots[free_slot].h_sizes;
+  s->slots[free_slot].batch = b;
+  s->inflight += b->reqs.size();
+  s->stats.batches++;
+  if (b->reqs.size() > s->stats.max_batch) s->stats.max_batch = b->reqs.size();
+  return b;
+}
+
 void scheduler(zipnn_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
@@ -283,100 +365,32 @@ void scheduler(zipnn_server* s) {
       s->cv.wait(lk);
       continue;
     }
-    int free_slot = -1;
-    for (int i = 0; i < (int)s->slots.size(); i++)
-      if (!s->slots[i].batch) { free_slot = i; break; }
-    if (free_slot >= 0 && !s->pending.empty()) {
-      // admit in arrival order while the budget allows
-      Batch* b = new Batch();
-      b->srv = s;
-      b->slot = free_slot;
-      std::vector<size_t> nbs;
-      std::vector<int> dts;
-      uint64_t chunk = 0;
-      while (!s->pending.empty() && b->reqs.size() < (size_t)kMaxBatch) {
-        Req* q = s->pending.front();
-        if (q->r.op == ZIPNN_OP_COMPRESS && chunk &&
-            (q->r.chunk_bytes ? q->r.chunk_bytes : ZIPNN_DEFAULT_CHUNK) != chunk)
-          break;  // a batch's compress requests share one chunk size
-        const uint64_t in = in_bytes(q->r), outn = out_bytes_needed(q->r);
-        if (s->charged + in + s->arena.used() + outn > s->budget) break;
-        uint64_t oo;
-        if (!s->arena.alloc(outn, &oo)) break;
-        q->out_off = oo;
-        q->out_size = outn;
-        s->charged += in;
-        q->in_charge = in;
-        q->t_admit = now_s();
-        s->pending.pop_front();
-        b->reqs.push_back(q);
-        if (q->r.op == ZIPNN_OP_COMPRESS) {
-          nbs.push_back(q->r.input_bytes);
-          dts.push_back(q->r.dtype);
-          chunk = q->r.chunk_bytes ? q->r.chunk_bytes : ZIPNN_DEFAULT_CHUNK;
-        }
-      }
-      // batch workspace for the compress requests (or per request on failure)
-      bool ok = true;
-      if (!nbs.empty()) {
-        const uint64_t ws = zipnn_batch_compress_workspace_size(nbs.data(), dts.data(),
-                                                                (int)nbs.size(), chunk);
-        uint64_t wo = 0;
-        if (ws && s->charged + s->arena.used() + ws <= s->budget && s->arena.alloc(ws, &wo)) {
-          b->ws_off = wo;
-          b->ws_size = ws;
-        } else {
-          ok = false;
-        }
-      }
-      if (!ok) {
-        // not enough room for the scratch: hand the compress requests back
-        std::vector<Req*> keep;
-        for (auto it = b->reqs.rbegin(); it != b->reqs.rend(); ++it) {
-          Req* q = *it;
-          if (q->r.op == ZIPNN_OP_COMPRESS) {
-            s->arena.release(q->out_off, q->out_size);
-            s->charged -= q->in_charge;
-            q->in_charge = 0;
-            s->pending.push_front(q);
-          } else {
-            keep.push_back(q);
-          }
-        }
-        b->reqs.assign(keep.rbegin(), keep.rend());
-      }
-      if (b->reqs.empty()) {
-        delete b;
-        if (s->inflight == 0 && s->arena.used() == 0 && s->charged == 0) {
-          // nothing running or held and the head request still does not fit:
-          // it can never fit, so fail it (unreachable after the submit check)
-          Req* q = s->pending.front();
-          s->pending.pop_front();
-          zipnn_completion c;
-          memset(&c, 0, sizeof(c));
-          c.id = q->id;
-          c.tag = q->r.tag;
-          c.status = ZIPNN_EBUSY;
-          c.op = q->r.op;
-          c.t_submit = q->t_submit;
-          c.t_done = now_s();
-          s->done.push_back(c);
-          s->live.erase(q->id);
-          delete q;
-          continue;
-        }
-      } else {
-        b->h_sizes = s->slots[free_slot].h_sizes;
-        s->slots[free_slot].batch = b;
-        s->inflight += b->reqs.size();
-        s->stats.batches++;
-        if (b->reqs.size() > s->stats.max_batch) s->stats.max_batch = b->reqs.size();
-        // launch without the lock: submitters and the slot waiters stay free
-        lk.unlock();
-        launch_batch(s, free_slot, b);
-        lk.lock();
-        continue;
-      }
+    bool never_fits = false;
+    Batch* b = admit(s, &never_fits);
+    if (b) {
+      // launch without the lock: submitters and the slot waiters stay free
+      lk.unlock();
+      launch_batch(s, b->slot, b);
+      lk.lock();
+      continue;
+    }
+    if (never_fits) {
+      // the head request can never fit: fail it (unreachable after the
+      // submit check)
+      Req* q = s->pending.front();
+      s->pending.pop_front();
+      zipnn_completion c;
+      memset(&c, 0, sizeof(c));
+      c.id = q->id;
+      c.tag = q->r.tag;
+      c.status = ZIPNN_EBUSY;
+      c.op = q->r.op;
+      c.t_submit = q->t_submit;
+      c.t_done = now_s();
+      s->done.push_back(c);
+      s->live.erase(q->id);
+      delete q;
+      continue;
     }
     s->cv.wait(lk);
   }
@@ -444,15 +458,29 @@ zipnn_status zipnn_server_submit(zipnn_server* s, const zipnn_request* r, uint64
   Req* q = new Req();
   q->r = *r;
   q->t_submit = now_s();
+  Batch* b = nullptr;
+  uint64_t qid = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    q->id = s->next_id++;
+    q->id = qid = s->next_id++;
     s->pending.push_back(q);
     s->live[q->id] = q;
     s->stats.submitted++;
+    // nothing queued ahead and a slot free: admit and launch on this thread,
+    // without waking the scheduler (its hand-off costs tens of microseconds)
+    bool never_fits = false;
+    if (!s->stop && s->pending.size() == 1) b = admit(s, &never_fits);
   }
-  s->cv.notify_all();
-  if (id) *id = q->id;
+  if (id) *id = qid;
+  if (b) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    launch_batch(s, b->slot, b);
+    if (prev != s->device && prev >= 0) cudaSetDevice(prev);
+  } else {
+    s->cv.notify_all();
+  }
   return ZIPNN_OK;
 }
 

@@ -174,3 +174,43 @@ def test_batches_with_and_without_deltas(with_delta, mixed_dtypes):
         Z.sync_status()
         for x, o in zip(xs, outs):
             assert np.array_equal(u8(o), u8(x)), nt
+
+
+def _modes(stream: bytes, chunk: int) -> list[tuple[int, int]]:
+    G = struct.unpack_from("<I", stream, 24)[0]
+    return [tuple(stream[64 + 16 * (chunk * G + g) + 12: 64 + 16 * (chunk * G + g) + 14])
+            for g in range(G)]
+
+
+@pytest.mark.parametrize("pattern", ["fp32_const_low", "fp32_zero_mid", "bf16_const_low"])
+def test_fast_loops_with_constant_and_zero_groups(pattern):
+    """The fast loops read raw groups through a per-thread shared-memory ring
+    (FP32) or registers (16-bit), prefetched into L2 by the chunk's window;
+    ZERO and CONST groups come from the map's value byte instead.  Three full
+    256 KiB chunks plus a ragged one, every CTA size and table width."""
+    if pattern.startswith("fp32"):
+        x = W.gaussian(3 * 65536 + 1000, 0.05, 99, torch.float32)
+        b = x.view(torch.int32)
+        b = (b & ~0xFF) | 0x5A if pattern == "fp32_const_low" else b & ~0xFF00
+        x, dt = b.view(torch.float32), Z.FP32
+        want_mode = (3, 0x5A) if pattern == "fp32_const_low" else (2, 0)
+        g_const = 3 if pattern == "fp32_const_low" else 2
+    else:
+        g = np.random.default_rng(100)
+        e = (0x7F - np.minimum(g.geometric(0.5, size=3 * 131072 + 777) - 1, 20)).astype(np.uint16)
+        x = torch.from_numpy(((e << 7) | 0x2A).view(np.int16)).view(torch.bfloat16)
+        dt, want_mode, g_const = Z.BF16, (3, 0x2A), 1
+    xs = u8(x)
+    c = Z.compress(x.cuda())
+    s = c.to_bytes()
+    assert s == O.compress(xs, dt, Z.DEFAULT_CHUNK)
+    for ch in range(3):
+        m = _modes(s, ch)
+        assert m[0][0] == 1 and m[g_const] == want_mode, (ch, m)
+    out = torch.empty_like(x, device="cuda")
+    for nt in (128, 256):
+        for w in (11, 12):
+            out.zero_()
+            Z.batch_decompress([c], [out], tune=Z.tuning(threads=nt, lut_bits=w))
+            Z.sync_status()
+            assert np.array_equal(u8(out), xs), (nt, w)

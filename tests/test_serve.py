@@ -2,7 +2,8 @@
 
 Each request's result must be the same alone and in the mix (tolerance: 0
 bytes), equal to the direct C-ABI result, and the admission must respect the
-budget while still batching concurrent requests.
+budget while still batching concurrent requests (a request that finds the
+server idle is launched on the submitting thread at once).
 """
 from __future__ import annotations
 
@@ -81,7 +82,16 @@ def test_results_identical_alone_and_in_the_mix():
     assert set(r_alone) == set(r_mix) == set(range(len(reqs)))
     for i in range(len(reqs)):
         assert r_alone[i] == r_mix[i], i
-    assert st.completed == len(reqs) and st.max_batch > 1
+    assert st.completed == len(reqs)
+    # one slot and room for all: a request submitted to an idle server is
+    # launched at once, the ones arriving while it runs queue and go out
+    # together as one batch
+    one = Z.Server(1 << 30, slots=1)
+    r_one = _run(one, reqs, containers, one_at_a_time=False)
+    st1 = one.stats()
+    one.close()
+    assert r_one == r_alone
+    assert st1.completed == len(reqs) and st1.max_batch > 1
     # the results are the codec's: containers equal the direct API's (and the
     # oracle's for a sample), decoded tensors equal their inputs
     for i, (op, x, base) in enumerate(reqs):
