@@ -16,13 +16,19 @@
 //      both fit in it (symbols and bits consumed), else its first code; with
 //      W = 11 a 12-bit first code is resolved in the entry by its last bit,
 //      with W = 10 longer first codes go through the canonical limits,
-//   4. decodes: thread t owns interleaved sub-stream t, i.e. the vectors
+//   4. decodes: thread t owns interleaved sub-streams t (and t + nthr when
+//      there are twice as many sub-streams as threads), i.e. the vectors
 //      v = t, t+T, ... of the chunk, so each warp step touches 32 consecutive
-//      16-byte vectors: raw-group loads (two vectors ahead of use) and the
-//      16-B output stores are fully coalesced; the inverse permutation and the
-//      XOR with a delta base happen in registers.  Chunks laid out as
-//      "exponent Huffman, every other group raw" (nearly every chunk of a
-//      model) take a specialised loop without per-group mode tests.
+//      16-byte vectors: raw-group loads and the 16-B output stores are fully
+//      coalesced; the inverse permutation and the XOR with a delta base happen
+//      in registers.  Chunks laid out as "exponent Huffman, every other group
+//      raw, zero or constant" (nearly every chunk of a model) take a
+//      specialised loop without per-group mode tests; its raw words arrive two
+//      steps ahead in registers (16-bit) or through a per-thread ring of
+//      asynchronous copies in shared memory (FP32), after a bulk L2 prefetch
+//      of the chunk's first steps issued while the tables are built.  Kernels
+//      for launches holding a delta (GEN) add the loops for a SPARSE exponent
+//      group and for two coded 16-bit groups.
 // The decoder is total: symbol counts are fixed by the map, bit reads past a
 // payload return zero bits, invalid codes and bad map entries set the error
 // word, and every loop is bounded; the wait for a bulk copy gives up after 2 s
@@ -517,14 +523,16 @@ __device__ __forceinline__ void bulk_prefetch_l2(const uint8_t* p, uint64_t byte
 }
 
 // The fast loops read the raw groups (and a delta's base) straight from
-// global memory, each thread two vectors ahead: too few bytes in flight per SM
-// to cover DRAM latency.  Step k of a fast loop consumes vectors [kT, (k+1)T)
-// of the chunk, i.e. a contiguous slice of T * 16/G bytes of every raw group
-// and T * 16 bytes of the base, so one thread of the CTA keeps the slices of
-// the next D steps in flight as bulk L2 prefetches.  D = the CTA's share of an
-// L2 budget (pf_bytes) over the bytes of one step, at least 2, at most the
-// whole chunk.  Only when one pass over the sub-streams covers every lane
-// (T == NS * nthr), so that all threads sweep the slices together.
+// global memory, each thread a few vectors ahead: too few bytes in flight per
+// SM to cover DRAM latency.  Step k of a fast loop consumes vectors
+// [kT, (k+1)T) of the chunk, i.e. a contiguous slice of T * 16/G bytes of
+// every raw group and T * 16 bytes of the base, so the slices of the first D
+// steps are requested into L2 as bulk prefetches while the tables are built,
+// and the FP32 and delta loops keep requesting D steps ahead of themselves.
+// D = the CTA's share of an L2 budget (pf_bytes) over the bytes of one step,
+// at least 2, at most the whole chunk.  Only when one pass over the
+// sub-streams covers every lane (T == NS * nthr), so that all threads sweep
+// the slices together.
 template <int G>
 __device__ __forceinline__ uint32_t pf_steps(uint32_t rawm, bool has_base, uint32_t T,
                                              uint32_t nper, uint32_t pf_bytes) {
@@ -548,9 +556,6 @@ __device__ __forceinline__ void prefetch_steps(const uint8_t* const (&rawp)[G], 
 // Per-thread asynchronous copies global -> shared (no registers held while in
 // flight); groups complete in the order they were committed.  The ring is
 // touched only by these volatile statements, whose order the compiler keeps.
-__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(g));
-}
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g));
 }
@@ -560,11 +565,6 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N));
-}
-__device__ __forceinline__ uint2 lds64(uint32_t saddr) {
-  uint2 v;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr));
-  return v;
 }
 __device__ __forceinline__ uint32_t lds32v(uint32_t saddr) {
   uint32_t v;
@@ -794,7 +794,8 @@ __device__ __forceinline__ uint32_t fast_pair(const FastGroup& F, FastReader& r,
 // t, t + nthr, ... (NS in lockstep, interleaved for instruction-level
 // parallelism); every vector is 16 B of output: V/2 pair lookups per coded
 // group (none for an all-zero vector of a SPARSE group), one load per raw
-// group (two vectors ahead), bit-select merge with the rotated exponent
+// group (two vectors ahead; the base at use, prefetched into L2 D steps
+// ahead), bit-select merge with the rotated exponent
 // symbols, a 16-B store.  No per-vector mode tests and no tails inside the
 // loop.  Each sub-stream must end exactly where the next one starts (the last
 // one within the bitstream); a mismatch flags the chunk as corrupt.
