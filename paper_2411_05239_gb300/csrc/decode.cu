@@ -562,6 +562,16 @@ __device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;");
 }
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ uint4 lds128(uint32_t saddr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(saddr));
+  return v;
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N));
@@ -794,8 +804,9 @@ __device__ __forceinline__ uint32_t fast_pair(const FastGroup& F, FastReader& r,
 // t, t + nthr, ... (NS in lockstep, interleaved for instruction-level
 // parallelism); every vector is 16 B of output: V/2 pair lookups per coded
 // group (none for an all-zero vector of a SPARSE group), one load per raw
-// group (two vectors ahead; the base at use, prefetched into L2 D steps
-// ahead), bit-select merge with the rotated exponent
+// group (two vectors ahead), the base from a per-thread ring of asynchronous
+// copies (RB steps ahead, and in L2 D steps ahead), bit-select merge with the
+// rotated exponent
 // symbols, a 16-B store.  No per-vector mode tests and no tails inside the
 // loop.  Each sub-stream must end exactly where the next one starts (the last
 // one within the bitstream); a mismatch flags the chunk as corrupt.
@@ -834,6 +845,11 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
   const uint4* base = J.base ? reinterpret_cast<const uint4*>(J.base + off0) : nullptr;
   const uint8_t* base8 = J.base ? J.base + off0 : nullptr;
   uint32_t bad = 0;
+  // delta base through a per-thread ring of 16-B asynchronous copies (RB steps
+  // ahead; slot sl, sub-stream j at ring + ((sl * NS + j) * nthr + tid) * 16)
+  constexpr uint32_t RB = kRingBytes / (NS * 16u) >= 4 ? 4u : 2u;
+  const uint32_t bring = stg.ring + (uint32_t)tid * 16u;
+  const uint32_t bstride = (uint32_t)nthr * 16u;
   // L2 prefetch window; steps [0, D) were requested when the chunk was set up.
   // Lane 0 of warp (k / 2) mod (warps) requests steps k + D and k + D + 1.
   const bool pfl = (tid & 31) == 0 && T == (uint32_t)(NS * nthr);
@@ -865,6 +881,20 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
         load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
         if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
       }
+    }
+    // base words of step k into ring slot k mod RB (one commit group per step)
+    auto issue_base = [&](uint32_t k) {
+      if (k < nper) {
+        const uint32_t sl = (k & (RB - 1u)) * NS;
+#pragma unroll
+        for (int j = 0; j < NS; j++)
+          cp_async16(bring + (sl + j) * bstride, base8 + 16ull * (vt[j] + k * T));
+      }
+      cp_async_commit();
+    };
+    if (base) {
+#pragma unroll
+      for (uint32_t k = 0; k < RB; k++) issue_base(k);
     }
     // vector k of every sub-stream; rr holds its raw words and receives those
     // of vector k + 2
@@ -899,6 +929,8 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
           for (int j = 0; j < NS; j++) ex[g][j][q] = __byte_perm(h[0][j], h[1][j], 0x5410);
         }
       }
+      // this thread's base copies of step k have landed
+      if (base) cp_async_wait<RB - 1>();
 #pragma unroll
       for (int j = 0; j < NS; j++) {
         const uint32_t v = vt[j] + k * T;
@@ -917,11 +949,13 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
         if constexpr (NC == 1)
           if (k + 2 < nper) load_raw_vec<DT>(rawp, rawm, cw, v + 2 * T, rr[j]);
         if (base) {
-          const uint4 bb = __ldg(base + v);
+          const uint4 bb = lds128(bring + ((k & (RB - 1u)) * NS + j) * bstride);
           x[0] ^= bb.x; x[1] ^= bb.y; x[2] ^= bb.z; x[3] ^= bb.w;
         }
         dst[v] = make_uint4(x[0], x[1], x[2], x[3]);
       }
+      // the base slot is free again: step k + RB
+      if (base) issue_base(k + RB);
     };
     for (uint32_t k = 0; k < nper; k += 2) {
       if (pfl && ((k >> 1) & wmask) == wid && k + D < nper)
@@ -929,6 +963,7 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
       vec(k, ra);
       if (k + 1 < nper) vec(k + 1, rb);
     }
+    if (base) cp_async_wait<0>();
     // every sub-stream ends where the next begins
 #pragma unroll
     for (int g = 0; g < NC; g++)
@@ -1396,9 +1431,12 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
   if (max_groups < 1 || max_groups > 4) max_groups = 4;
-  // raw-word rings: launches that can hold FP32 chunks
+  // per-thread rings: launches that can hold FP32 chunks (raw words) or
+  // deltas (base)
   const uint32_t ring =
-      (uniform_dtype == ZIPNN_FP32 || uniform_dtype < 0) ? kRingBytes * (uint32_t)threads : 0u;
+      (uniform_dtype == ZIPNN_FP32 || uniform_dtype < 0 || has_delta)
+          ? kRingBytes * (uint32_t)threads
+          : 0u;
   const uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w, ring);
   const int smem = decode_smem_bytes(w, max_chunk, frac64, max_groups, ring);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
