@@ -144,9 +144,13 @@ def barrier(world: int):
 
 
 def kernel_hash() -> str:
+    """Hash of the decoder's sources (decode*.cu, decode_kernels.cuh) and the
+    shared internal header."""
+    csrc = os.path.join(ROOT, "paper_2411_05239_gb300", "csrc")
+    files = sorted(f for f in os.listdir(csrc) if f.startswith("decode")) + ["zipnn_internal.cuh"]
     h = hashlib.sha256()
-    for f in ("decode.cu", "zipnn_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2411_05239_gb300", "csrc", f), "rb") as fh:
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
