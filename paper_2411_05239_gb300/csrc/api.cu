@@ -24,7 +24,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
                              int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta);
+                             bool has_delta, bool general, uint32_t stage_need);
 }  // namespace zipnn
 
 using namespace zipnn;
@@ -474,7 +474,7 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
                                    nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0,
                                    stage_frac64(s->dtype, s->flags),
-                                   (s->flags & ZIPNN_FLAG_DELTA) != 0);
+                                   (s->flags & ZIPNN_FLAG_DELTA) != 0, false, 0u);
   return cuda_status(e);
 }
 
@@ -519,7 +519,7 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
-                         uniform, max_chunk, lanes256, frac64, has_delta);
+                         uniform, max_chunk, lanes256, frac64, has_delta, false, 0u);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

@@ -13,29 +13,38 @@ const void* decode_kernel_w11_256(int dtype, bool gen);
 const void* decode_kernel_w12_128(int dtype, bool gen);
 const void* decode_kernel_w12_256(int dtype, bool gen);
 
-// Stage size: room for the payloads of the largest chunk (frac64 / 64 of it,
-// see stage_frac64), at most what lets two CTAs share an SM, and always room
-// for the tables of every Huffman group after the first.
-uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w,
-                            uint32_t ring) {
-  const uint64_t cap = (uint64_t)kStageCapPerSm / 2 - (4u << w) - kStaticReserve - ring;
-  const uint64_t want = (max_chunk * (uint64_t)frac64 / 64 + 1024 + 127) & ~127ull;
+namespace {
+
+// Stage size.  Without a measured need (stage_need = 0): room for the payloads
+// of the largest chunk (frac64 / 64 of it, see stage_frac64), at most what lets
+// two CTAs share an SM.  With one (a plan that read its containers' chunk
+// maps): exactly that many bytes, up to the whole SM when only one CTA per SM
+// can stage the payloads.  Always room for the tables of every Huffman group
+// after the first.  Multiples of 128 B, as the decoder's table placement
+// assumes.
+uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w, uint32_t ring,
+                            uint32_t stage_need) {
+  const uint64_t fixed = (4u << w) + kStaticReserve + ring;
+  uint64_t cap = (uint64_t)kStageCapPerSm / 2 - fixed;
+  uint64_t want;
+  if (stage_need) {
+    want = ((uint64_t)stage_need + 127) & ~127ull;
+    if (want > cap) cap = (uint64_t)kStageCapPerSm - fixed;
+  } else {
+    want = (max_chunk * (uint64_t)frac64 / 64 + 1024 + 127) & ~127ull;
+  }
   uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > cap ? cap : want));
   const uint32_t tabs = (uint32_t)(max_groups - 1) * (4u << w) + 256u;
   return st > tabs ? st : tabs;
 }
 
-// Dynamic shared memory of one decode CTA: one table slot, the stage and the
-// fast loops' raw-word rings.
-int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups, uint32_t ring) {
-  return (4 << w) + (int)decode_stage_bytes(max_chunk, frac64, max_groups, w, ring) + (int)ring;
-}
+}  // namespace
 
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
                              int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta) {
+                             bool has_delta, bool general, uint32_t stage_need) {
   if (nchunks_total == 0) return cudaSuccess;
   JobRef r;
   r.table = h_one ? nullptr : d_jobs;
@@ -58,13 +67,16 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   const int want = (tuning && tuning->threads) ? tuning->threads : 256;
   const int threads =
       (want == 256 && w >= 11 && uniform_dtype >= 0 && lanes256) ? 256 : kDecThreads;
-  // W = 10 has no fast loops and no delta kernels
+  // the GEN kernels for launches with deltas or, as a plan's chunk maps show,
+  // chunks with two coded groups or a SPARSE first group; W = 10 has no fast
+  // loops and no GEN kernels
+  const bool gen = has_delta || general;
   const void* kern =
       w == 10   ? decode_kernel_w10_128(uniform_dtype, false)
-      : w == 11 ? (threads == 256 ? decode_kernel_w11_256(uniform_dtype, has_delta)
-                                  : decode_kernel_w11_128(uniform_dtype, has_delta))
-                : (threads == 256 ? decode_kernel_w12_256(uniform_dtype, has_delta)
-                                  : decode_kernel_w12_128(uniform_dtype, has_delta));
+      : w == 11 ? (threads == 256 ? decode_kernel_w11_256(uniform_dtype, gen)
+                                  : decode_kernel_w11_128(uniform_dtype, gen))
+                : (threads == 256 ? decode_kernel_w12_256(uniform_dtype, gen)
+                                  : decode_kernel_w12_128(uniform_dtype, gen));
   int per_sm = 0;
   if (tuning && tuning->ctas_per_sm > 0) per_sm = tuning->ctas_per_sm;
   if (max_groups < 1 || max_groups > 4) max_groups = 4;
@@ -74,8 +86,8 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
       (uniform_dtype == ZIPNN_FP32 || uniform_dtype < 0 || has_delta)
           ? kRingBytes * (uint32_t)threads
           : 0u;
-  uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w, ring);
-  const int smem = decode_smem_bytes(w, max_chunk, frac64, max_groups, ring);
+  uint32_t stage = decode_stage_bytes(max_chunk, frac64, max_groups, w, ring, stage_need);
+  const int smem = (int)((4u << w) + stage + ring);  // one table slot | stage | rings
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // all of the unified L1 / shared array as shared memory, so the CTAs per

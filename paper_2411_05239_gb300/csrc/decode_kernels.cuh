@@ -44,11 +44,6 @@
 
 namespace zipnn {
 
-// Shared-memory sizing of a decode launch (decode.cu).
-uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w,
-                              uint32_t ring);
-int decode_smem_bytes(int w, uint64_t max_chunk, int frac64, int max_groups, uint32_t ring);
-
 namespace {
 
 constexpr int kDecThreads = 128;  // CTA size of mixed-dtype and W = 10 launches; else 256

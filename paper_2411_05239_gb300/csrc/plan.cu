@@ -25,7 +25,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
                              int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta);
+                             bool has_delta, bool general, uint32_t stage_need);
 uint32_t* plan_err_word();
 }  // namespace zipnn
 
@@ -44,6 +44,58 @@ struct zipnn_plan {
 namespace {
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// What a decode launch needs, read from its containers' chunk maps: per chunk
+// the shared-memory stage that holds its coded (HUFF / SPARSE) payloads, 16-B
+// padded, plus 32 B and the table of every coded group after the first (the
+// decoder's staging rule), and whether a chunk takes the general fast loops
+// (two coded groups, or a SPARSE first group).
+struct MapNeed {
+  uint64_t max_stage = 0;  // largest per-chunk need
+  uint64_t chunks = 0;     // chunks seen
+  uint64_t over = 0;       // chunks whose need exceeds the default stage
+  bool general = false;
+};
+
+void add_map_need(const uint8_t* map, uint32_t n_chunks, uint32_t G, int w, uint64_t dflt,
+                  MapNeed* nd) {
+  for (uint32_t c = 0; c < n_chunks; c++) {
+    uint64_t used = 0;
+    uint32_t ncoded = 0;
+    bool sparse0 = false;
+    for (uint32_t g = 0; g < G; g++) {
+      const uint8_t* e = map + ((uint64_t)c * G + g) * kEntryBytes;
+      uint32_t size;
+      memcpy(&size, e + 8, 4);
+      const uint32_t mode = e[12];
+      if (mode == kHuff || mode == kSparse) {
+        used += align_up(size, 16);
+        ncoded++;
+        if (g == 0 && mode == kSparse) sparse0 = true;
+      }
+    }
+    nd->chunks++;
+    if (ncoded) {
+      const uint64_t need = used + 32 + (uint64_t)(ncoded - 1) * (4u << w);
+      if (need > nd->max_stage) nd->max_stage = need;
+      if (need > dflt) nd->over++;
+    }
+    if (ncoded >= 2 || sparse0) nd->general = true;
+  }
+}
+
+// The stage a plan asks for: 0 (the launcher's default rule) while the default
+// stage holds the payloads of at least 99% of the chunks, else the largest
+// need (which may leave one CTA per SM: the only way to stage such chunks).
+uint32_t planned_stage(const MapNeed& nd) {
+  if (nd.over * 100 <= nd.chunks) return 0;
+  return (uint32_t)(nd.max_stage > 0xFFFFFFFFull ? 0xFFFFFFFFull : nd.max_stage);
+}
+
+int plan_lut_bits(const zipnn_tuning* tuning) {
+  int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 12;
+  return w < 10 ? 10 : (w > 12 ? 12 : w);
+}
 
 zipnn_status fail(zipnn_plan* p, cudaError_t e) {
   if (p) {
@@ -120,6 +172,23 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
     if ((int)s->n_groups > max_groups) max_groups = (int)s->n_groups;
     jobs[i] = J;
   }
+  // stage and kernel variant from the chunk maps present now
+  MapNeed nd;
+  {
+    const int w = plan_lut_bits(tuning);
+    const uint64_t dflt = max_chunk * (uint64_t)frac64 / 64 + 1024;
+    std::vector<uint8_t> mb;
+    for (int i = 0; i < count; i++) {
+      const zipnn_stream* s = &streams[i];
+      const uint64_t mbytes = (uint64_t)s->n_chunks * s->n_groups * kEntryBytes;
+      if (s->nbytes < kHdrBytes + mbytes) continue;  // malformed: the decoder reports it
+      mb.resize((size_t)mbytes);
+      if (mbytes && cudaMemcpy(mb.data(), static_cast<const uint8_t*>(s->data) + kHdrBytes,
+                               (size_t)mbytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ZIPNN_ECUDA;
+      add_map_need(mb.data(), s->n_chunks, s->n_groups, w, dflt, &nd);
+    }
+  }
   uint32_t* err = plan_err_word();
   if (!err) return ZIPNN_ECUDA;
   zipnn_plan* p = new zipnn_plan();
@@ -139,7 +208,8 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   if (tuning) tu = *tuning;
   e = capture(p, [&](cudaStream_t cs) {
     return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
-                            uniform, max_chunk, lanes256, frac64, has_delta);
+                            uniform, max_chunk, lanes256, frac64, has_delta, nd.general,
+                            planned_stage(nd));
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
@@ -306,6 +376,21 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       int max_groups = 1, uniform = jobs[a].dtype;
       bool lanes256 = true, has_delta = false;
       int frac64 = 0;
+      for (int i = a; i < b; i++) {
+        if (stage_frac64(jobs[i].dtype, jobs[i].flags) > frac64)
+          frac64 = stage_frac64(jobs[i].dtype, jobs[i].flags);
+        if (jobs[i].chunk_bytes > max_chunk) max_chunk = jobs[i].chunk_bytes;
+      }
+      // stage and kernel variant from the host copies' chunk maps
+      MapNeed nd;
+      const uint64_t dflt = max_chunk * (uint64_t)frac64 / 64 + 1024;
+      for (int i = a; i < b; i++) {
+        const zipnn_stream* s = &streams[i];
+        const uint64_t mbytes = (uint64_t)s->n_chunks * s->n_groups * kEntryBytes;
+        if (s->nbytes < kHdrBytes + mbytes) continue;
+        add_map_need(static_cast<const uint8_t*>(h_containers[i]) + kHdrBytes, s->n_chunks,
+                     s->n_groups, plan_lut_bits(&tu), dflt, &nd);
+      }
       for (int i = a; i < b && r == cudaSuccess; i++) {
         if (jobs[i].flags & ZIPNN_FLAG_DELTA) has_delta = true;
         if (stage_frac64(jobs[i].dtype, jobs[i].flags) > frac64)
@@ -322,7 +407,8 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);
       if (r == cudaSuccess)
         r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err, tickets + k,
-                             cs, uniform, max_chunk, lanes256, frac64, has_delta);
+                             cs, uniform, max_chunk, lanes256, frac64, has_delta, nd.general,
+                             planned_stage(nd));
     }
     // the last wait above joined the copy stream back into the capture stream
     return r;

@@ -214,3 +214,42 @@ def test_fast_loops_with_constant_and_zero_groups(pattern):
             Z.batch_decompress([c], [out], tune=Z.tuning(threads=nt, lut_bits=w))
             Z.sync_status()
             assert np.array_equal(u8(out), xs), (nt, w)
+
+
+@pytest.mark.parametrize("which", ["clean_fp16", "pruned_bf16", "clean_fp16_and_gauss"])
+def test_plans_size_their_stage_from_the_chunk_maps(which):
+    """A decode plan reads its containers' chunk maps: FP16 holding BF16
+    values codes both byte groups (about 170 KiB per 256 KiB chunk, more than
+    the default stage), so the plan stages them with one CTA per SM and runs
+    the two-group loop; pruned BF16 has SPARSE exponent groups.  Plans and load
+    plans must decode every byte as the direct calls do."""
+    if which == "clean_fp16":
+        xs = [W.clean_fp16_from_bf16(3 * 131072 + 999, 110)]
+    elif which == "pruned_bf16":
+        xs = [pruned_bf16(4 * 131072, 111)]
+    else:
+        xs = [W.clean_fp16_from_bf16(2 * 131072, 112), W.gaussian(3 * 131072 + 5, 0.02, 113,
+                                                                   torch.float16)]
+    cs = [Z.compress(x.cuda()) for x in xs]
+    for c, x in zip(cs, xs):
+        assert c.to_bytes() == O.compress(u8(x), Z.dtype_code(x, None), Z.DEFAULT_CHUNK)
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    for nt in (128, 256):
+        for o in outs:
+            o.zero_()
+        p = Z.plan_decompress(cs, outs, tune=Z.tuning(threads=nt))
+        p.launch()
+        Z.sync_status()
+        p.close()
+        for x, o in zip(xs, outs):
+            assert np.array_equal(u8(o), u8(x)), nt
+    h = [torch.from_numpy(np.frombuffer(c.to_bytes(), dtype=np.uint8).copy()).pin_memory()
+         for c in cs]
+    for o in outs:
+        o.zero_()
+    p = Z.plan_load(cs, h, outs)
+    p.launch()
+    Z.sync_status()
+    p.close()
+    for x, o in zip(xs, outs):
+        assert np.array_equal(u8(o), u8(x))
