@@ -235,7 +235,10 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
  * (new weights in the same buffers); creation synchronises the device once.
  *
  * zipnn_plan_decompress: the persistent decoder over all containers (work
- *   items pulled from a device ticket), as zipnn_batch_decompress.
+ *   items pulled from a device ticket), as zipnn_batch_decompress.  Creation
+ *   reads the containers' chunk maps (a device-to-host copy) to size the
+ *   decoder's shared-memory stage and pick its kernel variant; maps that
+ *   change later change the speed, never the decoded bytes.
  * zipnn_plan_compress: the four encoder kernels over all tensors, as
  *   zipnn_batch_compress_into, with the scratch owned by the plan.
  * Errors: EINVAL for bad arguments (as the corresponding direct calls),
@@ -260,7 +263,8 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
  *   about segment_bytes (0 = 512 MiB); each segment's persistent decode starts
  *   as soon as its copies have landed, while the copies of the next segments
  *   proceed on another stream: one graph, copies and decoding overlapped.
- *   Pageable host memory cannot be captured and returns ECUDA. */
+ *   Pageable host memory cannot be captured and returns ECUDA.  Creation
+ *   reads the host containers' chunk maps to size each segment's stage. */
 zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_containers,
                              const void* const* d_bases, void* const* d_dsts, int count,
                              size_t segment_bytes, const zipnn_tuning* tuning, zipnn_plan** out);
