@@ -39,7 +39,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t* g_err_ptr[kMaxDevices];
 
+// A caller-chosen error word for this thread's launches (the request server
+// gives each batch its own), else the device's.
+thread_local uint32_t* t_err_override = nullptr;
+
 uint32_t* err_word() {
+  if (t_err_override) return t_err_override;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -189,6 +194,7 @@ Job decode_job(const zipnn_stream* s, const void* base, void* dst) {
 
 namespace zipnn {
 uint32_t* plan_err_word() { return err_word(); }
+void set_thread_err_word(uint32_t* d_err) { t_err_override = d_err; }
 
 uint32_t default_lanes_for(int dtype, size_t chunk_bytes, bool delta) {
   const bool wide = !delta && (dtype == ZIPNN_BF16 || dtype == ZIPNN_FP16);

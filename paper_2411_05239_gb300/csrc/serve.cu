@@ -101,6 +101,8 @@ struct Slot {
   cudaStream_t st = nullptr;
   Batch* batch = nullptr;
   uint64_t* h_sizes = nullptr;  // pinned, mapped: container sizes of the slot's batch
+  uint32_t* d_err = nullptr;    // the device error word of the slot's batches
+  uint32_t* h_err = nullptr;    // pinned: its value after each batch
   // completion: the scheduler records `ev` after the batch and hands the batch
   // to this slot's waiter thread, which blocks on the event (lower latency than
   // a stream host callback) and then queues the batch as finished
@@ -119,6 +121,7 @@ struct Batch {
   uint64_t* h_sizes = nullptr;  // the slot's pinned size array
   double t_done = 0;
   int32_t launch_status = 0;
+  uint32_t dev_err = 0;  // the batch's device error word (decoder / encoder flags)
 };
 
 }  // namespace
@@ -176,6 +179,7 @@ void slot_waiter(zipnn_server* s, int si) {
     lk.unlock();
     cudaEventSynchronize(sl.ev);
     b->t_done = now_s();
+    b->dev_err = *sl.h_err;
     lk.lock();
     s->finished.push_back(b);
     s->cv.notify_all();
@@ -212,6 +216,9 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
     }
   }
   int32_t rc = ZIPNN_OK;
+  // the batch's kernels report into the slot's own error word
+  Slot& slot = s->slots[(size_t)si];
+  set_thread_err_word(slot.d_err);
   if (ncomp)
     rc = zipnn_batch_compress_into(csrc.data(), cbase.data(), cnb.data(), cdt.data(), (int)ncomp,
                                    chunk, 0, cout.data(), ccap.data(), s->arena_base + b->ws_off,
@@ -219,8 +226,11 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
   if (rc == ZIPNN_OK && !dstr.empty())
     rc = zipnn_batch_decompress(dstr.data(), dbase.data(), ddst.data(), (int)dstr.size(), nullptr,
                                 st);
+  set_thread_err_word(nullptr);
   b->launch_status = rc;
-  Slot& sl = s->slots[(size_t)si];
+  Slot& sl = slot;
+  cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaMemsetAsync(sl.d_err, 0, sizeof(uint32_t), st);
   cudaEventRecord(sl.ev, st);
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -231,9 +241,14 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
 
 void finish_batch(zipnn_server* s, Batch* b) {
   size_t ci = 0;
+  // a device-side error fails every request of its batch (the kernels share
+  // one error word per batch)
+  int32_t st = b->launch_status;
+  if (st == ZIPNN_OK && b->dev_err)
+    st = (b->dev_err & 1u) ? ZIPNN_ECORRUPT : ((b->dev_err & 2u) ? ZIPNN_ENOMEM : ZIPNN_ETIMEOUT);
   for (Req* q : b->reqs) {
     q->t_done = b->t_done;
-    q->status = b->launch_status;
+    q->status = st;
     if (q->r.op == ZIPNN_OP_COMPRESS) {
       q->out_bytes = b->h_sizes[ci++];
     } else {
@@ -419,10 +434,17 @@ zipnn_status zipnn_server_create(uint64_t budget_bytes, int slots, zipnn_server*
     cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
     sl.wcv.reset(new std::condition_variable());
-    if (!sl.ev || cudaHostAlloc(reinterpret_cast<void**>(&sl.h_sizes), sizeof(uint64_t) * kMaxBatch,
-                                cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    if (!sl.ev ||
+        cudaHostAlloc(reinterpret_cast<void**>(&sl.h_sizes), sizeof(uint64_t) * kMaxBatch,
+                      cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&sl.h_err), sizeof(uint32_t),
+                      cudaHostAllocPortable) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&sl.d_err), sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(sl.d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
       for (auto& s2 : s->slots) {
         if (s2.h_sizes) cudaFreeHost(s2.h_sizes);
+        if (s2.h_err) cudaFreeHost(s2.h_err);
+        if (s2.d_err) cudaFree(s2.d_err);
         if (s2.ev) cudaEventDestroy(s2.ev);
         if (s2.st) cudaStreamDestroy(s2.st);
       }
@@ -552,6 +574,8 @@ void zipnn_server_destroy(zipnn_server* s) {
     cudaEventDestroy(sl.ev);
     cudaStreamDestroy(sl.st);
     cudaFreeHost(sl.h_sizes);
+    cudaFreeHost(sl.h_err);
+    cudaFree(sl.d_err);
   }
   for (auto& kv : s->live) delete kv.second;
   cudaFree(s->arena_base);

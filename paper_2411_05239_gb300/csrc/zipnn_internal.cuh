@@ -154,6 +154,9 @@ struct EncodeScratch {
 // CTA at 256 KiB), chunk_bytes / 1024 for FP32, U8 and deltas (whose payloads
 // are small enough for the start-bit tables to show); clamped to [1, 1024].
 uint32_t default_lanes_for(int dtype, size_t chunk_bytes, bool delta);
+// Route the device error word of this host thread's launches to d_err (a
+// 4-byte device word), or back to the device's own word (nullptr).
+void set_thread_err_word(uint32_t* d_err);
 size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njobs);
 void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total, int njobs,
                           EncodeScratch* s);

@@ -135,3 +135,33 @@ def test_budget_is_respected_under_a_burst():
     for c in done:
         assert c.status == 0
     s.close()
+
+
+def test_corrupt_container_fails_its_request_and_the_server_goes_on():
+    """Each batch's kernels report into the batch's own device error word: a
+    container whose map entry names no valid mode completes with ECORRUPT,
+    and the next request (same slot) completes normally."""
+    import time
+    x = W.gaussian(300_000, 0.02, 3000, device="cuda")
+    c = Z.compress(x)
+    buf = c.device_tensor().clone()
+    buf[64 + 12] = 7                                    # invalid mode in the first map entry
+    bad = Z.wrap(buf)
+    s = Z.Server(1 << 28, slots=1)
+    got = {}
+    for tag, cont in ((0, bad), (1, c)):
+        s.submit_decompress(cont, tag=tag)
+        t_end = time.time() + 60
+        while tag not in got:
+            assert time.time() < t_end, "server did not finish"
+            for comp in s.poll():
+                got[comp.tag] = (comp.status, s.output(comp).cpu().numpy().tobytes()
+                                 if comp.status == 0 else None)
+                s.release(comp.id)
+            time.sleep(0.001)
+    s.close()
+    assert got[0][0] == -3                               # ZIPNN_ECORRUPT
+    assert got[1][0] == 0
+    assert got[1][1] == x.view(torch.uint8).cpu().numpy().tobytes()
+    # the library's own error word was not touched
+    Z.sync_status()
