@@ -10,22 +10,8 @@
 #include <cuda_runtime.h>
 
 #include "zipnn.h"
-#include "zipnn_internal.cuh"
+#include "host_internal.h"
 
-namespace zipnn {
-cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int njobs,
-                                     uint64_t nchunks_total, uint64_t ngc_total,
-                                     const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
-                                     int max_groups, int uniform_dtype);
-cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
-                                  uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st, int uniform_dtype);
-cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
-                             uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
-                             uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
-                             int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta, bool general, uint32_t stage_need);
-}  // namespace zipnn
 
 using namespace zipnn;
 

@@ -2,6 +2,7 @@
 // which calls the translation unit of the requested table width
 // (decode_w10/11/12.cu; the kernels are in decode_kernels.cuh).
 #include "decode_kernels.cuh"
+#include "host_internal.h"
 
 namespace zipnn {
 

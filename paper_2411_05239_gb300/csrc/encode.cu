@@ -17,7 +17,7 @@
 #include <cstring>
 #include <cuda_runtime.h>
 
-#include "zipnn_internal.cuh"
+#include "host_internal.h"
 
 namespace zipnn {
 

@@ -27,7 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "zipnn.h"
-#include "zipnn_internal.cuh"
+#include "host_internal.h"
 
 using namespace zipnn;
 
@@ -229,8 +229,9 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
   set_thread_err_word(nullptr);
   b->launch_status = rc;
   Slot& sl = slot;
+  // the word is read back after the batch; it is cleared (on the slot's
+  // stream, before its next batch) only when it was set
   cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-  cudaMemsetAsync(sl.d_err, 0, sizeof(uint32_t), st);
   cudaEventRecord(sl.ev, st);
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -244,8 +245,12 @@ void finish_batch(zipnn_server* s, Batch* b) {
   // a device-side error fails every request of its batch (the kernels share
   // one error word per batch)
   int32_t st = b->launch_status;
-  if (st == ZIPNN_OK && b->dev_err)
-    st = (b->dev_err & 1u) ? ZIPNN_ECORRUPT : ((b->dev_err & 2u) ? ZIPNN_ENOMEM : ZIPNN_ETIMEOUT);
+  if (b->dev_err) {
+    if (st == ZIPNN_OK)
+      st = (b->dev_err & 1u) ? ZIPNN_ECORRUPT : ((b->dev_err & 2u) ? ZIPNN_ENOMEM : ZIPNN_ETIMEOUT);
+    Slot& sl = s->slots[(size_t)b->slot];
+    cudaMemsetAsync(sl.d_err, 0, sizeof(uint32_t), sl.st);
+  }
   for (Req* q : b->reqs) {
     q->t_done = b->t_done;
     q->status = st;

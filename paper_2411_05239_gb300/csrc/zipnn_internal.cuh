@@ -137,36 +137,3 @@ __device__ __forceinline__ void merge32(const uint32_t g[4], uint32_t x[4]) {
 }
 
 }  // namespace zipnn
-
-// Host-side launchers (defined in the .cu files).
-namespace zipnn {
-struct EncodeScratch {
-  uint32_t* hist;      // [ngc][256]
-  uint32_t* codes;     // [ngc][256] (len << 16 | code)
-  uint8_t* tabs;       // [ngc][kTabBytes]
-  GcMeta* meta;        // [ngc]
-  uint64_t* offs;      // [ngc] payload offsets
-  uint64_t* totals;    // [njobs]
-  uint32_t* zsyms;     // [ngc] symbols inside all-zero vectors (SPARSE candidate)
-};
-// Sub-streams per group-chunk when a call gives none: chunk_bytes / 512 for
-// plain 16-bit containers (two sub-streams per thread of a 256-thread decoder
-// CTA at 256 KiB), chunk_bytes / 1024 for FP32, U8 and deltas (whose payloads
-// are small enough for the start-bit tables to show); clamped to [1, 1024].
-uint32_t default_lanes_for(int dtype, size_t chunk_bytes, bool delta);
-// Route the device error word of this host thread's launches to d_err (a
-// 4-byte device word), or back to the device's own word (nullptr).
-void set_thread_err_word(uint32_t* d_err);
-size_t encode_scratch_bytes(uint64_t nchunks_total, uint64_t ngc_total, int njobs);
-void encode_scratch_carve(void* base, uint64_t nchunks_total, uint64_t ngc_total, int njobs,
-                          EncodeScratch* s);
-cudaError_t launch_encode_analyse(const Job* d_jobs, int njobs, uint64_t nchunks_total,
-                                  uint64_t ngc_total, int max_groups, const EncodeScratch& s,
-                                  uint32_t* d_err, cudaStream_t st);
-cudaError_t launch_encode_pack(const Job* d_jobs, int njobs, uint64_t nchunks_total,
-                               int max_groups, int max_lanes, const EncodeScratch& s,
-                               uint32_t* d_err, cudaStream_t st);
-cudaError_t launch_decode(const Job* d_jobs, int njobs, uint64_t nchunks_total, int max_groups,
-                          int max_lanes, const zipnn_tuning* tuning, uint32_t* d_err,
-                          uint32_t* d_ticket, cudaStream_t st);
-}  // namespace zipnn
