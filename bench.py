@@ -541,10 +541,11 @@ def run_tensors(args):
         xs = [W.clean_fp16_from_bf16(device="cuda")]
         name = "clean_fp16_from_bf16_128mib"
     else:
-        n = sum(sp.numel for sp in W.delta_specs())
+        n = sum(sp.numel for sp in W.delta_specs(n_layers=args.delta_layers))
         nxt, base = W.delta_pair(n, seed=3, device="cuda")
         xs, bases = [nxt], [base]
-        name = "checkpoint_delta_1.7b_bf16"
+        name = ("checkpoint_delta_1.7b_bf16" if args.delta_layers == 24
+                else f"checkpoint_delta_bf16_{args.delta_layers}l")
     orig = sum(x.numel() * x.element_size() for x in xs)
     bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases, lanes=args.lanes)
     bc()
@@ -738,6 +739,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="checkpoint",
                     choices=["checkpoint", "serve", "plain", "fp32", "fp16", "delta",
                              "clean_fp32", "clean_fp16"])
+    ap.add_argument("--delta-layers", type=int, default=24,
+                    help="layers of the delta workload (24 = the 1.7B-parameter configuration)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
