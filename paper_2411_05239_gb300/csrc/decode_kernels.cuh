@@ -799,6 +799,28 @@ __device__ __forceinline__ uint32_t fast_pair(const FastGroup& F, FastReader& r,
   return e;
 }
 
+// fast_pair for a SPARSE group without a branch on the vector's bitmap bit:
+// every lane looks up the window at its position, and only lanes whose
+// vector holds a non-zero symbol (live) advance, report invalid codes and
+// keep the symbols (the warp's 32 vectors share one bitmap word, so a branch
+// would make the warp run both sides whenever its vectors mix).
+template <int W>
+__device__ __forceinline__ uint32_t fast_pair_if(const FastGroup& F, FastReader& r,
+                                                 const GroupTab& tb, uint32_t& bad, bool live) {
+  const uint8_t* syms = reinterpret_cast<const uint8_t*>(tb.words) + 12;
+  uint32_t b2 = 0;
+  const uint32_t e = pair_at<W>(__funnelshift_l(r.w1, r.w0, r.pos), F.lut, tb, syms, b2);
+  bad |= live ? b2 : 0u;
+  r.pos += live ? (e >> 27) : 0u;
+  if (r.pos >= 32u) {
+    r.pos -= 32u;
+    r.w0 = r.w1;
+    r.w1 = F.words[min(r.idx, F.wlim)];
+    r.idx++;
+  }
+  return live ? e : 0u;
+}
+
 // Fast loop for the other layouts of deltas, clean and pruned models: group 0
 // coded (HUFF or SPARSE) and staged; with NC = 2 (16-bit dtypes)
 // group 1 coded and staged too, else every group after the first raw, zero or
@@ -923,7 +945,7 @@ __device__ __forceinline__ void decode_fast_coded(const Job& J, uint64_t c, cons
 #pragma unroll
             for (int j = 0; j < NS; j++) {
               if (F[g].sparse)
-                h[p][j] = coded[j] ? fast_pair<W>(F[g], R[g][j], S.tab[g], bad) : 0u;
+                h[p][j] = fast_pair_if<W>(F[g], R[g][j], S.tab[g], bad, coded[j]);
               else
                 h[p][j] = fast_pair<W>(F[g], R[g][j], S.tab[g], bad);
             }
