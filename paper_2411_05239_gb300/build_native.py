@@ -3,7 +3,8 @@
 Each .cu translation unit is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and the objects are
 linked into ``paper_2411_05239_gb300/libzipnn_gpu.so``.  Used by
-``__graft_entry__.build()``; runs on x86 (cross-compile) and on the Arm GPU machine.
+``__graft_entry__.build()``; host code is portable C++ (no x86 intrinsics), so the
+same build runs on x86_64 (cross-compiling the device code) and on aarch64 hosts.
 """
 from __future__ import annotations
 
