@@ -555,7 +555,8 @@ def run_tensors(args):
     outs = [torch.empty_like(x) for x in xs]
     pc = Z.plan_compress(bc)
     pd = Z.plan_decompress(cs, outs, bases=bases,
-                           tune=Z.tuning(lut_bits=args.lut_bits, ctas_per_sm=args.ctas_per_sm))
+                           tune=Z.tuning(threads=args.threads, lut_bits=args.lut_bits,
+                                          ctas_per_sm=args.ctas_per_sm))
     pd.launch()
     Z.sync_status()
     for x, o in zip(xs, outs):
