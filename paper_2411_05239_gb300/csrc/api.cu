@@ -508,7 +508,10 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   if (e != cudaSuccess) return cuda_status(e);
   Job* d_jobs = static_cast<Job*>(dmem);
   unsigned long long* d_ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dmem) + tbytes);
-  e = g_ring.h2d(d_jobs, jobs.data(), tbytes, st);
+  // the job table and the two zeroed work-queue counters after it, in one copy
+  std::vector<uint8_t> up(tbytes + 16, 0);
+  memcpy(up.data(), jobs.data(), tbytes);
+  e = g_ring.h2d(d_jobs, up.data(), up.size(), st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
                          uniform, max_chunk, lanes256, frac64, has_delta, false, 0u);

@@ -105,10 +105,6 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   if (per_sm == 0 || per_sm > occ) per_sm = occ;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > nchunks_total) grid = nchunks_total;
-  if (d_ticket) {
-    e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-  }
   uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
   // the fast loops' L2 prefetch budget, shared by the CTAs that run at once
   uint64_t pf64 = kPfBudget / grid;

@@ -1370,8 +1370,20 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
         default: ok = decode_chunk<ZIPNN_U8, W, GEN>(J, c, S, lut0, stg, err); break;
       }
     }
-    if (!ok) return;  // a bulk copy timed out: leave the stage alone
+    if (!ok) break;  // a bulk copy timed out: leave the stage alone
     __syncthreads();
+  }
+  // the last CTA to leave resets the work queue for the next launch on the
+  // same buffer (ticket[0]: next work item, ticket[1]: CTAs done)
+  if (ticket) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      if (atomicAdd(ticket + 1, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+        atomicExch(ticket, 0ull);
+        atomicExch(ticket + 1, 0ull);
+      }
+    }
   }
 }
 

@@ -36,8 +36,9 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
                                   cudaStream_t st, int uniform_dtype);
 
 // Decoder (decode.cu): one persistent launch over all chunks of the jobs.
-// d_ticket: a device work-queue counter (reset by the launch), or nullptr for
-// a static assignment of chunks to CTAs.  frac64: stage size as a fraction of
+// d_ticket: the device work queue, two 64-bit counters that must be zero
+// before the first launch on them (the kernel's last CTA zeroes them again),
+// or nullptr for a static assignment of chunks to CTAs.  frac64: stage size as a fraction of
 // the largest chunk (stage_frac64); has_delta: some job has a base; general:
 // use the general fast loops (two coded groups, SPARSE first groups) even
 // without a delta; stage_need: a stage size measured from the chunk maps (0 =

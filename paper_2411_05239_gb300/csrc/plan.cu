@@ -187,6 +187,7 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
   Job* d_jobs = static_cast<Job*>(p->dmem);
   auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p->dmem) + tbytes);
   e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ticket, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) return fail(p, e);
   zipnn_tuning tu;
   memset(&tu, 0, sizeof(tu));
@@ -334,12 +335,13 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
   p->count = count;
   cudaGetDevice(&p->device);
   const size_t tbytes = align_up(sizeof(Job) * (size_t)count, 256);
-  const size_t kbytes = align_up(sizeof(unsigned long long) * (size_t)nseg, 256);
+  const size_t kbytes = align_up(2 * sizeof(unsigned long long) * (size_t)nseg, 256);
   cudaError_t e = cudaMalloc(&p->dmem, tbytes + kbytes);
   if (e != cudaSuccess) return fail(p, e);
   Job* d_jobs = static_cast<Job*>(p->dmem);
   auto* tickets = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p->dmem) + tbytes);
   e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(tickets, 0, kbytes);
   if (e != cudaSuccess) return fail(p, e);
   zipnn_tuning tu;
   memset(&tu, 0, sizeof(tu));
@@ -391,9 +393,9 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       if (r == cudaSuccess) r = cudaEventRecord(evs[(size_t)k], sc);
       if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);
       if (r == cudaSuccess)
-        r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err, tickets + k,
-                             cs, uniform, max_chunk, lanes256, frac64, has_delta, nd.general,
-                             planned_stage(nd));
+        r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err,
+                             tickets + 2 * k, cs, uniform, max_chunk, lanes256, frac64,
+                             has_delta, nd.general, planned_stage(nd));
     }
     // the last wait above joined the copy stream back into the capture stream
     return r;
