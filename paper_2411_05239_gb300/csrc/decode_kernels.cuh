@@ -144,6 +144,7 @@ struct Smem {
   GroupTab tab[4];
   uint32_t* lut_ptr[4];  // pair table of each Huffman group
   unsigned long long chunk;
+  int job;               // job of the CTA's previous work item
 };
 
 // Groups carried as Huffman sub-streams: HUFF, and SPARSE (the same after a
@@ -1343,7 +1344,10 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   stg.extra_tx = (debug_flags & 1u) ? 16u : 0u;
   stg.limit_ns = (debug_flags & 1u) ? 100000000ull : kWaitLimitNs;
   const int tid = threadIdx.x;
-  if (tid == 0) mbar_init(&bar);
+  if (tid == 0) {
+    mbar_init(&bar);
+    S.job = 0;
+  }
   __syncthreads();
   for (uint64_t iter = 0;; iter++) {
     // work item: from the device queue (batched form) or a static stride
@@ -1356,7 +1360,19 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
       chunk = blockIdx.x + iter * gridDim.x;
     }
     if (chunk >= nchunks_total) break;
-    const int j = jr.table ? find_job(jr.table, jr.n, chunk) : 0;
+    // the job of this chunk: work items come in increasing order, so scan
+    // forward from the previous item's job (a few steps; after eight, search)
+    int j = 0;
+    if (jr.table) {
+      j = S.job;
+      int steps = 0;
+      while (j + 1 < jr.n && jr.table[j + 1].chunk_begin <= chunk && steps < 8) {
+        j++;
+        steps++;
+      }
+      if (steps == 8) j += find_job(jr.table + j, jr.n - j, chunk);
+      if (tid == 0) S.job = j;
+    }
     const Job& J = jr.table ? jr.table[j] : jr.one;
     const uint64_t c = chunk - J.chunk_begin;
     bool ok;
