@@ -189,7 +189,8 @@ void slot_waiter(zipnn_server* s, int si) {
 // Launch one batch on slot `si` (called without the lock; the batch belongs to
 // the scheduler until the slot's waiter has seen it complete).
 void launch_batch(zipnn_server* s, int si, Batch* b) {
-  cudaStream_t st = s->slots[si].st;
+  Slot& slot = s->slots[(size_t)si];
+  cudaStream_t st = slot.st;
   std::vector<const void*> csrc, cbase;
   std::vector<size_t> cnb, ccap;
   std::vector<int> cdt;
@@ -217,7 +218,6 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
   }
   int32_t rc = ZIPNN_OK;
   // the batch's kernels report into the slot's own error word
-  Slot& slot = s->slots[(size_t)si];
   set_thread_err_word(slot.d_err);
   if (ncomp)
     rc = zipnn_batch_compress_into(csrc.data(), cbase.data(), cnb.data(), cdt.data(), (int)ncomp,
@@ -228,16 +228,15 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
                                 st);
   set_thread_err_word(nullptr);
   b->launch_status = rc;
-  Slot& sl = slot;
   // the word is read back after the batch; it is cleared (on the slot's
   // stream, before its next batch) only when it was set
-  cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-  cudaEventRecord(sl.ev, st);
+  cudaMemcpyAsync(slot.h_err, slot.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(slot.ev, st);
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    sl.launched = b;
+    slot.launched = b;
   }
-  sl.wcv->notify_one();
+  slot.wcv->notify_one();
 }
 
 void finish_batch(zipnn_server* s, Batch* b) {
