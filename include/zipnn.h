@@ -275,8 +275,8 @@ void zipnn_plan_destroy(zipnn_plan* plan);
  * decompress requests with admission against a device-memory budget.
  * zipnn_server_create allocates a device arena of budget_bytes (outputs and
  * scratch live there) and `slots` CUDA streams, and starts a scheduler thread
- * on the current device.  zipnn_server_submit (thread-safe, non-blocking)
- * queues a request; the scheduler admits requests in arrival order while their
+ * on the current device.  zipnn_server_submit (thread-safe, does not wait for
+ * the device) queues a request; the scheduler admits requests in arrival order while their
  * input bytes (caller-owned, charged only), output and scratch fit the budget
  * and a slot is free, and launches everything admitted in one pass as one
  * batch (one batched compression + one persistent batched decode) on that
@@ -284,7 +284,12 @@ void zipnn_plan_destroy(zipnn_plan* plan);
  * zipnn_server_poll returns completions; each output stays in the arena (and
  * charged) until zipnn_server_release.  A request whose footprint exceeds the
  * whole budget is refused at submit with EBUSY.  The caller's inputs must stay
- * valid until the request completes.  Times are seconds on a steady clock. */
+ * valid until the request completes.  A request that finds nothing queued and
+ * a slot free is admitted and launched on the submitting thread (the call
+ * then also returns after the launch, not only after queueing).  Completion
+ * status: the launch's status, else the batch's device error word (a corrupt
+ * container fails every request of its batch with ECORRUPT).  Times are
+ * seconds on the host's steady clock (std::chrono::steady_clock). */
 #define ZIPNN_OP_COMPRESS 0
 #define ZIPNN_OP_DECOMPRESS 1
 typedef struct zipnn_request {
@@ -301,7 +306,7 @@ typedef struct zipnn_request {
 typedef struct zipnn_completion {
     uint64_t id;           /* server id returned by submit */
     uint64_t tag;
-    int32_t status;        /* zipnn_status of the launch */
+    int32_t status;        /* zipnn_status of the request's batch */
     int32_t op;
     void* d_output;        /* container (compress) or tensor (decompress) in the arena */
     uint64_t output_bytes;
