@@ -89,6 +89,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+// Count `bytes` of the barrier's expected transaction bytes as arrived without
+// a copy (cancels bytes that were expected but never requested).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -1283,8 +1289,19 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   if (timed_out) atomicOr(&CI.bad, 2u);
   __syncthreads();
   if (CI.bad & 2u) {
-    if (tid == 0) atomicOr(err, 4u);
-    if (timed_out) mbar_wait(stg.bar, stg.parity ^ 1u, stg.limit_ns);  // copies may still land
+    // The wait gave up (ETIMEOUT).  Before the CTA leaves, drain the copies it
+    // issued, so that none of them can still write into this shared memory:
+    // thread 0 first cancels the bytes that were expected but never requested
+    // (the test-only fault injection), so the phase completes exactly when the
+    // real copies have landed; then every thread waits for it, again bounded.
+    // Only copies that themselves never finish end this second wait by its
+    // limit, and then the drain is best effort.
+    if (tid == 0) {
+      atomicOr(err, 4u);
+      if (stg.extra_tx) mbar_complete_tx(stg.bar, stg.extra_tx);
+    }
+    __syncthreads();
+    mbar_wait(stg.bar, stg.parity ^ 1u, stg.limit_ns);
     return false;
   }
   if (bad_tab) {
@@ -1350,29 +1367,31 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   }
   __syncthreads();
   for (uint64_t iter = 0;; iter++) {
-    // work item: from the device queue (batched form) or a static stride
-    uint64_t chunk;
-    if (ticket) {
-      if (tid == 0) S.chunk = atomicAdd(ticket, 1ull);
-      __syncthreads();
-      chunk = S.chunk;
-    } else {
-      chunk = blockIdx.x + iter * gridDim.x;
-    }
-    if (chunk >= nchunks_total) break;
-    // the job of this chunk: work items come in increasing order, so scan
-    // forward from the previous item's job (a few steps; after eight, search)
-    int j = 0;
-    if (jr.table) {
-      j = S.job;
-      int steps = 0;
-      while (j + 1 < jr.n && jr.table[j + 1].chunk_begin <= chunk && steps < 8) {
-        j++;
-        steps++;
+    // work item, from the device queue (batched form) or a static stride, and
+    // its job: thread 0 alone finds both and publishes them before the
+    // barrier; S.chunk and S.job are read by the others only after it, and
+    // written again only after the barrier that ends the iteration.  Work
+    // items come in increasing order, so the job is found by scanning forward
+    // from the previous item's job (a few steps; after eight, a search).
+    if (tid == 0) {
+      const uint64_t ch = ticket ? atomicAdd(ticket, 1ull) : blockIdx.x + iter * gridDim.x;
+      int jj = 0;
+      if (jr.table && ch < nchunks_total) {
+        jj = S.job;
+        int steps = 0;
+        while (jj + 1 < jr.n && jr.table[jj + 1].chunk_begin <= ch && steps < 8) {
+          jj++;
+          steps++;
+        }
+        if (steps == 8) jj += find_job(jr.table + jj, jr.n - jj, ch);
       }
-      if (steps == 8) j += find_job(jr.table + j, jr.n - j, chunk);
-      if (tid == 0) S.job = j;
+      S.chunk = ch;
+      S.job = jj;
     }
+    __syncthreads();
+    const uint64_t chunk = S.chunk;
+    if (chunk >= nchunks_total) break;
+    const int j = S.job;
     const Job& J = jr.table ? jr.table[j] : jr.one;
     const uint64_t c = chunk - J.chunk_begin;
     bool ok;
