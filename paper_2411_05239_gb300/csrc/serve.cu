@@ -321,32 +321,49 @@ Batch* admit(zipnn_server* s, bool* never_fits) {
       chunk = q->r.chunk_bytes ? q->r.chunk_bytes : ZIPNN_DEFAULT_CHUNK;
     }
   }
-  // batch workspace for the compress requests
+  // batch workspace for the compress requests.  Requests were admitted for
+  // their input and output bytes alone; when the workspace of all the batch's
+  // compress requests does not fit as well, requests go back to the front of
+  // the queue from the tail of the batch (arrival order kept) until it fits
+  // or a single compress request is left.  Only that one's own workspace can
+  // then fail to fit, and only while other requests hold memory (the submit
+  // check counts a request's workspace).
+  auto hand_back = [&](Req* q) {
+    s->arena.release(q->out_off, q->out_size);
+    s->charged -= q->in_charge;
+    q->in_charge = 0;
+    s->pending.push_front(q);
+  };
   bool ok = true;
-  if (!nbs.empty()) {
+  while (!nbs.empty()) {
     const uint64_t ws =
         zipnn_batch_compress_workspace_size(nbs.data(), dts.data(), (int)nbs.size(), chunk);
     uint64_t wo = 0;
     if (ws && s->charged + s->arena.used() + ws <= s->budget && s->arena.alloc(ws, &wo)) {
       b->ws_off = wo;
       b->ws_size = ws;
-    } else {
-      ok = false;
+      break;
     }
+    if (nbs.size() == 1) {
+      ok = false;
+      break;
+    }
+    Req* q = b->reqs.back();
+    b->reqs.pop_back();
+    if (q->r.op == ZIPNN_OP_COMPRESS) {
+      nbs.pop_back();
+      dts.pop_back();
+    }
+    hand_back(q);
   }
   if (!ok) {
-    // not enough room for the scratch: hand the compress requests back
+    // not even one compress request's workspace fits now: hand the compress
+    // requests back (the decompress requests of the batch still run)
     std::vector<Req*> keep;
     for (auto it = b->reqs.rbegin(); it != b->reqs.rend(); ++it) {
       Req* q = *it;
-      if (q->r.op == ZIPNN_OP_COMPRESS) {
-        s->arena.release(q->out_off, q->out_size);
-        s->charged -= q->in_charge;
-        q->in_charge = 0;
-        s->pending.push_front(q);
-      } else {
-        keep.push_back(q);
-      }
+      if (q->r.op == ZIPNN_OP_COMPRESS) hand_back(q);
+      else keep.push_back(q);
     }
     b->reqs.assign(keep.rbegin(), keep.rend());
   }
@@ -394,8 +411,9 @@ void scheduler(zipnn_server* s) {
       continue;
     }
     if (never_fits) {
-      // the head request can never fit: fail it (unreachable after the
-      // submit check)
+      // nothing runs or holds memory and the head request still does not
+      // fit: it never will (the submit check makes this unreachable for a
+      // request whose input, output and workspace fit the budget); fail it
       Req* q = s->pending.front();
       s->pending.pop_front();
       zipnn_completion c;

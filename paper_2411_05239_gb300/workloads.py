@@ -171,3 +171,29 @@ def request_trace(n: int = 2000, seed: int = 4, rate: float = 200.0,
 
 
 TORCH_DTYPE = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32}
+
+
+def serve_inputs(trace: list[Request], device="cuda"):
+    """Input tensors of a request trace: one pool per dtype, sized for the
+    largest request, holding plain N(0, 0.02) values and a delta pair made as
+    in ``delta_pair`` (a 30% perturbation at 1e-4, cast to the dtype); request
+    r takes the first r.nbytes bytes of its dtype's pool.  Returns a function
+    mapping a request to (tensor, base or None)."""
+    maxb = max(r.nbytes for r in trace) if trace else 0
+    pools = {}
+    for k, (dt, tdt) in enumerate(TORCH_DTYPE.items()):
+        es = torch.tensor([], dtype=tdt).element_size()
+        n = maxb // es + 1
+        nxt, base = delta_pair(n, seed=40 + k, device=device)
+        plain = gaussian(n, 0.02, seed=50 + k, dtype=tdt, device=device)
+        if tdt != torch.bfloat16:
+            nxt, base = nxt.to(tdt), base.to(tdt)
+        pools[dt] = (plain, nxt, base)
+
+    def inputs(r: Request):
+        es = {"bf16": 2, "fp16": 2, "fp32": 4}[r.dtype]
+        n = r.nbytes // es
+        plain, nxt, base = pools[r.dtype]
+        return (nxt[:n], base[:n]) if r.delta else (plain[:n], None)
+
+    return inputs

@@ -165,3 +165,123 @@ def test_corrupt_container_fails_its_request_and_the_server_goes_on():
     assert got[1][1] == x.view(torch.uint8).cpu().numpy().tobytes()
     # the library's own error word was not touched
     Z.sync_status()
+
+
+def test_batch_workspace_that_does_not_fit_hands_back_the_tail():
+    """Two compress requests whose inputs and outputs fit the budget together,
+    but whose combined encoder workspace does not: the admission pass that
+    takes both must hand the second back (arrival order kept) and run the
+    first alone, and both must complete.  A decompress request's output, held
+    until released, keeps both queued so that one pass sees them together."""
+    import ctypes
+    import time
+    torch.cuda.set_device(0)
+    chunk = Z.DEFAULT_CHUNK
+    n = 16 << 20                                  # elements: 32 MiB of BF16 each
+    nb = 2 * n
+    a256 = lambda v: (v + 255) // 256 * 256
+
+    def batch_ws(k):
+        sizes = (ctypes.c_size_t * k)(*([nb] * k))
+        dts = (ctypes.c_int * k)(*([Z.BF16] * k))
+        return int(Z.lib().zipnn_batch_compress_workspace_size(sizes, dts, k, chunk))
+
+    out = a256(Z.compress_bound(nb, Z.BF16, chunk))
+    ws1, ws2 = batch_ws(1), batch_ws(2)
+    assert ws2 - ws1 > 8192
+    budget = 2 * nb + 2 * out + ws2 - 4096        # both fit, their joint workspace does not
+    assert nb + out + ws1 <= budget               # the first alone does
+    x1 = W.gaussian(n, 0.02, 3100, device="cuda")
+    x2 = W.gaussian(n, 0.02, 3101, device="cuda")
+    # the blocker's output (held) leaves no room for the first compress request
+    n0 = (budget - nb - out) // 2 + (1 << 20)
+    x0 = W.gaussian(n0, 0.02, 3102, device="cuda")
+    c0 = Z.compress(x0)
+    assert c0.nbytes + a256(2 * n0) <= budget
+    s = Z.Server(budget, slots=1)
+    id0 = s.submit_decompress(c0, tag=0)
+    got, t_end = {}, time.time() + 60
+    while 0 not in got:
+        assert time.time() < t_end, "server did not finish"
+        for c in s.poll():
+            got[c.tag] = c
+        time.sleep(0.001)
+    assert got[0].status == 0
+    s.submit_compress(x1, tag=1)
+    s.submit_compress(x2, tag=2)
+    time.sleep(0.05)
+    assert s.poll() == []                         # both wait for the blocker's memory
+    s.release(id0)
+    res, t_end = {}, time.time() + 60
+    while len(res) < 2:
+        assert time.time() < t_end, "server did not finish"
+        for c in s.poll():
+            assert c.status == 0, (c.tag, c.status)
+            res[c.tag] = s.output(c).cpu().numpy().tobytes()
+            s.release(c.id)
+        time.sleep(0.001)
+    st = s.stats()
+    s.close()
+    assert st.max_batch == 1                      # the joint batch was split
+    assert res[1] == Z.compress(x1).to_bytes()
+    assert res[2] == Z.compress(x2).to_bytes()
+
+
+def test_served_stream_slice_at_real_sizes():
+    """The first 60 requests of the served-stream trace (seed 4) at their real
+    sizes (log-uniform 64 KiB - 2 GiB, BF16/FP16/FP32, 15% deltas), submitted
+    as one burst to a 4-slot server whose budget holds the largest request plus
+    1 GiB, so requests queue and batch.  Every compress result must equal the
+    direct C-ABI container byte for byte and match the oracle on sampled
+    chunks (first, last, one random); every decompress result must equal its
+    input."""
+    import time
+    from tests.test_gpu_parity import _check_sampled_chunks
+    torch.cuda.set_device(0)
+    trace = W.request_trace(seed=4)[:60]
+    inputs = W.serve_inputs(trace, device="cuda")
+    containers, need = {}, 0
+    a256 = lambda v: (v + 255) // 256 * 256
+    for r in trace:
+        x, b = inputs(r)
+        code = Z.dtype_code(x, None)
+        if r.op == "decompress":
+            containers[r.rid] = Z.compress(x, base=b)
+            need = max(need, containers[r.rid].nbytes + r.nbytes)
+        else:
+            need = max(need, r.nbytes + a256(Z.compress_bound(r.nbytes, code, Z.DEFAULT_CHUNK))
+                       + a256(Z.workspace_size(r.nbytes, code, Z.DEFAULT_CHUNK)))
+    assert max(r.nbytes for r in trace) > (1 << 30)       # the slice reaches GiB sizes
+    s = Z.Server(need + (1 << 30), slots=4)
+    for r in trace:
+        x, b = inputs(r)
+        if r.op == "compress":
+            s.submit_compress(x, base=b, tag=r.rid)
+        else:
+            s.submit_decompress(containers[r.rid], base=b, tag=r.rid)
+    rng = np.random.default_rng(4)
+    seen, t_end = set(), time.time() + 600
+    while len(seen) < len(trace):
+        assert time.time() < t_end, "server did not finish"
+        for c in s.poll():
+            assert c.status == 0, (c.tag, c.status)
+            r = trace[c.tag]
+            x, b = inputs(r)
+            got = s.output(c)
+            if r.op == "compress":
+                direct = Z.compress(x, base=b)
+                assert got.numel() == direct.nbytes
+                assert torch.equal(got, direct.device_tensor()), r.rid
+                data = x if b is None else (x.view(torch.uint8) ^ b.view(torch.uint8))
+                n = direct.zs.n_chunks
+                chunks = sorted({0, n - 1, int(rng.integers(0, n))})
+                _check_sampled_chunks(direct, data, Z.dtype_code(x, None), chunks)
+                del direct
+            else:
+                assert torch.equal(got, x.contiguous().view(-1).view(torch.uint8)), r.rid
+            seen.add(c.tag)
+            s.release(c.id)
+        time.sleep(0.001)
+    st = s.stats()
+    s.close()
+    assert st.completed == len(trace) and st.max_batch > 1
