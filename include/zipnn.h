@@ -154,8 +154,9 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
  * start-up).  Same arguments and output as zipnn_compress_into minus the
  * workspace: the scratch is a fixed 8 MiB device array inside the library
  * (held by every GPU that loads it until exit), so one call handles at most
- * 3,578 (chunk, byte group) pairs -- 447 MiB of BF16/FP16 or 223 MiB of FP32 at
- * 256 KiB chunks; larger inputs return ZIPNN_ENOMEM before any launch.  It
+ * 3,572 (chunk, byte group) pairs (2,348 bytes of scratch each) -- 446.5 MiB
+ * of BF16/FP16 or 223.25 MiB of FP32 at 256 KiB chunks, 3,572 chunks of U8;
+ * larger inputs return ZIPNN_ENOMEM before any launch.  It
  * calls no allocator.  All calls on a device share that array: calls whose
  * kernels overlap on the GPU (e.g. unordered streams) race and corrupt each
  * other's output, so order them.  The first call on a device looks up the
@@ -209,20 +210,40 @@ zipnn_status zipnn_batch_compress_into_ex(
  * 64 bytes).  The stream does not own d_data.  ECORRUPT if the header is bad. */
 zipnn_status zipnn_stream_wrap(const void* d_data, size_t nbytes, zipnn_stream* out);
 
-/* Original size and dtype of a container. */
+/* Original size and dtype of a container: the exact byte count that
+ * decompression gives back (Sec. 2.3, "Lossless compression": compression
+ * followed by decompression returns the input exactly), read from the header
+ * fields that the map of Sec. 5.1 ("Metadata and parallelism") travels with.
+ * Host-only; never touches the device.  EINVAL if s is NULL. */
 zipnn_status zipnn_decompressed_size(const zipnn_stream* s, size_t* nbytes, int* dtype);
 
-/* Decompress s into d_dst (caller-owned, exactly orig_nbytes bytes).
+/* Decompress s into d_dst (caller-owned, exactly orig_nbytes bytes): the
+ * inverse of compression, giving back the original bytes exactly (Sec. 2.3,
+ * "Lossless compression").  The chunk map (Sec. 5.1, "Metadata and
+ * parallelism") locates every chunk and byte group, so all chunks decode in
+ * parallel in one launch; each group is Huffman-decoded, copied (raw) or
+ * filled (zero, constant) and the groups are merged back into the dtype's
+ * byte order (the inverse of Sec. 3.1 / 3.2); a delta container is XOR-ed
+ * with its base (Sec. 4.2).
  * d_base_or_null must be the delta base (orig_nbytes) iff s is a delta
- * container, else NULL (EINVAL otherwise).  Chunks that fail validation on
- * the device are skipped and reported as ECORRUPT by zipnn_sync_status. */
+ * container, else NULL (EINVAL otherwise).  EINVAL also for a malformed
+ * stream descriptor, a dst_nbytes other than orig_nbytes or an unaligned
+ * pointer.  Chunks that fail validation on the device are skipped and
+ * reported as ECORRUPT by zipnn_sync_status. */
 zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null, void* d_dst,
                               size_t dst_nbytes, void* cuda_stream);
 
 /* Decompress count containers in ONE persistent kernel that pulls
- * (tensor, chunk) work items from a device queue (the batching form).
+ * (tensor, chunk) work items from a device queue (the batching form).  Each
+ * container decodes to exactly its original bytes (Sec. 2.3), as with
+ * zipnn_decompress; the chunk maps (Sec. 5.1, "Metadata and parallelism") make
+ * every chunk of every container an independent work item, which is what
+ * lets one grid serve tensors of uneven sizes (the paper's multi-worker
+ * decompression of Sec. 5.3 is the CPU counterpart).
  * streams[i] decodes into d_dsts[i]; d_bases may be NULL (no deltas) or hold
- * one base pointer (or NULL) per container.  tuning may be NULL. */
+ * one base pointer (or NULL) per container.  tuning may be NULL.  Errors as
+ * zipnn_decompress, per container; ENOMEM if the job table cannot be
+ * allocated (stream-ordered, freed after the launch). */
 zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* const* d_bases,
                                     void* const* d_dsts, int count, const zipnn_tuning* tuning,
                                     void* cuda_stream);

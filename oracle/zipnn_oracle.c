@@ -33,7 +33,12 @@
  *   - code lengths: package-merge (Larmore & Hirschberg 1990) limited to 12
  *     bits, leaves ordered by (count ascending, symbol descending), leaves
  *     before packages on equal weight; canonical codes as in RFC 1951 3.2.2;
- *     table as code-length counts followed by the symbols (JPEG DHT layout);
+ *     table as code-length counts followed by the symbols (JPEG DHT layout).
+ *     Two departures from the project's first plan for this step, both format
+ *     choices that change no code cost: equal counts are ordered by symbol
+ *     descending (the plan had ascending), and the selected lengths are used
+ *     as they come out of package-merge, with no second pass that re-sorts
+ *     symbols by count and re-deals the sorted lengths;
  *   - raw-vs-Huffman: exact per group-chunk decision with a 1/64 margin;
  *     the paper's skip-ahead probe (Sec. 3.2, "Identifying compressibility")
  *     is an option: after a group-chunk comes out raw, the same group of the

@@ -13,10 +13,14 @@
 // Costs and rules of the fixed array:
 //   - every GPU that loads the library holds kStaticScratchBytes (8 MiB) of it
 //     until the process exits;
-//   - one call may use at most that much scratch, which is 2,344 bytes per
-//     (chunk, byte group) pair plus 1.5 KiB: 3,578 pairs, e.g. 447 MiB of BF16
-//     or 223 MiB of FP32 at 256 KiB chunks; larger inputs are rejected with
-//     ZIPNN_ENOMEM before anything is launched;
+//   - one call may use at most that much scratch: 2,348 bytes per (chunk,
+//     byte group) pair (1 KiB histogram, 1 KiB code table, 272 B table bytes,
+//     16 B mode record, 8 B offset, 4 B zero count), each array rounded up to
+//     256 B, plus 512 B -- at most 3,572 pairs, e.g. 446.5 MiB of BF16/FP16 or
+//     223.25 MiB of FP32 at 256 KiB chunks; larger inputs are rejected with
+//     ZIPNN_ENOMEM before anything is launched (the check calls the same
+//     sizing function as the workspace entry point, so the figure cannot
+//     drift from the layout);
 //   - all calls on a device share the array and it keeps the last call's
 //     contents.  Nothing in it has to start at zero: every scratch word a call
 //     reads was written earlier by the same call.  Two calls whose kernels

@@ -67,9 +67,25 @@ def test_static_scratch_matches_workspace_entry_point_twice():
 
 def test_static_scratch_rejects_oversize_input():
     f = _static_fn()
-    # 448 MiB of BF16 at 256 KiB chunks = 1,792 chunks x 2 groups = 3,584 pairs > 3,578.
+    # 448 MiB of BF16 at 256 KiB chunks = 1,792 chunks x 2 groups = 3,584 pairs > 3,572.
     # The size check comes before any launch, so the tiny buffer is never touched.
     x = torch.empty(16, dtype=torch.uint8, device="cuda")
     rc = f(x.data_ptr(), None, 448 << 20, Z.BF16, 262144, 0, x.data_ptr(), 1 << 40, None,
            torch.cuda.current_stream().cuda_stream)
     assert rc == -2                      # ZIPNN_ENOMEM
+
+
+def test_static_scratch_limit_is_exact():
+    """The documented limit, 3,572 (chunk, byte group) pairs, is the real one:
+    U8 input has one group per chunk, so 3,572 chunks of 4 KiB are accepted
+    (and give the workspace entry point's bytes) and 3,573 are refused."""
+    f = _static_fn()
+    chunk = 4096
+    g = torch.Generator(device="cuda").manual_seed(34)
+    x = (torch.randn(3572 * chunk, device="cuda", generator=g) * 3).round().clamp(-128, 127)
+    x = x.to(torch.int8).view(torch.uint8)
+    assert _static(x, None, Z.U8, chunk) == _reference(x, None, chunk)
+    big = torch.empty(16, dtype=torch.uint8, device="cuda")
+    rc = f(big.data_ptr(), None, 3573 * chunk, Z.U8, chunk, 0, big.data_ptr(), 1 << 40, None,
+           torch.cuda.current_stream().cuda_stream)
+    assert rc == -2                      # ZIPNN_ENOMEM, before any launch
