@@ -359,3 +359,79 @@ def test_two_substreams_per_thread_path(lanes):
     y = Z.decompress(cs[0])
     Z.sync_status()
     assert torch.equal(y.cpu().view(torch.int16), xs[0].view(torch.int16))
+
+
+@pytest.mark.parametrize("name", __import__("tests.test_oracle_pins", fromlist=["x"]).GOLDEN_CONTAINERS)
+def test_gpu_writes_the_golden_containers(name):
+    """The hand-derived containers (tests/golden), including the three that sit
+    exactly on the mode decisions (raw threshold, one byte below it, SPARSE /
+    HUFF size tie): the GPU encoder must write them byte for byte and decode
+    them back."""
+    from tests.test_oracle_pins import _load_golden
+    f, want = _load_golden(name)
+    data = np.frombuffer(bytes.fromhex(f["input"].replace(" ", "")), dtype=np.uint8).copy()
+    dtype = int(f["dtype"])
+    x = torch.from_numpy(data).cuda()
+    c = Z.compress(x, chunk_bytes=int(f["chunk_bytes"]), lanes=int(f["lanes"]), dtype=dtype)
+    assert c.to_bytes().hex() == want.hex()
+    buf = torch.from_numpy(np.frombuffer(want, dtype=np.uint8).copy()).cuda()
+    y = Z.decompress(Z.wrap(buf))
+    Z.sync_status()
+    assert np.array_equal(u8(y), data)
+
+
+
+def _check_map_consistent(c: Z.Compressed):
+    """Every map offset is the sum of the 16-B padded payload sizes before it,
+    and the header's total is the payload offset plus all of them (the chunk
+    map of Sec. 5.1), for the whole container."""
+    P, G, ent = _map(c)
+    run = 0
+    for off, size, mode, value in ent:
+        assert off == run
+        run += (size + 15) // 16 * 16
+    hdr = c.device_tensor()[:64].cpu().numpy().tobytes()
+    total, = struct.unpack_from("<Q", hdr, 40)
+    assert total == P + run == c.nbytes
+
+
+def test_checkpoint_8b_timed_compress_plan_full_size():
+    """The path the benchmark times, at full size: BatchCompressor + the
+    graph-captured compression plan over all 290 tensors in ONE job table, at
+    256 KiB chunks and 512 lanes.  Every container's map must be consistent;
+    at least 3 chunks per tensor (the first, the last and random ones) of 20
+    tensors -- the embedding, both norms of a layer, the head and every kind of
+    projection -- must equal the oracle's chunk encoding byte for byte; then the
+    graph-captured persistent decode must give back every tensor exactly."""
+    specs = W.llama8b_specs()
+    ts = W.checkpoint_bf16(specs, seed=2, device="cuda")
+    bc = Z.BatchCompressor(ts, chunk_bytes=262144, lanes=512)
+    pc = Z.plan_compress(bc)
+    for o in bc.outs:
+        o.fill_(0xA5)                      # stale bytes cannot pass for output
+    pc.launch()
+    Z.sync_status()
+    cs = bc.containers()
+    assert all(c.zs.lanes == 512 and c.zs.chunk_bytes == 262144 for c in cs)
+    ratio = sum(c.nbytes for c in cs) / sum(t.numel() * 2 for t in ts)
+    assert 0.64 < ratio < 0.68
+    rng = np.random.default_rng(22)
+    names = [s.name for s in specs]
+    pick = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 145, 146, 149, 150, 200, 283, 286, 287, 288, 289]
+    assert names[0] == "embed" and names[8].endswith("norm1") and names[289] == "head"
+    for i in range(len(cs)):
+        if i in pick or i % 29 == 0:
+            _check_map_consistent(cs[i])
+    for i in pick:
+        c = cs[i]
+        n = c.zs.n_chunks
+        chunks = sorted({0, n - 1} | {int(v) for v in rng.integers(0, n, size=3)})
+        _check_sampled_chunks(c, ts[i], Z.BF16, chunks)
+    pc.close()
+    outs = [torch.empty_like(t) for t in ts]
+    pd = Z.plan_decompress(cs, outs)
+    pd.launch()
+    Z.sync_status()
+    for t, o in zip(ts, outs):
+        assert torch.equal(t.view(torch.int16), o.view(torch.int16))
+    pd.close()

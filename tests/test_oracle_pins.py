@@ -288,8 +288,12 @@ def _load_golden(name):
     return fields, bytes.fromhex("".join(stream))
 
 
-@pytest.mark.parametrize("name", ["bf16_two_symbols.txt", "fp32_four_groups.txt",
-                                  "u8_sparse_vectors.txt"])
+GOLDEN_CONTAINERS = ["bf16_two_symbols.txt", "fp32_four_groups.txt", "u8_sparse_vectors.txt",
+                     "u8_raw_at_threshold.txt", "u8_huff_below_threshold.txt",
+                     "u8_sparse_huff_tie.txt"]
+
+
+@pytest.mark.parametrize("name", GOLDEN_CONTAINERS)
 def test_golden_containers(name):
     f, want = _load_golden(name)
     data = np.frombuffer(bytes.fromhex(f["input"].replace(" ", "")), dtype=np.uint8)
