@@ -289,6 +289,36 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
 zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_containers,
                              const void* const* d_bases, void* const* d_dsts, int count,
                              size_t segment_bytes, const zipnn_tuning* tuning, zipnn_plan** out);
+/* Sharded decoding of one checkpoint over `world` GPUs (one process per GPU).
+ * ZipNN's chunks are independent and the map records every chunk and byte
+ * group (Sec. 5.1, "Chunking", "Metadata and parallelism"), so the chunks of
+ * `count` containers taken in order form one sequence of work items that
+ * ranks can split with no exchange.
+ *
+ * zipnn_partition_chunks (host only, calls no CUDA function): cuts that
+ *   sequence into `world` contiguous ranges of near-equal decode traffic; a
+ *   chunk weighs its stored payload bytes (16-B padded) plus its original
+ *   bytes.  h_maps[i] is a host copy of container i's first 64 + 16 *
+ *   n_chunks * n_groups bytes (header and map; a whole host container will
+ *   do), streams[i] its descriptor.  Writes world + 1 global chunk indices to
+ *   bounds: rank r owns chunks [bounds[r], bounds[r+1]); bounds[0] = 0 and
+ *   bounds[world] = the total.  Each range's weight is within one chunk's
+ *   weight of an equal share.  EINVAL for bad descriptors or world < 1,
+ *   ECORRUPT for a map entry with an unknown mode.
+ * zipnn_plan_decompress_range: as zipnn_plan_decompress, for the global
+ *   chunks [chunk_lo, chunk_hi) only.  For a container whose chunks
+ *   [a, b) (its own numbering) fall in the range, d_dsts[i] receives the
+ *   original bytes [a * chunk_bytes, min(b * chunk_bytes, orig_nbytes)) --
+ *   a buffer of just that extent, 16-B aligned -- and d_bases[i] (deltas)
+ *   holds the base's bytes of the same extent.  Containers with no chunk in
+ *   the range are ignored (their d_dsts entries may be NULL).  EINVAL if the
+ *   range is empty or runs past the last chunk. */
+zipnn_status zipnn_partition_chunks(const zipnn_stream* streams, const void* const* h_maps,
+                                    int count, int world, uint64_t* bounds);
+zipnn_status zipnn_plan_decompress_range(const zipnn_stream* streams, const void* const* d_bases,
+                                         void* const* d_dsts, int count, uint64_t chunk_lo,
+                                         uint64_t chunk_hi, const zipnn_tuning* tuning,
+                                         zipnn_plan** out);
 zipnn_status zipnn_plan_launch(zipnn_plan* plan, void* cuda_stream);
 void zipnn_plan_destroy(zipnn_plan* plan);
 

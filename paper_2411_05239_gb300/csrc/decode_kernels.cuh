@@ -1393,7 +1393,7 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     if (chunk >= nchunks_total) break;
     const int j = S.job;
     const Job& J = jr.table ? jr.table[j] : jr.one;
-    const uint64_t c = chunk - J.chunk_begin;
+    const uint64_t c = chunk - J.chunk_begin + J.chunk0;
     bool ok;
     if (DTS >= 0) {
       ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN>(J, c, S, lut0, stg, err);

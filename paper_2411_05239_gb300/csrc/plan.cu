@@ -113,38 +113,50 @@ cudaError_t capture(zipnn_plan* p, F body) {
 
 extern "C" {
 
-zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* const* d_bases,
-                                   void* const* d_dsts, int count, const zipnn_tuning* tuning,
-                                   zipnn_plan** out) {
-  if (!out || count <= 0 || !streams || !d_dsts) return ZIPNN_EINVAL;
+// Decode plan over the global chunk range [lo, hi) of the containers taken in
+// order as one sequence (all of it for zipnn_plan_decompress; a rank's share
+// for zipnn_plan_decompress_range).  A container whose chunks fall partly in
+// the range becomes a job over those chunks only (Job.chunk0), and its
+// destination (and base) pointer is shifted so that the kernel's
+// dst + chunk * chunk_bytes lands in the caller's buffer of the range.
+static zipnn_status plan_decode_range(const zipnn_stream* streams, const void* const* d_bases,
+                                      void* const* d_dsts, int count, uint64_t lo, uint64_t hi,
+                                      const zipnn_tuning* tuning, zipnn_plan** out) {
+  if (!out || count <= 0 || !streams || !d_dsts || lo > hi) return ZIPNN_EINVAL;
   *out = nullptr;
-  std::vector<Job> jobs((size_t)count);
-  uint64_t chunk = 0, max_chunk = 0;
+  std::vector<Job> jobs;
+  std::vector<const zipnn_stream*> used;
+  uint64_t chunk = 0, max_chunk = 0, g = 0;
   int max_groups = 1;
-  int uniform = streams[0].dtype;
+  int uniform = -2;
   bool lanes256 = true, has_delta = false;
   int frac64 = 0;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
-    if (s->flags & ZIPNN_FLAG_DELTA) has_delta = true;
-    if (s->dtype != uniform) uniform = -1;
-    if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
-    if (s->lanes % 256) lanes256 = false;
-    if (stage_frac64(s->dtype, s->flags) > frac64) frac64 = stage_frac64(s->dtype, s->flags);
-    if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
-    const void* base = d_bases ? d_bases[i] : nullptr;
-    if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
-    if ((s->orig_nbytes && !d_dsts[i]) || !aligned16(d_dsts[i]) || !aligned16(base))
-      return ZIPNN_EINVAL;
     if (s->n_groups != (uint32_t)elem_size(s->dtype) || s->dtype < 0 || s->dtype > ZIPNN_U8 ||
         s->lanes < 1 || s->lanes > ZIPNN_MAX_LANES || s->chunk_bytes < ZIPNN_MIN_CHUNK ||
         (uint64_t)s->n_chunks != (s->orig_nbytes + s->chunk_bytes - 1) / s->chunk_bytes)
       return ZIPNN_EINVAL;
+    const uint64_t a = lo > g ? lo - g : 0;
+    const uint64_t b = hi < g + s->n_chunks ? (hi > g ? hi - g : 0) : s->n_chunks;
+    g += s->n_chunks;
+    if (a >= b) continue;  // no chunk of this container in the range
+    if (!s->data || !aligned16(s->data)) return ZIPNN_EINVAL;
+    const void* base = d_bases ? d_bases[i] : nullptr;
+    if (((s->flags & ZIPNN_FLAG_DELTA) != 0) != (base != nullptr)) return ZIPNN_EINVAL;
+    if (!d_dsts[i] || !aligned16(d_dsts[i]) || !aligned16(base)) return ZIPNN_EINVAL;
+    if (s->flags & ZIPNN_FLAG_DELTA) has_delta = true;
+    uniform = (uniform == -2 || uniform == s->dtype) ? s->dtype : -1;
+    if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
+    if (s->lanes % 256) lanes256 = false;
+    if (stage_frac64(s->dtype, s->flags) > frac64) frac64 = stage_frac64(s->dtype, s->flags);
+    const uintptr_t shift = (uintptr_t)(a * s->chunk_bytes);
     Job J;
     memset(&J, 0, sizeof(J));
     J.src = static_cast<const uint8_t*>(s->data);
-    J.base = static_cast<const uint8_t*>(base);
-    J.dst = static_cast<uint8_t*>(d_dsts[i]);
+    J.base = base ? reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(base) - shift)
+                  : nullptr;
+    J.dst = reinterpret_cast<uint8_t*>(reinterpret_cast<uintptr_t>(d_dsts[i]) - shift);
     J.nbytes = s->orig_nbytes;
     J.chunk_bytes = s->chunk_bytes;
     J.lanes = s->lanes;
@@ -153,53 +165,94 @@ zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* cons
     J.flags = s->flags;
     J.stream_bytes = s->nbytes;
     J.chunk_begin = chunk;
-    chunk += J.n_chunks;
+    J.chunk0 = (uint32_t)a;
+    chunk += b - a;
     if ((int)s->n_groups > max_groups) max_groups = (int)s->n_groups;
-    jobs[i] = J;
+    jobs.push_back(J);
+    used.push_back(s);
   }
+  if (hi > g) return ZIPNN_EINVAL;
+  if (jobs.empty()) return ZIPNN_EINVAL;  // nothing to decode in the range
+  const int njobs = (int)jobs.size();
   // stage and kernel variant from the chunk maps present now
   MapNeed nd;
   {
     const int w = plan_lut_bits(tuning);
     const uint64_t dflt = max_chunk * (uint64_t)frac64 / 64 + 1024;
     std::vector<uint8_t> mb;
-    for (int i = 0; i < count; i++) {
-      const zipnn_stream* s = &streams[i];
+    for (int k = 0; k < njobs; k++) {
+      const zipnn_stream* s = used[(size_t)k];
       const uint64_t mbytes = (uint64_t)s->n_chunks * s->n_groups * kEntryBytes;
       if (s->nbytes < kHdrBytes + mbytes) continue;  // malformed: the decoder reports it
       mb.resize((size_t)mbytes);
       if (mbytes && cudaMemcpy(mb.data(), static_cast<const uint8_t*>(s->data) + kHdrBytes,
                                (size_t)mbytes, cudaMemcpyDeviceToHost) != cudaSuccess)
         return ZIPNN_ECUDA;
-      add_map_need(mb.data(), s->n_chunks, s->n_groups, w, dflt, &nd);
+      const Job& J = jobs[(size_t)k];
+      const uint64_t n = k + 1 < njobs ? jobs[(size_t)k + 1].chunk_begin - J.chunk_begin
+                                       : chunk - J.chunk_begin;
+      add_map_need(mb.data() + (uint64_t)J.chunk0 * s->n_groups * kEntryBytes, (uint32_t)n,
+                   s->n_groups, w, dflt, &nd);
     }
   }
   uint32_t* err = plan_err_word();
   if (!err) return ZIPNN_ECUDA;
   zipnn_plan* p = new zipnn_plan();
   p->kind = 1;
-  p->count = count;
+  p->count = njobs;
   p->nchunks = chunk;
   cudaGetDevice(&p->device);
-  const size_t tbytes = align_up(sizeof(Job) * (size_t)count, 256);
+  const size_t tbytes = align_up(sizeof(Job) * (size_t)njobs, 256);
   cudaError_t e = cudaMalloc(&p->dmem, tbytes + 256);
   if (e != cudaSuccess) return fail(p, e);
   Job* d_jobs = static_cast<Job*>(p->dmem);
   auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(p->dmem) + tbytes);
-  e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ticket, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) return fail(p, e);
   zipnn_tuning tu;
   memset(&tu, 0, sizeof(tu));
   if (tuning) tu = *tuning;
+  const int uni = uniform < 0 ? -1 : uniform;
   e = capture(p, [&](cudaStream_t cs) {
-    return launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, &tu, err, ticket, cs,
-                            uniform, max_chunk, lanes256, frac64, has_delta, nd.general,
+    return launch_decode_ex(d_jobs, nullptr, njobs, chunk, max_groups, &tu, err, ticket, cs, uni,
+                            max_chunk, lanes256, frac64, has_delta, nd.general,
                             planned_stage(nd));
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
   return ZIPNN_OK;
+}
+
+zipnn_status zipnn_plan_decompress(const zipnn_stream* streams, const void* const* d_bases,
+                                   void* const* d_dsts, int count, const zipnn_tuning* tuning,
+                                   zipnn_plan** out) {
+  if (!out || count <= 0 || !streams || !d_dsts) return ZIPNN_EINVAL;
+  uint64_t total = 0;
+  for (int i = 0; i < count; i++) {
+    total += streams[i].n_chunks;
+    // every container decodes in full: its destination must be given (an
+    // empty tensor has no chunks and needs none)
+    if (streams[i].orig_nbytes && !d_dsts[i]) return ZIPNN_EINVAL;
+  }
+  if (total == 0) {
+    // only empty containers: a plan whose launch does nothing
+    zipnn_plan* p = new zipnn_plan();
+    p->kind = 1;
+    cudaGetDevice(&p->device);
+    cudaError_t e = capture(p, [&](cudaStream_t) { return cudaSuccess; });
+    if (e != cudaSuccess) return fail(p, e);
+    *out = p;
+    return ZIPNN_OK;
+  }
+  return plan_decode_range(streams, d_bases, d_dsts, count, 0, total, tuning, out);
+}
+
+zipnn_status zipnn_plan_decompress_range(const zipnn_stream* streams, const void* const* d_bases,
+                                         void* const* d_dsts, int count, uint64_t chunk_lo,
+                                         uint64_t chunk_hi, const zipnn_tuning* tuning,
+                                         zipnn_plan** out) {
+  return plan_decode_range(streams, d_bases, d_dsts, count, chunk_lo, chunk_hi, tuning, out);
 }
 
 zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d_bases,

@@ -64,6 +64,11 @@ struct Job {
   int32_t dtype;
   uint32_t flags;
   uint32_t skip;          // compress: skip-ahead probe window (0 = exact decisions)
+  uint32_t chunk0;        // decompress: first chunk of the tensor this job decodes (a
+                          // range job of a sharded decode; 0 otherwise).  Work item k of
+                          // the job decodes chunk chunk0 + k; dst and base are then
+                          // shifted on the host so that dst + chunk * chunk_bytes lands
+                          // in the caller's buffer of the range
 };
 
 // Per group-chunk result of the code builder.

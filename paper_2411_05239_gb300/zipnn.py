@@ -32,7 +32,8 @@ EXPORTS = [
     "zipnn_batch_decompress", "zipnn_sync_status", "zipnn_stream_free",
     "zipnn_batch_compress_workspace_size", "zipnn_batch_compress_into",
     "zipnn_plan_decompress", "zipnn_plan_compress", "zipnn_plan_launch", "zipnn_plan_destroy",
-    "zipnn_plan_load", "zipnn_batch_compress_into_ex",
+    "zipnn_plan_load", "zipnn_batch_compress_into_ex", "zipnn_partition_chunks",
+    "zipnn_plan_decompress_range",
 ]
 
 
@@ -108,6 +109,11 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(sz), vp, sz, vp, vp], i32),
         "zipnn_plan_load": ([zsp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                              i32, sz, ctypes.POINTER(ZTuning), ctypes.POINTER(vp)], i32),
+        "zipnn_partition_chunks": ([zsp, ctypes.POINTER(vp), i32, i32,
+                                    ctypes.POINTER(ctypes.c_uint64)], i32),
+        "zipnn_plan_decompress_range": ([zsp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32,
+                                         ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.POINTER(ZTuning), ctypes.POINTER(vp)], i32),
         "zipnn_plan_launch": ([vp, vp], i32),
         "zipnn_plan_destroy": ([vp], None),
     }
@@ -341,9 +347,17 @@ class BatchCompressor:
     applies the skip-ahead probe (Sec. 3.2): after a raw group-chunk the same
     group of the next probe_skip chunks is stored raw."""
 
-    def __init__(self, xs: list[torch.Tensor], chunk_bytes: int = DEFAULT_CHUNK, lanes: int = 0,
+    def __init__(self, xs: list[torch.Tensor], chunk_bytes: int | None = None, lanes: int = 0,
                  bases: list[torch.Tensor | None] | None = None, probe_skip: int = 0):
         n = len(xs)
+        if chunk_bytes is None:
+            # the autotuner's setting for this workload when one is cached,
+            # else 256 KiB chunks and the default lanes
+            t = tuned_settings(dtype_code(xs[0], None),
+                               sum(x.numel() * x.element_size() for x in xs))
+            chunk_bytes = int(t["chunk_bytes"]) if t else DEFAULT_CHUNK
+            if t and not lanes and bases is None:
+                lanes = int(t["lanes"])
         self.xs = xs
         self.chunk_bytes = chunk_bytes
         self.codes = [dtype_code(x, None) for x in xs]
@@ -402,10 +416,24 @@ class Plan:
             pass
 
 
+def tuned_settings(dtype: int, nbytes: int) -> dict | None:
+    """The autotuner's cached setting for (this GPU, dtype, size class), or None."""
+    from . import autotune
+    return autotune.cached(dtype, nbytes)
+
+
 def plan_decompress(cs: list[Compressed], outs: list[torch.Tensor],
                     bases: list[torch.Tensor | None] | None = None,
                     tune: ZTuning | None = None) -> Plan:
+    """Graph-captured persistent decode of all containers.  With no tuning
+    given, the autotuner's cached decoder setting for the workload is used
+    when there is one (the setting changes speed only, never bytes)."""
     n = len(cs)
+    if tune is None and n:
+        t = tuned_settings(cs[0].dtype_code, sum(c.orig_nbytes for c in cs))
+        if t:
+            tune = tuning(threads=int(t["threads"]), ctas_per_sm=int(t["ctas_per_sm"]),
+                          lut_bits=int(t["lut_bits"]))
     arr = (ZStream * n)(*[c.zs for c in cs])
     dsts = _ptrs(outs)
     bp = _ptrs(bases) if bases is not None else None
@@ -436,6 +464,62 @@ def plan_load(cs: list[Compressed], h_containers: list[torch.Tensor], outs: list
                                ctypes.byref(tune) if tune else None, ctypes.byref(h))
     _check(rc, "zipnn_plan_load")
     return Plan(h.value, [cs, h_containers, outs, bases])
+
+
+def partition_chunks(streams: list[ZStream], host_maps: list, world: int) -> list[int]:
+    """Split the chunks of the containers (taken in order) into `world`
+    contiguous ranges of near-equal decode traffic (zipnn_partition_chunks).
+    host_maps[i]: host bytes (numpy uint8 array, bytes or a CPU tensor) holding
+    at least container i's header and map.  Returns world + 1 global chunk
+    indices; rank r owns [b[r], b[r+1])."""
+    import numpy as np
+    n = len(streams)
+    arr = (ZStream * n)(*streams)
+    keep = [np.ascontiguousarray(np.frombuffer(m, dtype=np.uint8)) if isinstance(m, (bytes, bytearray))
+            else (m.contiguous().numpy() if isinstance(m, torch.Tensor) else np.ascontiguousarray(m))
+            for m in host_maps]
+    maps = (ctypes.c_void_p * n)(*[k.ctypes.data if k.size else None for k in keep])
+    out = (ctypes.c_uint64 * (world + 1))()
+    _check(lib().zipnn_partition_chunks(arr, maps, n, world, out), "zipnn_partition_chunks")
+    return [int(v) for v in out]
+
+
+def range_extents(streams: list[ZStream], lo: int, hi: int) -> list[tuple[int, int, int] | None]:
+    """For the global chunk range [lo, hi): per container, (first chunk, byte
+    offset, byte count) of its part of the range, or None when it has none."""
+    out, g = [], 0
+    for s in streams:
+        a = max(lo, g) - g
+        b = min(hi, g + s.n_chunks) - g
+        g += s.n_chunks
+        if a >= b or b <= 0:
+            out.append(None)
+            continue
+        start = a * s.chunk_bytes
+        end = min(b * s.chunk_bytes, s.orig_nbytes)
+        out.append((a, start, end - start))
+    return out
+
+
+def plan_decompress_range(cs: list[Compressed], outs: list, lo: int, hi: int,
+                          bases: list | None = None, tune: ZTuning | None = None) -> Plan:
+    """Decode plan for the global chunks [lo, hi) of the containers (a rank's
+    share of a sharded decode): outs[i] is a CUDA buffer holding exactly
+    container i's part of the range (see range_extents), or None when it has
+    none; bases[i] likewise holds the base's bytes of that part."""
+    n = len(cs)
+    arr = (ZStream * n)(*[c.zs for c in cs])
+    dsts = (ctypes.c_void_p * n)(*[(_flat_u8(o).data_ptr() if o is not None else None)
+                                   for o in outs])
+    bp = None
+    if bases is not None:
+        bp = (ctypes.c_void_p * n)(*[(_flat_u8(b).data_ptr() if b is not None else None)
+                                     for b in bases])
+    h = ctypes.c_void_p()
+    rc = lib().zipnn_plan_decompress_range(arr, bp, dsts, n, lo, hi,
+                                           ctypes.byref(tune) if tune else None, ctypes.byref(h))
+    _check(rc, "zipnn_plan_decompress_range")
+    return Plan(h.value, [cs, outs, bases])
 
 
 def plan_compress(bc: BatchCompressor) -> Plan:
