@@ -289,26 +289,40 @@ def run_gb300(args):
     tuned = None
     lanes = args.lanes
     if args.autotune:
+        # the autotuner sweeps chunk sizes 64 KiB - 1 MiB (container), lanes,
+        # table width, CTA size and CTAs per SM (decoder) on a sample and caches
+        # the winner for this workload (GPU, dtype, size class); the library's
+        # Python API then takes the cached setting itself: the compressor below
+        # is given no chunk size and the decode plan no tuning
         from paper_2411_05239_gb300 import autotune as AT
         sample = [ts[0][: 64 * 1024 * 1024]] + ts[1:1 + 2 * 9]
-        tuned = AT.tune(sample, reps=3, chunks=(128 << 10, 256 << 10, 512 << 10),
-                        lut_bits=(11, 12), ctas=(0, 2, 3))
+        tuned = AT.tuned(sample, nbytes=orig, force=not args.autotune_cache, reps=3,
+                         chunks=AT.CHUNKS, lut_bits=(11, 12), ctas=(0, 2, 3))
+        if args.autotune_log and "table" in tuned:
+            with open(args.autotune_log, "w") as f:
+                json.dump(tuned["table"], f)
         args.chunk = tuned["chunk_bytes"]
-        lanes = tuned["lanes"]
         args.lut_bits = tuned["lut_bits"]
         args.threads = tuned["threads"]
         args.ctas_per_sm = tuned["ctas_per_sm"]
         torch.cuda.synchronize()
     # compression plan (batched, graph-captured) and a first pass for the sizes
-    bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk, lanes=lanes)
+    if args.autotune:
+        bc = Z.BatchCompressor(ts)                        # the cached setting
+    else:
+        bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk, lanes=lanes)
     bc()
     Z.sync_status()
     cs = bc.containers()
+    args.chunk = cs[0].zs.chunk_bytes
     comp_bytes = sum(c.nbytes for c in cs)
     outs = [torch.empty_like(t) for t in ts]
-    tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm, lut_bits=args.lut_bits)
+    tune = None if args.autotune else Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm,
+                                               lut_bits=args.lut_bits)
     comp_plan = Z.plan_compress(bc)
     dec_plan = Z.plan_decompress(cs, outs, tune=tune)
+    if tune is None:
+        tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm, lut_bits=args.lut_bits)
 
     # correctness gate before timing (bit-exact round trip on the device)
     comp_plan.launch()
@@ -478,6 +492,11 @@ def run_gb300(args):
                    "lanes": cs[0].zs.lanes, "lut_bits": args.lut_bits or 12, "threads": args.threads or 256,
                    "ctas_per_sm": args.ctas_per_sm,
                    "autotuned": tuned is not None,
+                   "autotune": (None if tuned is None else
+                                {"chunks_swept": tuned.get("chunks_swept"),
+                                 "candidates": tuned.get("candidates"),
+                                 "from_cache": tuned.get("from_cache"),
+                                 "sample_decode_gbs": tuned.get("decode_gbs")}),
                    "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
                    "form": "batched: 1 graph launch compress + 1 graph launch persistent decode"},
         "decompress_gbs": value, "compress_gbs": world * orig / comp_s / 1e9,
@@ -505,6 +524,21 @@ def run_gb300(args):
         "paper_context": "ZipNN CPU: up to 80 GB/s decompression, 13 GB/s compression "
                          "(Xeon Platinum 8480+, 224 cores, 16 workers)",
     }
+    # the other the benchmark spec configurations on the same run (rank 0, one GPU):
+    # the 3.43 GB checkpoint delta (config 4) and a shortened served stream
+    # (config 5: the first requests of the trace, both paths, every result checked)
+    if rank == 0 and world == 1 and args.configs:
+        del comp_plan, dec_plan, bc, cs, outs, ts
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**vars(args))
+        sub.chunk, sub.lanes, sub.threads, sub.lut_bits, sub.ctas_per_sm = 256 << 10, 0, 0, 0, 0
+        label, xs, bases = tensor_workload("delta", 24)
+        c4 = measure_tensors(label, xs, bases, sub, steps=10, warmup=3, cpu_sample_mb=32)
+        del xs, bases
+        torch.cuda.empty_cache()
+        c5 = measure_serve(sub, args.configs_serve_requests, 200.0)
+        torch.cuda.empty_cache()
+        line["configs"] = {"c4_checkpoint_delta": c4, "c5_served_stream": c5}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -513,39 +547,37 @@ def run_gb300(args):
     return 0
 
 
-def run_tensors(args):
-    """Single-configuration modes: plain 8 MiB BF16 (L2-flushed between steps),
-    256 MiB row-scaled FP32, 256 MiB N(0, 0.02) FP16, the 3.43 GB checkpoint
-    delta (base + next), and the clean-model tensors (FP32 / FP16 holding BF16
-    values, Sec. 3.2).
-    Same step as the checkpoint mode: graph-captured compress + decode."""
+def tensor_workload(name: str, delta_layers: int = 24):
+    """(label, tensors, bases) of a single-configuration workload."""
     from paper_2411_05239_gb300 import workloads as W
-    from paper_2411_05239_gb300 import zipnn as Z
-
-    torch.cuda.set_device(0)
-    hbm_peak, peak_kind = peaks()
     bases = None
-    if args.workload == "plain":
-        xs = [W.plain_bf16(device="cuda")]
-        name = "plain_bf16_8mib"
-    elif args.workload == "fp32":
-        xs = [W.rowscaled_fp32(device="cuda")]
-        name = "rowscaled_fp32_256mib"
-    elif args.workload == "fp16":
+    if name == "plain":
+        xs, label = [W.plain_bf16(device="cuda")], "plain_bf16_8mib"
+    elif name == "fp32":
+        xs, label = [W.rowscaled_fp32(device="cuda")], "rowscaled_fp32_256mib"
+    elif name == "fp16":
         xs = [W.gaussian(134_217_728, 0.02, 9, torch.float16, device="cuda")]
-        name = "gaussian_fp16_256mib"
-    elif args.workload == "clean_fp32":
-        xs = [W.clean_fp32_from_bf16(device="cuda")]
-        name = "clean_fp32_from_bf16_256mib"
-    elif args.workload == "clean_fp16":
-        xs = [W.clean_fp16_from_bf16(device="cuda")]
-        name = "clean_fp16_from_bf16_128mib"
+        label = "gaussian_fp16_256mib"
+    elif name == "clean_fp32":
+        xs, label = [W.clean_fp32_from_bf16(device="cuda")], "clean_fp32_from_bf16_256mib"
+    elif name == "clean_fp16":
+        xs, label = [W.clean_fp16_from_bf16(device="cuda")], "clean_fp16_from_bf16_128mib"
     else:
-        n = sum(sp.numel for sp in W.delta_specs(n_layers=args.delta_layers))
+        n = sum(sp.numel for sp in W.delta_specs(n_layers=delta_layers))
         nxt, base = W.delta_pair(n, seed=3, device="cuda")
         xs, bases = [nxt], [base]
-        name = ("checkpoint_delta_1.7b_bf16" if args.delta_layers == 24
-                else f"checkpoint_delta_bf16_{args.delta_layers}l")
+        label = ("checkpoint_delta_1.7b_bf16" if delta_layers == 24
+                 else f"checkpoint_delta_bf16_{delta_layers}l")
+    return label, xs, bases
+
+
+def measure_tensors(label: str, xs, bases, args, steps: int, warmup: int,
+                    cpu_sample_mb: int) -> dict:
+    """Graph-captured compress + decode of one workload, L2 flushed (256 MB
+    write) before each timed phase; CUDA events on the launching stream; the
+    oracle on a prefix of the same tensor as the CPU baseline."""
+    from paper_2411_05239_gb300 import zipnn as Z
+    hbm_peak, peak_kind = peaks()
     orig = sum(x.numel() * x.element_size() for x in xs)
     bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases, lanes=args.lanes)
     bc()
@@ -556,36 +588,40 @@ def run_tensors(args):
     pc = Z.plan_compress(bc)
     pd = Z.plan_decompress(cs, outs, bases=bases,
                            tune=Z.tuning(threads=args.threads, lut_bits=args.lut_bits,
-                                          ctas_per_sm=args.ctas_per_sm))
+                                         ctas_per_sm=args.ctas_per_sm))
     pd.launch()
     Z.sync_status()
     for x, o in zip(xs, outs):
         if not torch.equal(x.view(torch.uint8), o.view(torch.uint8)):
             raise SystemExit("round trip mismatch")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-    s = torch.cuda.current_stream()
-    K = args.steps
+    st = torch.cuda.current_stream()
+    K = steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    for k in range(args.warmup + K):
-        e = ev[k - args.warmup] if k >= args.warmup else None
+    for k in range(warmup + K):
+        e = ev[k - warmup] if k >= warmup else None
         flush.fill_(k & 255)
-        if e: e[0].record(s)
-        pc.launch(s)
-        if e: e[1].record(s)
+        if e: e[0].record(st)
+        pc.launch(st)
+        if e: e[1].record(st)
         flush.fill_((k + 1) & 255)
-        if e: e[2].record(s)
-        pd.launch(s)
-        if e: e[3].record(s)
+        if e: e[2].record(st)
+        pd.launch(st)
+        if e: e[3].record(st)
     torch.cuda.synchronize()
     Z.sync_status()
+    # the timed launches' results are the inputs again
+    for x, o in zip(xs, outs):
+        if not torch.equal(x.view(torch.uint8), o.view(torch.uint8)):
+            raise SystemExit("round trip mismatch after the timed launches")
     cm = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     dm = sorted(e[2].elapsed_time(e[3]) for e in ev)
     dmean = statistics.mean(dm)
     alg = comp + orig + (orig if bases else 0)
-    # CPU baseline: the oracle on (a prefix of) the same tensor, 1 thread
+    alg_c = orig + comp + (orig if bases else 0)
     cpu = None
-    if args.cpu_sample_mb > 0:
-        lim = max(args.chunk, (args.cpu_sample_mb << 20) // args.chunk * args.chunk)
+    if cpu_sample_mb > 0:
+        lim = max(args.chunk, (cpu_sample_mb << 20) // args.chunk * args.chunk)
         xb = xs[0].view(torch.uint8).reshape(-1)
         samp = xb[:lim].cpu().numpy()
         bsamp = bases[0].view(torch.uint8).reshape(-1)[:lim].cpu().numpy() if bases else None
@@ -595,63 +631,148 @@ def run_tensors(args):
                "sample": f"first {r['bytes'] >> 20} MiB of the tensor"
                          + (" and its base" if bases else "")
                          + "; oracle compress then decompress, 1 thread"}
-    line = {
-        "metric": METRIC, "value": orig / (dmean / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1,
-        "steps": K, "warmup": args.warmup, "higher_is_better": True, "dtype": "u8",
-        "data": "synthetic", "config": {"workload": name, "bytes": orig, "chunk_bytes": args.chunk,
-                                        "l2": "flushed (256 MB write) before each timed phase"},
-        "compress_gbs": orig / (cm / 1e3) / 1e9, "ratio": comp / orig,
+    pc.close()
+    pd.close()
+    return {
+        "workload": label, "bytes": orig, "chunk_bytes": args.chunk, "steps": K,
+        "decompress_gbs": orig / (dmean / 1e3) / 1e9, "compress_gbs": orig / (cm / 1e3) / 1e9,
+        "ratio": comp / orig,
         "decompress_ms": {"mean": dmean, "p99": dm[min(K - 1, int(math.ceil(0.99 * K)) - 1)]},
+        "compress_ms": {"mean": cm},
         "roofline": {"kernel": "k_decode", "bound": "hbm", "achieved": alg / (dmean / 1e3) / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
-                     "frac": alg / (dmean / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
+                     "frac": alg / (dmean / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg},
+        "roofline_compress": {"bound": "hbm", "achieved": alg_c / (cm / 1e3) / 1e9,
+                              "peak": hbm_peak, "unit": "GB/s",
+                              "frac": alg_c / (cm / 1e3) / 1e9 / hbm_peak},
+        "l2": "flushed (256 MB write) before each timed phase",
         "cpu_baseline": cpu,
+    }
+
+
+def run_tensors(args):
+    """Single-configuration modes: plain 8 MiB BF16, 256 MiB row-scaled FP32,
+    256 MiB N(0, 0.02) FP16, the 3.43 GB checkpoint delta (base + next), and the
+    clean-model tensors (FP32 / FP16 holding BF16 values, Sec. 3.2).  Same step
+    as the checkpoint mode: graph-captured compress + decode."""
+    torch.cuda.set_device(0)
+    label, xs, bases = tensor_workload(args.workload, args.delta_layers)
+    r = measure_tensors(label, xs, bases, args, args.steps, args.warmup, args.cpu_sample_mb)
+    line = {
+        "metric": METRIC, "value": r["decompress_gbs"], "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": label, "bytes": r["bytes"],
+                                        "chunk_bytes": args.chunk, "l2": r["l2"]},
+        "compress_gbs": r["compress_gbs"], "ratio": r["ratio"],
+        "decompress_ms": r["decompress_ms"], "roofline": r["roofline"],
+        "roofline_compress": r["roofline_compress"], "cpu_baseline": r["cpu_baseline"],
         "impl": "gb300",
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args):
-    """Served stream: 2,000 requests, Poisson arrivals at 200 req/s, compress /
-    decompress (70/30), BF16/FP16/FP32 (60/20/20), sizes log-uniform in
-    [64 KiB, 2 GiB], 15% deltas against a resident base; HBM budget 40 GB.
-    Served (continuous batching) and plain (serial, one stream, one launch per
-    request) paths replay the same trace; latency = completion - arrival."""
+class ServeChecks:
+    """Checks on a served (or plain) stream's results: every result by device
+    identity (a compress result is decoded back on the device and compared
+    with its input; a decompress result is compared with its input), and a
+    seeded 5% sample of the compress results against the oracle on three
+    chunks each (first, last, one random), whose bytes are copied to the host
+    at completion and encoded by the oracle after the timed region."""
+
+    def __init__(self, trace, inputs, maxb: int, frac: float = 0.05, seed: int = 4):
+        rng = np.random.default_rng(seed)
+        self.sample = {r.rid for r in trace if rng.random() < frac}
+        self.rng = np.random.default_rng(seed + 1)
+        self.inputs = inputs
+        self.scratch = torch.empty(maxb + 16, dtype=torch.uint8, device="cuda")
+        self.kept = []          # (rid, dtype, lanes, [(chunk bytes, [(mode, value, payload)])])
+        self.checked = 0
+
+    def check(self, r, out: torch.Tensor) -> None:
+        from paper_2411_05239_gb300 import zipnn as Z
+        x, b = self.inputs(r)
+        xb = x.contiguous().view(-1).view(torch.uint8)
+        if r.op == "compress":
+            c = Z.wrap(out)
+            y = self.scratch[:c.orig_nbytes]
+            Z.decompress(c, out=y.view(x.dtype) if c.orig_nbytes else y, base=b)
+            if not torch.equal(y, xb):
+                raise SystemExit(f"request {r.rid}: decoded container differs from the input")
+            if r.rid in self.sample:
+                self.kept.append(self._chunks(r, c, x, b))
+        else:
+            if not torch.equal(out, xb):
+                raise SystemExit(f"request {r.rid}: decoded tensor differs from the input")
+        self.checked += 1
+
+    def _chunks(self, r, c, x, b):
+        import struct
+        t = c.device_tensor()
+        n, G, C = c.zs.n_chunks, c.zs.n_groups, c.zs.chunk_bytes
+        P = 64 + 16 * n * G
+        ent = t[64:P].cpu().numpy().tobytes()
+        xb = x.contiguous().view(-1).view(torch.uint8)
+        if b is not None:
+            xb = xb ^ b.contiguous().view(-1).view(torch.uint8)
+        out = []
+        for ch in sorted({0, n - 1, int(self.rng.integers(0, n))}):
+            groups = []
+            for g in range(G):
+                off, size, mode, value = struct.unpack_from("<QIBB", ent, 16 * (ch * G + g))
+                groups.append((mode, value, t[P + off:P + off + size].cpu().numpy().tobytes()))
+            out.append((xb[ch * C:(ch + 1) * C].cpu().numpy(), groups))
+        return (r.rid, c.dtype_code, c.zs.lanes, out)
+
+    def oracle_verdict(self) -> dict:
+        import oracle as O
+        bad = 0
+        for rid, dtype, lanes, chunks in self.kept:
+            for data, groups in chunks:
+                want = O.compress_chunk(data, dtype, lanes)
+                if [(m, v, p) for m, v, p in want] != groups:
+                    bad += 1
+        if bad:
+            raise SystemExit(f"{bad} sampled chunks differ from the oracle")
+        return {"identity_checked": self.checked, "oracle_sampled_requests": len(self.kept),
+                "oracle_sampled_chunks": sum(len(k[3]) for k in self.kept), "mismatches": 0}
+
+
+def measure_serve(args, n_requests: int, rate: float) -> dict:
+    """Served stream: Poisson arrivals, compress / decompress (70/30),
+    BF16/FP16/FP32 (60/20/20), sizes log-uniform in [64 KiB, 2 GiB], 15% deltas
+    against a resident base; HBM budget 40 GB.  The served (continuous
+    batching) and plain (serial, one stream, one launch per request) paths
+    replay the same trace with one clock: latency = completion - SCHEDULED
+    arrival (t0 + t_arrival on the host's monotonic clock, the clock the server
+    stamps completions with).  Every result of both replays is checked (device
+    identity) and a seeded 5% sample of the served compress results against the
+    oracle."""
     import threading as th
     from paper_2411_05239_gb300 import workloads as W
     from paper_2411_05239_gb300 import zipnn as Z
 
     torch.cuda.set_device(0)
-    trace = W.request_trace(n=args.serve_requests, seed=4, rate=args.serve_rate)
+    trace = W.request_trace(n=n_requests, seed=4, rate=rate)
     maxb = max(r.nbytes for r in trace)
-    pools = {}
-    for k, (dt, tdt) in enumerate(W.TORCH_DTYPE.items()):
-        es = torch.tensor([], dtype=tdt).element_size()
-        n = maxb // es + 1
-        nxt, base = W.delta_pair(n, seed=40 + k, device="cuda")
-        plain = W.gaussian(n, 0.02, seed=50 + k, dtype=tdt, device="cuda")
-        pools[dt] = (plain, nxt.to(tdt) if tdt != torch.bfloat16 else nxt,
-                     base.to(tdt) if tdt != torch.bfloat16 else base)
-    def inputs(r):
-        es = {"bf16": 2, "fp16": 2, "fp32": 4}[r.dtype]
-        n = r.nbytes // es
-        plain, nxt, base = pools[r.dtype]
-        return (nxt[:n], base[:n]) if r.delta else (plain[:n], None)
+    inputs = W.serve_inputs(trace, device="cuda")
     containers = {}
     for r in trace:
         if r.op == "decompress":
             x, b = inputs(r)
             containers[r.rid] = Z.compress(x, base=b)
     torch.cuda.synchronize()
+    checks = ServeChecks(trace, inputs, maxb)
 
     # served path
     srv = Z.Server(args.serve_budget_gb << 30, slots=args.serve_slots)
-    lat, done_bytes, t_first, t_last = {}, 0, None, 0.0
-    t0 = time.perf_counter() + 0.5
+    lat, lat_submit, done_bytes, t_first, t_last = {}, {}, 0, None, 0.0
+    t0 = time.monotonic() + 0.5
+
     def submitter():
         for r in trace:
-            dt = t0 + r.t_arrival - time.perf_counter()
+            dt = t0 + r.t_arrival - time.monotonic()
             if dt > 0:
                 time.sleep(dt)
             x, b = inputs(r)
@@ -665,53 +786,78 @@ def run_serve(args):
         for c in srv.poll():
             if c.status != 0:
                 raise SystemExit(f"served request {c.tag} failed: {c.status}")
-            lat[c.tag] = (c.t_done - c.t_submit) * 1e3
-            done_bytes += trace[c.tag].nbytes
-            t_first = c.t_submit if t_first is None else min(t_first, c.t_submit)
+            r = trace[c.tag]
+            lat[c.tag] = (c.t_done - (t0 + r.t_arrival)) * 1e3
+            lat_submit[c.tag] = (c.t_done - c.t_submit) * 1e3
+            done_bytes += r.nbytes
+            t_first = t0 + r.t_arrival if t_first is None else min(t_first, t0 + r.t_arrival)
             t_last = max(t_last, c.t_done)
+            checks.check(r, srv.output(c))
             srv.release(c.id)
         time.sleep(0.0002)
     th_sub.join()
     st = srv.stats()
     srv.close()
     served = sorted(lat.values())
+    served_sub = sorted(lat_submit.values())
 
-    # plain path: serial, one stream, one launch set per request
+    # plain path: serial, one stream, one launch set per request; the same
+    # identity checks after each request's completion stamp
     out_buf = torch.empty(Z.compress_bound(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
                           device="cuda")   # FP32 has the largest bound and workspace
     ws = torch.empty(Z.workspace_size(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
                      device="cuda")
+    onb = torch.zeros(1, dtype=torch.int64, device="cuda")
     dec_out = torch.empty(maxb // 2 + 16, dtype=torch.int16, device="cuda")
+    plain_checks = ServeChecks(trace, inputs, maxb, frac=0.0)
     plat = []
-    t0 = time.perf_counter() + 0.2
+    t0 = time.monotonic() + 0.2
     for r in trace:
-        dt = t0 + r.t_arrival - time.perf_counter()
+        dt = t0 + r.t_arrival - time.monotonic()
         if dt > 0:
             time.sleep(dt)
         x, b = inputs(r)
         if r.op == "compress":
-            Z.compress_into(x, out_buf, ws, base=b)
+            Z.compress_into(x, out_buf, ws, onb, base=b)
         else:
             c = containers[r.rid]
             Z.decompress(c, out=dec_out.view(torch.uint8)[:c.orig_nbytes].view(x.dtype), base=b)
         torch.cuda.synchronize()
-        plat.append((time.perf_counter() - (t0 + r.t_arrival)) * 1e3)
+        plat.append((time.monotonic() - (t0 + r.t_arrival)) * 1e3)
+        if r.op == "compress":
+            plain_checks.check(r, out_buf[:int(onb.item())])
+        else:
+            plain_checks.check(r, dec_out.view(torch.uint8)[:r.nbytes])
     Z.sync_status()
     plain = sorted(plat)
+    verdict = checks.oracle_verdict()
+    verdict["plain_identity_checked"] = plain_checks.checked
     pct = lambda a, q: a[min(len(a) - 1, int(math.ceil(q * len(a))) - 1)]
     total = sum(r.nbytes for r in trace)
-    line = {
-        "metric": METRIC, "value": done_bytes / (t_last - t_first) / 1e9, "unit": "GB/s",
-        "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "served_stream", "requests": len(trace), "rate_per_s": args.serve_rate,
-                   "budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
-                   "offered_gb": total / 1e9},
+    return {
+        "workload": "served_stream", "requests": len(trace), "rate_per_s": rate,
+        "budget_gb": args.serve_budget_gb, "slots": args.serve_slots, "offered_gb": total / 1e9,
+        "latency_origin": "scheduled arrival (t0 + t_arrival), host monotonic clock, both paths",
         "served": {"p50_ms": pct(served, 0.5), "p99_ms": pct(served, 0.99),
                    "mean_ms": statistics.mean(served), "batches": st.batches,
-                   "max_batch": st.max_batch, "gbs": done_bytes / (t_last - t_first) / 1e9},
+                   "max_batch": st.max_batch, "gbs": done_bytes / (t_last - t_first) / 1e9,
+                   "from_submit_p50_ms": pct(served_sub, 0.5),
+                   "from_submit_p99_ms": pct(served_sub, 0.99)},
         "plain": {"p50_ms": pct(plain, 0.5), "p99_ms": pct(plain, 0.99),
                   "mean_ms": statistics.mean(plain)},
-        "impl": "gb300",
+        "checks": verdict,
+    }
+
+
+def run_serve(args):
+    """Config 5 alone (see measure_serve)."""
+    r = measure_serve(args, args.serve_requests, args.serve_rate)
+    line = {
+        "metric": METRIC, "value": r["served"]["gbs"], "unit": "GB/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+        "config": {k: r[k] for k in ("workload", "requests", "rate_per_s", "budget_gb", "slots",
+                                     "offered_gb", "latency_origin")},
+        "served": r["served"], "plain": r["plain"], "checks": r["checks"], "impl": "gb300",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -748,6 +894,14 @@ def main(argv=None):
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="request arrivals per second (the served-stream workload: 200)")
     ap.add_argument("--ref-sample-mb", type=int, default=48)
+    ap.add_argument("--configs", type=int, default=1,
+                    help="also measure the checkpoint delta and a shortened served stream")
+    ap.add_argument("--configs-serve-requests", type=int, default=400,
+                    help="requests of the served stream measured with the default workload")
+    ap.add_argument("--autotune-cache", type=int, default=0,
+                    help="reuse a cached autotuner result instead of sweeping again")
+    ap.add_argument("--autotune-log", default="",
+                    help="write the autotuner's per-candidate table (JSON) here")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -74,14 +74,16 @@ def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_
          ctas=(0, 2, 3, 4), lane_scales=(1, 2), threads=(128, 256),
          verbose: bool = False) -> dict:
     """Sweep the candidates on `sample` (CUDA tensors of one dtype); returns the
-    best setting with its measured decode / compress GB/s (original bytes)."""
+    best setting with its measured decode / compress GB/s (original bytes) and,
+    under "table", every candidate's figures."""
     orig = sum(t.numel() * t.element_size() for t in sample)
     outs = [torch.empty_like(t) for t in sample]
     results = []
     dtype = Z.dtype_code(sample[0], None)
-    for chunk, scale in [(c, k) for c in chunks for k in lane_scales]:
-        # one sub-stream per 1 KiB, or per 512 B, of each chunk
-        lanes = max(1, min(1024, chunk // 1024 * scale, chunk // 16))
+    # one sub-stream per 1 KiB, or per 512 B, of each chunk (at most 1024)
+    cands = sorted({(c, max(1, min(1024, c // 1024 * k, c // 16))) for c in chunks
+                    for k in lane_scales})
+    for chunk, lanes in cands:
         bc = Z.BatchCompressor(sample, chunk_bytes=chunk, lanes=lanes)
         bc()
         Z.sync_status()
@@ -107,21 +109,38 @@ def tune(sample: list[torch.Tensor], reps: int = 5, chunks=CHUNKS, lut_bits=LUT_
     best = max(results, key=lambda r: (round(r["decode_gbs"], 0), r["compress_gbs"]))
     best = dict(best)
     best["candidates"] = len(results)
+    best["chunks_swept"] = sorted({r["chunk_bytes"] for r in results})
+    best["table"] = results
     return best
 
 
-def tuned(sample: list[torch.Tensor], force: bool = False, **kw) -> dict:
-    """Cached tune() for the sample's (GPU, dtype, size class)."""
+def tuned(sample: list[torch.Tensor], force: bool = False, nbytes: int | None = None,
+          **kw) -> dict:
+    """Cached tune() for (GPU, dtype, size class).  The size class is that of
+    `nbytes` when given -- the whole workload the sample stands for, so that a
+    later lookup for that workload (cached()) finds the setting -- else the
+    sample's own size.  The cached entry leaves out the per-candidate table."""
     dtype = Z.dtype_code(sample[0], None)
-    nbytes = sum(t.numel() * t.element_size() for t in sample)
+    if nbytes is None:
+        nbytes = sum(t.numel() * t.element_size() for t in sample)
     k = key(dtype, nbytes)
     cache = load_cache()
     if k in cache and not force:
-        return cache[k]
+        hit = dict(cache[k])
+        hit["from_cache"] = True
+        return hit
     best = tune(sample, **kw)
-    cache[k] = best
+    cache[k] = {kk: v for kk, v in best.items() if kk != "table"}
     try:
         save_cache(cache)
     except OSError:
         pass
+    best["from_cache"] = False
     return best
+
+
+def cached(dtype: int, nbytes: int) -> dict | None:
+    """The cached setting for (this GPU, dtype, size class of nbytes), or None.
+    The library's Python API consults it when a batched compressor is given no
+    chunk size and a decode plan no tuning."""
+    return load_cache().get(key(dtype, nbytes))
