@@ -190,11 +190,22 @@ zipnn_status zipnn_batch_compress_into(const void* const* d_srcs, const void* co
  *   of the next probe_skip chunks of the tensor is stored raw without its
  *   decision counting, then decisions resume; 0 = every group-chunk decided on
  *   its own (the default).  The containers stay valid version-1 containers.
- * reserved: must be zero (EINVAL otherwise). */
+ * encoder: 0 = automatic: batches whose tensors are all BF16, all FP16 or all
+ *   U8, without probe_skip, run the single-pass encoder (one persistent
+ *   kernel: each chunk's histograms, codes, offset -- by a bounded look-back
+ *   over the chunks before it -- and packing, the second read of the chunk
+ *   coming from L2); others run four kernels (histograms, codes, offsets,
+ *   packing).  1 = always the four kernels.  Both write the same bytes.
+ *   EINVAL for other values.
+ * debug_flags: 0.  Bit 0 is fault injection for tests of the single-pass
+ *   encoder: the launch's first chunk never publishes its payload size, so the
+ *   look-backs that need it give up after 100 ms; those chunks are not
+ *   written and zipnn_sync_status reports ZIPNN_ETIMEOUT.  Other bits: EINVAL. */
 typedef struct zipnn_encode_options {
     uint32_t lanes;
     uint32_t probe_skip;
-    uint32_t reserved[2];
+    uint32_t encoder;
+    uint32_t debug_flags;
 } zipnn_encode_options;
 
 /* zipnn_batch_compress_into with encoder options (opts may be NULL: defaults);

@@ -251,8 +251,8 @@ zipnn_status zipnn_compress_into(const void* d_src, const void* d_base_or_null, 
   const uint64_t ngc = (uint64_t)J.n_chunks * elem_size(dtype);
   EncodeScratch s;
   encode_scratch_carve(d_workspace, J.n_chunks, ngc, 1, &s);
-  cudaError_t e = launch_encode_analyse_ex(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0, -1);
-  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, J.n_chunks, (int)lanes, s, st, -1);
+  cudaError_t e = launch_encode(nullptr, &J, 1, J.n_chunks, ngc, s, err, st, 0, (int)lanes, -1,
+                                false, 0);
   return cuda_status(e);
 }
 
@@ -327,7 +327,9 @@ extern "C" zipnn_status zipnn_batch_compress_into_ex(
   if (!d_outs) return ZIPNN_EINVAL;
   const uint32_t lanes = opts ? opts->lanes : 0u;
   const uint32_t skip = opts ? opts->probe_skip : 0u;
-  if (opts && (opts->reserved[0] || opts->reserved[1])) return ZIPNN_EINVAL;
+  const uint32_t encoder = opts ? opts->encoder : 0u;
+  const uint32_t dbg = opts ? opts->debug_flags : 0u;
+  if (encoder > 1 || (dbg & ~1u)) return ZIPNN_EINVAL;
   BatchPlan bp;
   zipnn_status rc = plan_batch_compress(d_srcs, d_bases, nbytes, dtypes, count, chunk_bytes,
                                         lanes, d_outs, out_capacities, d_out_nbytes, &bp);
@@ -344,11 +346,8 @@ extern "C" zipnn_status zipnn_batch_compress_into_ex(
   encode_scratch_carve(ws, bp.nchunks, bp.ngc, count, &s);
   cudaError_t e = g_ring.h2d(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(), st);
   if (e == cudaSuccess)
-    e = launch_encode_analyse_ex(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st,
-                                 bp.max_groups, bp.uniform);
-  if (e == cudaSuccess)
-    e = launch_encode_pack_ex(d_jobs, nullptr, count, bp.nchunks, bp.max_lanes, s, st,
-                              bp.uniform);
+    e = launch_encode(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st, bp.max_groups,
+                      bp.max_lanes, bp.uniform, skip != 0, (int)encoder, dbg);
   return cuda_status(e);
 }
 

@@ -120,9 +120,13 @@ __device__ __forceinline__ void hist16_word(uint32_t hl, uint32_t w) {
   red_shared_inc(hl + (((h >> 1) & 0x4000u) | (((h << 7) & 0x3F80u) | 0x8000u)));
 }
 
-template <int DT>
-__device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __restrict__ hist,
-                           uint32_t* __restrict__ zsyms) {
+// Histograms of chunk c of job J by the NT threads of the CTA, with the
+// lane-indexed counters in sh (G * 256 * 32 + G words); the bin totals go to
+// hist_out[g * 256 + b] and the symbols inside all-zero vectors to zs_out[g]
+// (global or shared memory).  Ends with every thread past a barrier.
+template <int DT, int NT = kHistThreads>
+__device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* hist_out,
+                           uint32_t* zs_out) {
   constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
   constexpr int V = 16 / (DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2));
   constexpr int ES = 16 / V;
@@ -133,7 +137,7 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   const uint8_t* base = J.base ? J.base + off : nullptr;
 
   uint32_t* zcnt = sh + G * 256 * 32;  // per group: symbols inside all-zero vectors
-  for (int i = tid; i < G * 256 * 32 + G; i += kHistThreads) sh[i] = 0;
+  for (int i = tid; i < G * 256 * 32 + G; i += NT) sh[i] = 0;
   __syncthreads();
   uint32_t zc[G];
 #pragma unroll
@@ -144,21 +148,21 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
   constexpr int U = 4;  // vectors in flight per thread
   uint64_t vstart = tid;
   if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
-    // whole rounds of kHistThreads * U vectors of whole 16-bit elements
-    const uint64_t nfast = nb % 16 ? 0 : nvec / ((uint64_t)kHistThreads * U) * (kHistThreads * U);
+    // whole rounds of NT * U vectors of whole 16-bit elements
+    const uint64_t nfast = nb % 16 ? 0 : nvec / ((uint64_t)NT * U) * (NT * U);
     const uint32_t hls = (uint32_t)__cvta_generic_to_shared(hl);
     // the second round, up to where the in-loop prefetches start
-    for (uint64_t vp = tid + (uint64_t)kHistThreads * U; vp < nfast && vp < 2ull * kHistThreads * U;
-         vp += kHistThreads) {
+    for (uint64_t vp = tid + (uint64_t)NT * U; vp < nfast && vp < 2ull * NT * U;
+         vp += NT) {
       prefetch_l2(reinterpret_cast<const uint4*>(src) + vp);
       if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + vp);
     }
-    for (uint64_t v0 = tid; v0 < nfast; v0 += (uint64_t)kHistThreads * U) {
+    for (uint64_t v0 = tid; v0 < nfast; v0 += (uint64_t)NT * U) {
       uint4 a[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const uint64_t v = v0 + (uint64_t)u * kHistThreads;
-        const uint64_t vp = v + 2ull * kHistThreads * U;  // two rounds ahead
+        const uint64_t v = v0 + (uint64_t)u * NT;
+        const uint64_t vp = v + 2ull * NT * U;  // two rounds ahead
         if (vp < nfast) {
           prefetch_l2(reinterpret_cast<const uint4*>(src) + vp);
           if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + vp);
@@ -182,16 +186,16 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
     }
     vstart = nfast + tid;
   }
-  for (uint64_t v0 = vstart; v0 < nvec; v0 += (uint64_t)kHistThreads * U) {
+  for (uint64_t v0 = vstart; v0 < nvec; v0 += (uint64_t)NT * U) {
     uint4 a[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const uint64_t v = v0 + (uint64_t)u * kHistThreads;
+      const uint64_t v = v0 + (uint64_t)u * NT;
       a[u] = v < nvec ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const uint64_t v = v0 + (uint64_t)u * kHistThreads;
+      const uint64_t v = v0 + (uint64_t)u * NT;
       if (v >= nvec) break;
       uint32_t g[4][4];
       split_vec(DT, a[u], g);
@@ -226,15 +230,16 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* __r
     if (lane == 0 && z) atomicAdd(&zcnt[g], z);
   }
   __syncthreads();
-  if (tid < G) zsyms[J.gc_begin + c * G + tid] = zcnt[tid];
+  if (tid < G) zs_out[tid] = zcnt[tid];
   // bin totals: thread b sums the 32 lane counters of bin b (rotated start so
   // the 32 threads of a warp read 32 different banks)
-  for (int b = tid; b < G * 256; b += kHistThreads) {
+  for (int b = tid; b < G * 256; b += NT) {
     uint32_t s = 0;
 #pragma unroll 8
     for (int i = 0; i < 32; i++) s += sh[b * 32 + ((i + b) & 31)];
-    hist[(J.gc_begin + c * G + b / 256) * 256 + (b & 255)] = s;
+    hist_out[b] = s;
   }
+  __syncthreads();
 }
 
 template <int DTS>
@@ -245,15 +250,18 @@ k_hist(JobRef jr, uint32_t* __restrict__ hist, uint32_t* __restrict__ zsyms) {
   const int j = find_job_chunk(jr, chunk);
   const Job& J = job_at(jr, j);
   const uint64_t c = chunk - J.chunk_begin;
+  const uint64_t gc0 = J.gc_begin + c * elem_size(J.dtype);
+  uint32_t* ho = hist + gc0 * 256;
+  uint32_t* zo = zsyms + gc0;
   if (DTS >= 0) {
-    hist_chunk<(DTS < 0 ? 0 : DTS)>(J, c, hsm, hist, zsyms);
+    hist_chunk<(DTS < 0 ? 0 : DTS)>(J, c, hsm, ho, zo);
     return;
   }
   switch (J.dtype) {
-    case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, hist, zsyms); break;
-    case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, hist, zsyms); break;
-    case ZIPNN_FP32: hist_chunk<ZIPNN_FP32>(J, c, hsm, hist, zsyms); break;
-    default: hist_chunk<ZIPNN_U8>(J, c, hsm, hist, zsyms); break;
+    case ZIPNN_BF16: hist_chunk<ZIPNN_BF16>(J, c, hsm, ho, zo); break;
+    case ZIPNN_FP16: hist_chunk<ZIPNN_FP16>(J, c, hsm, ho, zo); break;
+    case ZIPNN_FP32: hist_chunk<ZIPNN_FP32>(J, c, hsm, ho, zo); break;
+    default: hist_chunk<ZIPNN_U8>(J, c, hsm, ho, zo); break;
   }
 }
 
@@ -394,34 +402,22 @@ __device__ void pm_lengths(BuildSmem& S, const uint32_t cnt[8], uint32_t nz, int
 
 }
 
-__global__ void __launch_bounds__(kBuildWarps * 32)
-k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
-        const uint32_t* __restrict__ zsyms, uint32_t* __restrict__ codes,
-        uint8_t* __restrict__ tabs, GcMeta* __restrict__ meta) {
-  __shared__ BuildSmem smem[kBuildWarps];
+// Mode decision, length-limited code and canonical table of one group-chunk
+// by one warp: hist256 holds its 256 symbol counts (global or shared memory),
+// zs the symbols inside all-zero vectors, m the symbol count, T the
+// sub-streams and es the element size.  Writes the 256 (len << 16 | code)
+// entries to mycodes (coded groups only), the table bytes to tab and the
+// result to *meta_out.
+__device__ void build_gc(const uint32_t* hist256, uint32_t zs, uint32_t m, uint32_t T, int es,
+                         BuildSmem& S, uint32_t* mycodes, uint8_t* tab, GcMeta* meta_out) {
   const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5;
-  const uint64_t gc = (uint64_t)blockIdx.x * kBuildWarps + wid;
-  if (gc >= ngc_total) return;
-  BuildSmem& S = smem[wid];
-
-  const int j = find_job_gc(jr, gc);
-  const Job& J = job_at(jr, j);
-  const int es = elem_size(J.dtype), G = es;
-  const uint64_t local = gc - J.gc_begin;
-  const uint64_t c = local / G;
-  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
-  const uint32_t m = (uint32_t)(nb / es);
-  const uint32_t T = J.lanes;
-
   // counts of symbols s = lane + 32 k
   uint32_t cnt[8];
   uint32_t nz = 0;
   for (int k = 0; k < 8; k++) {
-    cnt[k] = hist[gc * 256 + lane + 32 * k];
+    cnt[k] = hist256[lane + 32 * k];
     nz += __popc(__ballot_sync(0xffffffffu, cnt[k] > 0));
   }
-  uint32_t* mycodes = codes + gc * 256;
   for (int k = 0; k < 8; k++) mycodes[lane + 32 * k] = 0;
 
   GcMeta res;
@@ -436,12 +432,11 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
     }
     res.mode = (nz == 0 || sym == 0) ? kZero : kConst;
     res.value = (res.mode == kConst) ? sym : 0;
-    if (lane == 0) meta[gc] = res;
+    if (lane == 0) *meta_out = res;
     return;
   }
 
   const uint32_t V = 16u / (uint32_t)es, nv = (m + V - 1) / V;
-  const uint32_t zs = zsyms[gc];
 
   // HUFF candidate: a code for all m symbols (skipped when the Shannon bound
   // already shows it cannot qualify)
@@ -505,7 +500,7 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
   } else {
     res.mode = kRaw;
     res.size = m;
-    if (lane == 0) meta[gc] = res;
+    if (lane == 0) *meta_out = res;
     return;
   }
 
@@ -514,7 +509,6 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
   for (int l = 0; l <= kMaxLen; l++) count[l] = 0;
   for (int l = 1; l <= kMaxLen; l++)
     for (int k = 0; k < 8; k++) count[l] += __popc(__ballot_sync(0xffffffffu, mylen[k] == l));
-  uint8_t* tab = tabs + gc * kTabBytes;
   if (lane < kMaxLen) tab[lane] = (uint8_t)count[lane + 1];
   uint32_t code0 = 0, first_idx = 0;
   const uint32_t ltmask = (1u << lane) - 1u;
@@ -532,7 +526,25 @@ k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
     }
     first_idx += count[l];
   }
-  if (lane == 0) meta[gc] = res;
+  if (lane == 0) *meta_out = res;
+}
+
+
+__global__ void __launch_bounds__(kBuildWarps * 32)
+k_build(JobRef jr, uint64_t ngc_total, const uint32_t* __restrict__ hist,
+        const uint32_t* __restrict__ zsyms, uint32_t* __restrict__ codes,
+        uint8_t* __restrict__ tabs, GcMeta* __restrict__ meta) {
+  __shared__ BuildSmem smem[kBuildWarps];
+  const int wid = threadIdx.x >> 5;
+  const uint64_t gc = (uint64_t)blockIdx.x * kBuildWarps + wid;
+  if (gc >= ngc_total) return;
+  const int j = find_job_gc(jr, gc);
+  const Job& J = job_at(jr, j);
+  const int es = elem_size(J.dtype), G = es;
+  const uint64_t c = (gc - J.gc_begin) / G;
+  const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
+  build_gc(hist + gc * 256, zsyms[gc], (uint32_t)(nb / es), J.lanes, es, smem[wid],
+           codes + gc * 256, tabs + gc * kTabBytes, meta + gc);
 }
 
 // ---------------------------------------------------------------------------
@@ -899,10 +911,54 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
   }
 }
 
+// Map entries of chunk c (threads 0..G-1) from S.meta and S.off.
+template <int G>
+__device__ __forceinline__ void write_map_entries(const Job& J, uint64_t c, const PackSmem& S) {
+  const int tid = threadIdx.x;
+  if (tid < G) {
+    uint8_t* e = J.dst + kHdrBytes + (c * G + tid) * kEntryBytes;
+    put_u64(e, S.off[tid]);
+    put_u32(e + 8, S.meta[tid].size);
+    e[12] = (uint8_t)S.meta[tid].mode;
+    e[13] = (uint8_t)S.meta[tid].value;
+    e[14] = 0;
+    e[15] = 0;
+  }
+}
+
+// Packing of chunk c whose mode records (S.meta), payload offsets (S.off) and
+// codes of its coded groups (S.codes) are in shared memory and whose map
+// entries have been written; tabp[g] points to group g's table bytes.
+template <int DT>
+__device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
+                                const uint8_t* const* tabp);
+
 template <int DT>
 __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
                            const uint32_t* codes, const uint8_t* tabs, const GcMeta* meta,
                            const uint64_t* offs) {
+  constexpr int G = PTraits<DT>::G;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint64_t gc0 = J.gc_begin + c * G;
+  if (tid < G) {
+    S.meta[tid] = meta[gc0 + tid];
+    S.off[tid] = offs[gc0 + tid];
+  }
+  __syncthreads();
+  write_map_entries<G>(J, c, S);
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if (S.meta[g].mode == kHuff || S.meta[g].mode == kSparse)
+      for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
+  const uint8_t* tabp[4] = {nullptr, nullptr, nullptr, nullptr};
+#pragma unroll
+  for (int g = 0; g < G; g++) tabp[g] = tabs + (gc0 + g) * kTabBytes;
+  pack_chunk_core<DT>(J, c, S, slots, tabp);
+}
+
+template <int DT>
+__device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
+                                const uint8_t* const* tabp) {
   constexpr int G = PTraits<DT>::G, V = PTraits<DT>::V, ES = 16 / V;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint64_t off0 = c * J.chunk_bytes;
@@ -918,20 +974,6 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
   const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
   uint8_t* out = J.dst;
-  const uint64_t gc0 = J.gc_begin + c * G;
-
-  if (tid < G) {
-    S.meta[tid] = meta[gc0 + tid];
-    S.off[tid] = offs[gc0 + tid];
-    uint8_t* e = out + kHdrBytes + (c * G + tid) * kEntryBytes;
-    put_u64(e, S.off[tid]);
-    put_u32(e + 8, S.meta[tid].size);
-    e[12] = (uint8_t)S.meta[tid].mode;
-    e[13] = (uint8_t)S.meta[tid].value;
-    e[14] = 0;
-    e[15] = 0;
-  }
-  __syncthreads();
   uint32_t huff = 0, raw = 0, sparse = 0;  // huff: every coded group (HUFF or SPARSE)
 #pragma unroll
   for (int g = 0; g < G; g++) {
@@ -939,10 +981,6 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     if (S.meta[g].mode == kSparse) sparse |= 1u << g;
     if (S.meta[g].mode == kRaw) raw |= 1u << g;
   }
-#pragma unroll
-  for (int g = 0; g < G; g++)
-    if (huff >> g & 1)
-      for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
   // SPARSE groups: the vector bitmap (bit v % 32 of word v / 32) is built in
   // pass A from the vectors it loads anyway; start from zero
   const uint32_t bmw = (uint32_t)((nvec + 31) / 32);
@@ -1085,7 +1123,7 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     uint8_t* p = out + P + S.off[g];
     const uint32_t nz = S.meta[g].nz;
     const uint32_t h = (uint32_t)align_up(12 + nz, 4);
-    const uint8_t* tab = tabs + (gc0 + g) * kTabBytes;
+    const uint8_t* tab = tabp[g];
     for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
     const uint32_t nbm = (sparse >> g & 1u) ? bmw : 0u;  // bitmap words (written in pass A)
     uint32_t* po = reinterpret_cast<uint32_t*>(p + h + 4 * nbm);
@@ -1188,6 +1226,25 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
   }
 }
 
+// The 64-byte container header of job J (one thread).
+__device__ void write_header(const Job& J, uint64_t total) {
+  uint8_t* h = J.dst;
+  const int G = elem_size(J.dtype);
+  const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+  h[0] = 'Z'; h[1] = 'N'; h[2] = 'N'; h[3] = '1';
+  h[4] = 1; h[5] = 0;
+  h[6] = (uint8_t)J.dtype;
+  h[7] = (uint8_t)J.flags;
+  put_u64(h + 8, J.nbytes);
+  put_u32(h + 16, J.chunk_bytes);
+  put_u32(h + 20, J.lanes);
+  put_u32(h + 24, (uint32_t)G);
+  put_u32(h + 28, J.n_chunks);
+  put_u64(h + 32, P);
+  put_u64(h + 40, total);
+  for (int k = 48; k < 64; k++) h[k] = 0;
+}
+
 template <int DTS>
 __global__ void __launch_bounds__(kPackThreads, 2)
 k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
@@ -1200,23 +1257,7 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
     const int j = (int)(blockIdx.x - nchunks_total);
     const Job& J = job_at(jr, j);
     if (totals[j] > J.out_capacity) return;
-    if (tid == 0) {
-      uint8_t* h = J.dst;
-      const int G = elem_size(J.dtype);
-      const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
-      h[0] = 'Z'; h[1] = 'N'; h[2] = 'N'; h[3] = '1';
-      h[4] = 1; h[5] = 0;
-      h[6] = (uint8_t)J.dtype;
-      h[7] = (uint8_t)J.flags;
-      put_u64(h + 8, J.nbytes);
-      put_u32(h + 16, J.chunk_bytes);
-      put_u32(h + 20, J.lanes);
-      put_u32(h + 24, (uint32_t)G);
-      put_u32(h + 28, J.n_chunks);
-      put_u64(h + 32, P);
-      put_u64(h + 40, totals[j]);
-      for (int k = 48; k < 64; k++) h[k] = 0;
-    }
+    if (tid == 0) write_header(J, totals[j]);
     return;
   }
   const uint64_t chunk = blockIdx.x;
@@ -1233,6 +1274,201 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
     case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, slots, codes, tabs, meta, offs); break;
     case ZIPNN_FP32: pack_chunk<ZIPNN_FP32>(J, c, S, slots, codes, tabs, meta, offs); break;
     default: pack_chunk<ZIPNN_U8>(J, c, S, slots, codes, tabs, meta, offs); break;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// k_compress: the whole encoder in one persistent kernel, for launches of one
+// dtype with at most two byte groups (BF16, FP16, U8).  Each CTA pulls chunks
+// from a device ticket and, per chunk:
+//   1. builds the histograms (the chunk's one read from DRAM);
+//   2. builds each group's code (warp g: group g) in shared memory;
+//   3. learns where its payloads go: the offset of a chunk within its
+//      container is the sum of the padded payload sizes of the chunks before
+//      it (the map of Sec. 5.1), found by a decoupled look-back over the
+//      chunks of its tensor (Merrill & Garland, "Single-pass Parallel Prefix
+//      Scan with Decoupled Look-back", 2016): the chunk publishes its own size
+//      at once, then adds up its predecessors' published sizes until one
+//      that has published its inclusive prefix;
+//   4. packs, reading the chunk again while it is still in L2 (two 512-thread
+//      CTAs per SM hold about 80 MB of chunks in flight).
+// The last chunk of a tensor writes its header and size.  Chunks are taken in
+// ticket order by running CTAs, so every chunk a look-back waits for belongs
+// to a CTA that is running or finished and publishes its size right after its
+// own code build: the wait always ends.  It is bounded all the same (%globaltimer,
+// 2 s): past the limit the chunk is not written and the call reports
+// ZIPNN_ETIMEOUT.  Work items past the chunks write the headers of empty tensors.
+
+constexpr uint64_t kLbAgg = 1ull << 62;    // look-back word: own padded size only
+constexpr uint64_t kLbIncl = 2ull << 62;   // look-back word: inclusive prefix
+constexpr uint64_t kLbValue = (1ull << 62) - 1;
+constexpr uint64_t kLbLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t enc_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const unsigned long long* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive prefix, within its tensor, of the chunk with global index `gchunk`
+// (index c within its tensor) whose payloads take `own` padded bytes.
+// *timed_out is set if a predecessor's word did not appear within the limit.
+// (Fault injection for tests, `hide`: the chunk publishes nothing, so the
+// look-backs that need it run out their limit.)
+__device__ uint64_t lookback(unsigned long long* lb, uint64_t gchunk, uint64_t c, uint64_t own,
+                             uint64_t limit_ns, bool hide, bool* timed_out) {
+  if (c == 0) {
+    if (!hide) st_relaxed_u64(lb + gchunk, kLbIncl | own);
+    return 0;
+  }
+  st_relaxed_u64(lb + gchunk, kLbAgg | own);
+  const uint64_t first = gchunk - c;  // the tensor's first chunk publishes an inclusive prefix
+  uint64_t prefix = 0, k = gchunk - 1;
+  const uint64_t t0 = enc_globaltimer();
+  for (;;) {
+    const uint64_t v = ld_relaxed_u64(lb + k);
+    if (!(v >> 62)) {
+      if (enc_globaltimer() - t0 > limit_ns) {
+        *timed_out = true;
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    prefix += v & kLbValue;
+    if ((v >> 62) == 2u) break;
+    if (k == first) {  // cannot happen: the first chunk's word is always inclusive
+      *timed_out = true;
+      break;
+    }
+    k--;
+  }
+  st_relaxed_u64(lb + gchunk, kLbIncl | (prefix + own));
+  return prefix;
+}
+
+struct FusedSmem {
+  uint32_t hist[2][256];       // bin totals of the chunk
+  uint32_t zs[2];              // symbols inside all-zero vectors
+  uint8_t tab[2][kTabBytes];   // table bytes of the coded groups
+  uint64_t chunk;              // the CTA's current work item
+  int job;                     // its job
+  uint32_t skip;               // 1: do not write the chunk (timed out / no room)
+};
+
+constexpr size_t kFusedDynBytes =
+    (size_t)kPackSlotWords * 4 > (size_t)(2 * 256 * 32 + 2) * 4
+        ? (size_t)kPackSlotWords * 4
+        : (size_t)(2 * 256 * 32 + 2) * 4;
+static_assert(2 * sizeof(BuildSmem) <= kFusedDynBytes, "build scratch must fit");
+
+template <int DT>
+__global__ void __launch_bounds__(kPackThreads, 2)
+k_compress(JobRef jr, uint64_t nchunks_total, unsigned long long* lb,
+           uint64_t* __restrict__ totals, uint32_t* __restrict__ err, uint32_t debug_flags) {
+  constexpr int G = PTraits<DT>::G, ES = 16 / PTraits<DT>::V;
+  static_assert(G <= 2, "the fused encoder handles at most two byte groups");
+  // counters of the histograms, then the code builders' scratch, then the
+  // packer's unit slots
+  extern __shared__ __align__(16) uint32_t dyn[];
+  __shared__ PackSmem S;
+  __shared__ FusedSmem F;
+  const int tid = threadIdx.x, wid = tid >> 5;
+  unsigned long long* ticket = lb + nchunks_total;
+  const uint64_t nitems = nchunks_total + (uint64_t)jr.n;
+  if (tid == 0) F.job = 0;
+  __syncthreads();
+  for (;;) {
+    // work item and its job (thread 0; items come in increasing order, so the
+    // job is found scanning forward from the previous one)
+    if (tid == 0) {
+      const uint64_t it = atomicAdd(ticket, 1ull);
+      int jj = 0;
+      if (it >= nchunks_total) {
+        jj = it < nitems ? (int)(it - nchunks_total) : 0;
+      } else if (jr.table) {
+        jj = F.job;
+        int steps = 0;
+        while (jj + 1 < jr.n && jr.table[jj + 1].chunk_begin <= it && steps < 8) {
+          jj++;
+          steps++;
+        }
+        if (steps == 8) jj += find_job(jr.table + jj, jr.n - jj, it);
+      }
+      F.chunk = it;
+      F.job = jj;
+    }
+    __syncthreads();
+    const uint64_t item = F.chunk;
+    if (item >= nitems) break;
+    const int j = F.job;
+    const Job& J = job_at(jr, j);
+    if (item >= nchunks_total) {
+      // header of an empty tensor (its only content)
+      if (tid == 0 && J.n_chunks == 0) {
+        const uint64_t total = kHdrBytes;
+        totals[j] = total;
+        if (J.out_nbytes) *J.out_nbytes = total;
+        if (total <= J.out_capacity) write_header(J, total);
+        else atomicOr(err, 2u);
+      }
+      __syncthreads();
+      continue;
+    }
+    const uint64_t c = item - J.chunk_begin;
+    const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - c * J.chunk_bytes);
+    // 1. histograms (ends past a barrier)
+    hist_chunk<DT, kPackThreads>(J, c, dyn, &F.hist[0][0], F.zs);
+    // 2. codes: warp g builds group g's
+    if (wid < G)
+      build_gc(F.hist[wid], F.zs[wid], (uint32_t)(nb / ES), J.lanes, ES,
+               reinterpret_cast<BuildSmem*>(dyn)[wid], S.codes[wid], F.tab[wid], &S.meta[wid]);
+    __syncthreads();
+    // 3. payload offsets (thread 0), header and size after the last chunk
+    if (tid == 0) {
+      uint64_t own = 0;
+#pragma unroll
+      for (int g = 0; g < G; g++) own += align_up(S.meta[g].size, 16);
+      bool timed_out = false;
+      // debug flag 1 (tests only): the first chunk of the launch hides its
+      // offset and the limit is 100 ms -> ETIMEOUT
+      const bool inject = (debug_flags & 1u) != 0;
+      const uint64_t prefix = lookback(lb, item, c, own, inject ? 100000000ull : kLbLimitNs,
+                                       inject && item == 0, &timed_out);
+      uint64_t run = prefix;
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        S.off[g] = run;
+        run += align_up(S.meta[g].size, 16);
+      }
+      const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
+      F.skip = (timed_out || P + run > J.out_capacity) ? 1u : 0u;
+      if (timed_out) atomicOr(err, 4u);
+      if (c + 1 == J.n_chunks) {
+        const uint64_t total = P + run;
+        totals[j] = total;
+        if (J.out_nbytes) *J.out_nbytes = total;
+        if (total > J.out_capacity) atomicOr(err, 2u);
+        else if (!timed_out) write_header(J, total);
+      }
+    }
+    __syncthreads();
+    // 4. map entries and packing (the chunk is read again, from L2)
+    if (!F.skip) {
+      write_map_entries<G>(J, c, S);
+      const uint8_t* tabp[4] = {F.tab[0], G > 1 ? F.tab[1] : nullptr, nullptr, nullptr};
+      pack_chunk_core<DT>(J, c, S, dyn, tabp);
+    }
+    __syncthreads();
   }
 }
 
@@ -1330,6 +1566,65 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
   kp<<<(unsigned)(nchunks_total + njobs), kPackThreads, ps, st>>>(r, nchunks_total, s.codes, s.tabs,
                                                                 s.meta, s.offs, s.totals);
   return cudaGetLastError();
+}
+
+bool fused_encoder_applies(int dtype, bool any_skip) {
+  return !any_skip && (dtype == ZIPNN_BF16 || dtype == ZIPNN_FP16 || dtype == ZIPNN_U8);
+}
+
+// The single-pass encoder (k_compress) for jobs of one dtype with at most two
+// groups and no skip-ahead probe.  Its look-back words (one per chunk) and
+// work ticket live in the histogram area of the scratch, which this kernel
+// does not otherwise use (it keeps its histograms in shared memory), and are
+// cleared here, on the stream, before the launch.
+cudaError_t launch_encode_fused(const Job* d_jobs, const Job* h_one, int njobs,
+                                uint64_t nchunks_total, const EncodeScratch& s, uint32_t* d_err,
+                                cudaStream_t st, int dtype, uint32_t debug_flags) {
+  JobRef r = make_ref(d_jobs, njobs, h_one);
+  unsigned long long* lb = reinterpret_cast<unsigned long long*>(s.hist);
+  cudaError_t e =
+      cudaMemsetAsync(lb, 0, (size_t)(nchunks_total + 2) * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const void* kern = dtype == ZIPNN_BF16   ? reinterpret_cast<const void*>(k_compress<ZIPNN_BF16>)
+                     : dtype == ZIPNN_FP16 ? reinterpret_cast<const void*>(k_compress<ZIPNN_FP16>)
+                                           : reinterpret_cast<const void*>(k_compress<ZIPNN_U8>);
+  const int dynb = (int)kFusedDynBytes;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dynb);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPackThreads, dynb);
+  if (occ < 1) occ = 1;
+  const uint64_t items = nchunks_total + (uint64_t)njobs;
+  uint64_t grid = (uint64_t)sms * (uint64_t)occ;
+  if (grid > items) grid = items;
+  if (grid < 1) grid = 1;
+  uint64_t* totals = s.totals;
+  void* args[] = {&r, &nchunks_total, &lb, &totals, &d_err, &debug_flags};
+  return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kPackThreads), args, (size_t)dynb, st);
+}
+
+cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64_t nchunks_total,
+                          uint64_t ngc_total, const EncodeScratch& s, uint32_t* d_err,
+                          cudaStream_t st, int max_groups, int max_lanes, int uniform_dtype,
+                          bool any_skip, int encoder, uint32_t debug_flags) {
+  const int dt = h_one ? h_one->dtype : uniform_dtype;
+  const bool skip = h_one ? h_one->skip != 0 : any_skip;
+  // (a launch of empty tensors only has no chunk, hence no histogram area to
+  // hold the single-pass kernel's ticket: the four-kernel path writes its headers)
+  if (encoder == 0 && nchunks_total > 0 && fused_encoder_applies(dt, skip))
+    return launch_encode_fused(d_jobs, h_one, njobs, nchunks_total, s, d_err, st, dt,
+                               debug_flags);
+  cudaError_t e = launch_encode_analyse_ex(d_jobs, h_one, njobs, nchunks_total, ngc_total, s,
+                                           d_err, st, max_groups, uniform_dtype);
+  if (e == cudaSuccess)
+    e = launch_encode_pack_ex(d_jobs, h_one, njobs, nchunks_total, max_lanes, s, st,
+                              uniform_dtype);
+  return e;
 }
 
 }  // namespace zipnn

@@ -34,6 +34,15 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
                                   cudaStream_t st, int uniform_dtype);
+// The whole encoder: the single-pass kernel (histogram, code build, offsets by
+// look-back, packing: one launch after a memset of its look-back words) when
+// every job is BF16, FP16 or U8 and none uses the skip-ahead probe and
+// encoder == 0, else the four kernels above.  Both write the same bytes.
+cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64_t nchunks_total,
+                          uint64_t ngc_total, const EncodeScratch& s, uint32_t* d_err,
+                          cudaStream_t st, int max_groups, int max_lanes, int uniform_dtype,
+                          bool any_skip, int encoder, uint32_t debug_flags = 0);
+bool fused_encoder_applies(int dtype, bool any_skip);
 
 // Decoder (decode.cu): one persistent launch over all chunks of the jobs.
 // d_ticket: the device work queue, two 64-bit counters that must be zero

@@ -22,8 +22,11 @@
 //     sizing function as the workspace entry point, so the figure cannot
 //     drift from the layout);
 //   - all calls on a device share the array and it keeps the last call's
-//     contents.  Nothing in it has to start at zero: every scratch word a call
-//     reads was written earlier by the same call.  Two calls whose kernels
+//     contents.  The one part that must start at zero (the single-pass
+//     encoder's per-chunk offset words and work counter, at the front of the
+//     array) is cleared by each call itself, on its stream, before its
+//     kernel; every other scratch word a call reads was written earlier by
+//     the same call.  Two calls whose kernels
 //     overlap on the GPU (e.g. on two streams without ordering) race on the
 //     array and produce garbage: order them on one stream or with events;
 //   - the first call on a device looks up the array's device address with
@@ -115,7 +118,6 @@ extern "C" zipnn_status zipnn_compress_into_static(const void* d_src, const void
   EncodeScratch s;
   encode_scratch_carve(scratch, nch, ngc, 1, &s);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  e = launch_encode_analyse_ex(nullptr, &J, 1, nch, ngc, s, err, st, 0, -1);
-  if (e == cudaSuccess) e = launch_encode_pack_ex(nullptr, &J, 1, nch, (int)lanes, s, st, -1);
+  e = launch_encode(nullptr, &J, 1, nch, ngc, s, err, st, 0, (int)lanes, -1, false, 0);
   return e == cudaSuccess ? ZIPNN_OK : ZIPNN_ECUDA;
 }

@@ -319,11 +319,8 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   e = cudaMemcpy(d_jobs, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(p, e);
   e = capture(p, [&](cudaStream_t cs) {
-    cudaError_t e2 = launch_encode_analyse_ex(d_jobs, nullptr, count, nch, ngc, s, err, cs,
-                                              max_groups, uniform);
-    if (e2 == cudaSuccess)
-      e2 = launch_encode_pack_ex(d_jobs, nullptr, count, nch, max_lanes, s, cs, uniform);
-    return e2;
+    return launch_encode(d_jobs, nullptr, count, nch, ngc, s, err, cs, max_groups, max_lanes,
+                         uniform, false, 0);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;

@@ -54,7 +54,7 @@ class ZStream(ctypes.Structure):
 
 class ZEncodeOptions(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("probe_skip", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("encoder", ctypes.c_uint32), ("debug_flags", ctypes.c_uint32)]
 
 
 class ZTuning(ctypes.Structure):
@@ -345,10 +345,12 @@ class BatchCompressor:
     Arguments are marshalled once; each call() enqueues the four encoder
     kernels for all tensors (zipnn_batch_compress_into_ex).  probe_skip > 0
     applies the skip-ahead probe (Sec. 3.2): after a raw group-chunk the same
-    group of the next probe_skip chunks is stored raw."""
+    group of the next probe_skip chunks is stored raw.  encoder = 1 forces the
+    four-kernel encoder (0: the single-pass kernel where it applies)."""
 
     def __init__(self, xs: list[torch.Tensor], chunk_bytes: int | None = None, lanes: int = 0,
-                 bases: list[torch.Tensor | None] | None = None, probe_skip: int = 0):
+                 bases: list[torch.Tensor | None] | None = None, probe_skip: int = 0,
+                 encoder: int = 0, debug_flags: int = 0):
         n = len(xs)
         if chunk_bytes is None:
             # the autotuner's setting for this workload when one is cached,
@@ -377,7 +379,7 @@ class BatchCompressor:
         self._bases = _ptrs(bases) if bases is not None else None
         self._outs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
         self.lanes = lanes
-        self.opts = ZEncodeOptions(lanes, probe_skip, (ctypes.c_uint32 * 2)(0, 0))
+        self.opts = ZEncodeOptions(lanes, probe_skip, encoder, debug_flags)
         self.n = n
 
     def __call__(self, stream=None) -> None:
