@@ -579,16 +579,18 @@ def measure_tensors(label: str, xs, bases, args, steps: int, warmup: int,
     from paper_2411_05239_gb300 import zipnn as Z
     hbm_peak, peak_kind = peaks()
     orig = sum(x.numel() * x.element_size() for x in xs)
-    bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases, lanes=args.lanes)
+    bc = Z.BatchCompressor(xs, chunk_bytes=args.chunk, bases=bases, lanes=args.lanes,
+                           encoder=getattr(args, "encoder", 0))
     bc()
     Z.sync_status()
     cs = bc.containers()
     comp = sum(c.nbytes for c in cs)
     outs = [torch.empty_like(x) for x in xs]
-    pc = Z.plan_compress(bc)
+    pc = Z.plan_compress(bc) if not getattr(args, "encoder", 0) else None
     pd = Z.plan_decompress(cs, outs, bases=bases,
                            tune=Z.tuning(threads=args.threads, lut_bits=args.lut_bits,
-                                         ctas_per_sm=args.ctas_per_sm))
+                                         ctas_per_sm=args.ctas_per_sm,
+                                         parts=getattr(args, "parts", 0)))
     pd.launch()
     Z.sync_status()
     for x, o in zip(xs, outs):
@@ -602,7 +604,10 @@ def measure_tensors(label: str, xs, bases, args, steps: int, warmup: int,
         e = ev[k - warmup] if k >= warmup else None
         flush.fill_(k & 255)
         if e: e[0].record(st)
-        pc.launch(st)
+        if pc is not None:
+            pc.launch(st)
+        else:
+            bc(st)                      # the single-pass encoder: a direct batched call
         if e: e[1].record(st)
         flush.fill_((k + 1) & 255)
         if e: e[2].record(st)
@@ -631,10 +636,12 @@ def measure_tensors(label: str, xs, bases, args, steps: int, warmup: int,
                "sample": f"first {r['bytes'] >> 20} MiB of the tensor"
                          + (" and its base" if bases else "")
                          + "; oracle compress then decompress, 1 thread"}
-    pc.close()
+    if pc is not None:
+        pc.close()
     pd.close()
     return {
         "workload": label, "bytes": orig, "chunk_bytes": args.chunk, "steps": K,
+        "encoder": "single-pass" if pc is None else "four kernels",
         "decompress_gbs": orig / (dmean / 1e3) / 1e9, "compress_gbs": orig / (cm / 1e3) / 1e9,
         "ratio": comp / orig,
         "decompress_ms": {"mean": dmean, "p99": dm[min(K - 1, int(math.ceil(0.99 * K)) - 1)]},
@@ -687,6 +694,9 @@ class ServeChecks:
         self.rng = np.random.default_rng(seed + 1)
         self.inputs = inputs
         self.scratch = torch.empty(maxb + 16, dtype=torch.uint8, device="cuda")
+        # comparison result, preallocated: no allocation (which could stall
+        # the whole device) while the stream is served
+        self.neq = torch.empty(maxb + 16, dtype=torch.bool, device="cuda")
         self.kept = []          # (rid, dtype, lanes, [(chunk bytes, [(mode, value, payload)])])
         self.checked = 0
         # mismatching bytes, summed on the device without waiting for it (the
@@ -721,12 +731,21 @@ class ServeChecks:
             c = self._stream_of(r, out)
             y = self.scratch[:r.nbytes]
             Z.decompress(c, out=y.view(x.dtype) if r.nbytes else y, base=b)
-            self.bad += (y != xb).sum()
+            self._count(y, xb)
             if r.rid in self.sample:
                 self.kept.append(self._chunks(r, Z.wrap(out), x, b))
         else:
-            self.bad += (out != xb).sum()
+            self._count(out, xb)
         self.checked += 1
+
+    def _count(self, a: torch.Tensor, b: torch.Tensor) -> None:
+        n = a.numel()
+        if n != b.numel():
+            raise SystemExit("result size differs from the input")
+        if n:
+            ne = self.neq[:n]
+            torch.ne(a, b, out=ne)
+            self.bad += ne.sum()
 
     def identity_verdict(self) -> None:
         from paper_2411_05239_gb300 import zipnn as Z
@@ -792,6 +811,39 @@ def measure_serve(args, n_requests: int, rate: float) -> dict:
             containers[r.rid] = Z.compress(x, base=b)
     torch.cuda.synchronize()
     checks = ServeChecks(trace, inputs, maxb)
+
+    # warm-up (untimed): a few requests of every kind through a server and the
+    # plain calls, so that first launches (kernel loading, pool growth) stay
+    # out of both paths' figures
+    kinds = {}
+    for r in trace:
+        kinds.setdefault((r.op, r.dtype, r.delta), r)
+    srv = Z.Server(args.serve_budget_gb << 30, slots=args.serve_slots)
+    warm_bytes = torch.empty(Z.compress_bound(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
+                             device="cuda")
+    warm_ws = torch.empty(Z.workspace_size(maxb, Z.FP32, Z.DEFAULT_CHUNK), dtype=torch.uint8,
+                          device="cuda")
+    for r in kinds.values():
+        x, b = inputs(r)
+        if r.op == "compress":
+            srv.submit_compress(x, base=b, tag=r.rid)
+            Z.compress_into(x, warm_bytes, warm_ws, base=b)
+        else:
+            srv.submit_decompress(containers[r.rid], base=b, tag=r.rid)
+            Z.decompress(containers[r.rid], out=warm_bytes[:r.nbytes].view(x.dtype), base=b)
+    left, t_end = len(kinds), time.monotonic() + 300
+    while left:
+        if time.monotonic() > t_end:
+            raise SystemExit("warm-up requests did not complete")
+        for c in srv.poll():
+            if c.status != 0:
+                raise SystemExit(f"warm-up request {c.tag} failed: {c.status}")
+            srv.release(c.id)
+            left -= 1
+        time.sleep(0.001)
+    srv.close()
+    del warm_bytes, warm_ws
+    torch.cuda.synchronize()
 
     # served path
     srv = Z.Server(args.serve_budget_gb << 30, slots=args.serve_slots)
@@ -911,6 +963,11 @@ def main(argv=None):
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--lut-bits", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0, help="sub-streams per chunk (0 = default)")
+    ap.add_argument("--parts", type=int, default=0,
+                    help="decoder work items per chunk for the single-tensor workloads "
+                         "(0 = automatic, 1 = never split)")
+    ap.add_argument("--encoder", type=int, default=0,
+                    help="0 = four-kernel encoder, 1 = single-pass encoder where it applies")
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick chunk size, lanes, table width, CTAs/SM on a sample first")
     ap.add_argument("--e2e-steps", type=int, default=3)

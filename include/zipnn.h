@@ -94,6 +94,11 @@ typedef struct zipnn_tuning {
                              waits for 16 bytes that are never copied, so its
                              bounded wait gives up after 100 ms and the call
                              reports ZIPNN_ETIMEOUT via zipnn_sync_status */
+    int32_t parts;        /* work items per chunk: 0 = automatic (launches whose
+                             chunks would fill at most half the SMs split each
+                             model-weight chunk's sub-streams over 2 or 4 work
+                             items of 128-thread CTAs), 1 = never split, 2 or
+                             4 = split whenever the lanes allow */
 } zipnn_tuning;
 
 /* Library version (the container version is 1). */
@@ -190,13 +195,14 @@ zipnn_status zipnn_batch_compress_into(const void* const* d_srcs, const void* co
  *   of the next probe_skip chunks of the tensor is stored raw without its
  *   decision counting, then decisions resume; 0 = every group-chunk decided on
  *   its own (the default).  The containers stay valid version-1 containers.
- * encoder: 0 = automatic: batches whose tensors are all BF16, all FP16 or all
- *   U8, without probe_skip, run the single-pass encoder (one persistent
- *   kernel: each chunk's histograms, codes, offset -- by a bounded look-back
- *   over the chunks before it -- and packing, the second read of the chunk
- *   coming from L2); others run four kernels (histograms, codes, offsets,
- *   packing).  1 = always the four kernels.  Both write the same bytes.
- *   EINVAL for other values.
+ * encoder: 0 = four kernels (histograms, codes, offsets, packing; the
+ *   default, and the faster on GB300).  1 = the single-pass encoder for
+ *   batches whose tensors are all BF16, all FP16 or all U8, without
+ *   probe_skip (one persistent kernel: each chunk's histograms, codes, offset
+ *   -- by a bounded look-back over the chunks before it -- and packing, the
+ *   chunk's second read coming from L2 when it is still there); the four
+ *   kernels for other batches.  Both write the same bytes.  EINVAL for other
+ *   values.
  * debug_flags: 0.  Bit 0 is fault injection for tests of the single-pass
  *   encoder: the launch's first chunk never publishes its payload size, so the
  *   look-backs that need it give up after 100 ms; those chunks are not

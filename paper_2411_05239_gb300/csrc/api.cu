@@ -465,7 +465,7 @@ zipnn_status zipnn_decompress(const zipnn_stream* s, const void* d_base_or_null,
   cudaError_t e = launch_decode_ex(nullptr, &J, 1, J.n_chunks, (int)s->n_groups, nullptr, err,
                                    nullptr, st, s->dtype, s->chunk_bytes, s->lanes % 256 == 0,
                                    stage_frac64(s->dtype, s->flags),
-                                   (s->flags & ZIPNN_FLAG_DELTA) != 0, false, 0u);
+                                   (s->flags & ZIPNN_FLAG_DELTA) != 0, false, 0u, s->lanes);
   return cuda_status(e);
 }
 
@@ -480,8 +480,10 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   int uniform = streams[0].dtype;
   bool lanes256 = true, has_delta = false;
   int frac64 = 0;
+  uint32_t common_lanes = streams[0].lanes;
   for (int i = 0; i < count; i++) {
     const zipnn_stream* s = &streams[i];
+    if (s->lanes != common_lanes) common_lanes = 0;
     if (s->flags & ZIPNN_FLAG_DELTA) has_delta = true;
     if (s->dtype != uniform) uniform = -1;
     if (s->chunk_bytes > max_chunk) max_chunk = s->chunk_bytes;
@@ -513,7 +515,8 @@ zipnn_status zipnn_batch_decompress(const zipnn_stream* streams, const void* con
   e = g_ring.h2d(d_jobs, up.data(), up.size(), st);
   if (e == cudaSuccess)
     e = launch_decode_ex(d_jobs, nullptr, count, chunk, max_groups, tuning, err, d_ticket, st,
-                         uniform, max_chunk, lanes256, frac64, has_delta, false, 0u);
+                         uniform, max_chunk, lanes256, frac64, has_delta, false, 0u,
+                         common_lanes);
   cudaFreeAsync(dmem, st);
   return cuda_status(e);
 }

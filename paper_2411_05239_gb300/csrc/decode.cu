@@ -45,7 +45,8 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
                              int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta, bool general, uint32_t stage_need) {
+                             bool has_delta, bool general, uint32_t stage_need,
+                             uint32_t common_lanes) {
   if (nchunks_total == 0) return cudaSuccess;
   JobRef r;
   r.table = h_one ? nullptr : d_jobs;
@@ -58,6 +59,7 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
     lanes256 = h_one->lanes % 256 == 0;
     frac64 = stage_frac64(h_one->dtype, h_one->flags);
     has_delta = (h_one->flags & ZIPNN_FLAG_DELTA) != 0;
+    common_lanes = h_one->lanes;
   }
   int w = (tuning && tuning->lut_bits) ? tuning->lut_bits : 12;
   if (w < 10) w = 10;
@@ -66,12 +68,33 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   // whose lane counts are multiples of 256 (one or two sub-streams per
   // thread in the fast loop), else 128
   const int want = (tuning && tuning->threads) ? tuning->threads : 256;
-  const int threads =
+  int threads =
       (want == 256 && w >= 11 && uniform_dtype >= 0 && lanes256) ? 256 : kDecThreads;
   // the GEN kernels for launches with deltas or, as a plan's chunk maps show,
   // chunks with two coded groups or a SPARSE first group; W = 10 has no fast
   // loops and no GEN kernels
   const bool gen = has_delta || general;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // Launches with few chunks (no more than half as many as SMs) split every
+  // chunk of the model-weight layout over `parts` work items -- disjoint
+  // sub-stream ranges, each a whole number of rounds of a 128-thread CTA --
+  // so that more SMs work on them (tuning->parts: 0 = this rule, 1 = never,
+  // 2 or 4 = whenever the lanes allow)
+  uint32_t parts = 1;
+  const int want_parts = tuning ? tuning->parts : 0;
+  if (!gen && w >= 11 && uniform_dtype >= 0 && common_lanes && want_parts != 1) {
+    for (uint32_t p = 4; p >= 2; p /= 2) {
+      if (common_lanes % (p * (uint32_t)kDecThreads) != 0) continue;
+      if (want_parts == 0 && nchunks_total * 2 > (uint64_t)sms) break;
+      if (want_parts == 0 && nchunks_total * p > 2ull * (uint64_t)sms) continue;
+      if (want_parts != 0 && (uint32_t)want_parts != p) continue;
+      parts = p;
+      threads = kDecThreads;
+      break;
+    }
+  }
   const void* kern =
       w == 10   ? decode_kernel_w10_128(uniform_dtype, false)
       : w == 11 ? (threads == 256 ? decode_kernel_w11_256(uniform_dtype, gen)
@@ -96,21 +119,18 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
   if (occ < 1) occ = 1;
   if (per_sm == 0 || per_sm > occ) per_sm = occ;
   uint64_t grid = (uint64_t)sms * per_sm;
-  if (grid > nchunks_total) grid = nchunks_total;
+  if (grid > nchunks_total * parts) grid = nchunks_total * parts;
   uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
   // the fast loops' L2 prefetch budget, shared by the CTAs that run at once
   uint64_t pf64 = kPfBudget / grid;
   uint32_t pf = (uint32_t)(pf64 > (64u << 20) ? (64u << 20) : pf64);
   // the kernel's parameters, in the order of k_decode's signature
-  void* args[] = {&r, &nchunks_total, &d_err, &d_ticket, &dbg, &stage, &pf};
+  void* args[] = {&r, &nchunks_total, &d_err, &d_ticket, &dbg, &stage, &pf, &parts};
   e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3((unsigned)threads), args, (size_t)smem, st);
   return e;
 }

@@ -151,6 +151,7 @@ struct Smem {
   uint32_t* lut_ptr[4];  // pair table of each Huffman group
   unsigned long long chunk;
   int job;               // job of the CTA's previous work item
+  uint32_t part;         // part of the chunk (chunks split over several work items)
 };
 
 // Groups carried as Huffman sub-streams: HUFF, and SPARSE (the same after a
@@ -615,9 +616,13 @@ struct RawRing {
 // with the rotated exponent symbols, a 16-B store.  No mode tests and no tails
 // inside the loop.  Each sub-stream must end exactly where the next one starts
 // (the last one within the bitstream); a mismatch flags the chunk as corrupt.
-template <int DT, int W, int NS>
+// The loop covers the sub-streams [t_lo, t_hi) of the chunk (all of them, or
+// one part of a chunk split over several work items), t_hi - t_lo a multiple
+// of NS * nthr.
+template <int DT, int W, int NS, bool SPLIT>
 __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem& S,
-                                            const Staging& stg, uint32_t* err) {
+                                            const Staging& stg, uint32_t* err, uint32_t t_lo,
+                                            uint32_t t_hi) {
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V;
   constexpr int RW = DT == ZIPNN_FP32 ? 3 : (DT == ZIPNN_U8 ? 1 : 2);
   constexpr bool RING = DT == ZIPNN_FP32;
@@ -657,7 +662,8 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   const bool pfl = DT == ZIPNN_FP32 && (tid & 31) == 0 && T == (uint32_t)(NS * nthr);
   const uint32_t wid = (uint32_t)tid >> 5, wmask = ((uint32_t)nthr >> 5) - 1u;
   const uint32_t D = pfl ? pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes) : 0u;
-  for (uint32_t t0 = tid; t0 < T; t0 += NS * nthr) {
+  const uint32_t t_begin = SPLIT ? t_lo : 0u, t_end = SPLIT ? t_hi : T;
+  for (uint32_t t0 = t_begin + tid; t0 < t_end; t0 += NS * nthr) {
     uint32_t w0[NS], w1[NS], pos[NS], idx[NS], vt[NS];
     uint32_t ra[NS][RW], rb[NS][RW];  // 16-bit: raw words of vectors k (even) and k + 1
     // FP32: raw words of step k into ring slot k mod RD (always one commit
@@ -1050,9 +1056,22 @@ __device__ __noinline__ void decode_other(const Job& J, uint64_t c, Smem& S, Sta
 // false if a bulk copy never completed (the caller must stop using the stage).
 // Shared memory: one table slot (lut0) for the first Huffman group; tables of
 // further Huffman groups and the staged payloads share the stage.
-template <int DT, int W, bool GEN>
+// With parts > 1 the chunk is one of `parts` work items (part = 0..parts-1):
+// a chunk of the dominant layout (below) whose T sub-streams split into
+// `parts` ranges that each fill whole rounds of the CTA's threads is decoded
+// range by range, part p doing sub-streams [p T / parts, (p+1) T / parts)
+// (each part stages the chunk's payload and builds its table); any other
+// chunk is decoded whole by part 0, and the other parts leave after reading
+// its map entries.
+// (SPLIT: compiled into the 128-thread kernels only, the ones split launches
+// use; the other kernels keep parts = 1 and their register allocation.)
+template <int DT, int W, bool GEN, bool SPLIT>
 __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, Staging& stg,
-                             uint32_t* err) {
+                             uint32_t* err, uint32_t part, uint32_t parts) {
+  if constexpr (!SPLIT) {
+    part = 0;
+    parts = 1;
+  }
   constexpr int G = Traits<DT>::G, V = Traits<DT>::V, ES = 16 / V;
   constexpr int kLut = 1 << W;
   constexpr uint32_t kLutBytes = 4u << W;
@@ -1086,9 +1105,29 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   }
   __syncthreads();
   if (CI.bad) {
-    if (tid == 0) atomicOr(err, 1u);
+    if (tid == 0 && part == 0) atomicOr(err, 1u);
     return true;
   }
+  // 1b. split over parts: only the dominant layout of model weights (group 0
+  // HUFF and stageable, the others raw, zero or constant, a whole chunk, the
+  // parts' sub-stream ranges whole rounds of the CTA's threads); this is
+  // decided before any bulk copy is issued, so a part that leaves has none
+  // in flight
+  bool split = false;
+  if (SPLIT && parts > 1) {
+    if constexpr (SPLIT && W >= 11 && !GEN) {
+      bool ok = CI.mode[0] == kHuff && nb == J.chunk_bytes && ((uint32_t)(nb / 16) % T) == 0 &&
+                T % parts == 0 && ((T / parts) % (uint32_t)nthr) == 0 &&
+                align_up(CI.size[0], 16) + 32 <= stg.cap;
+#pragma unroll
+      for (int g = 1; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
+      split = ok;
+    }
+    if (!split && part != 0) return true;  // part 0 decodes the whole chunk
+  }
+  const uint32_t t_lo = SPLIT && split ? part * (T / parts) : 0u;
+  const uint32_t t_hi = SPLIT && split ? t_lo + T / parts : T;
+  const uint32_t Tp = t_hi - t_lo;
   // 2. placement of tables and payloads; thread 0 issues the bulk copies
   if (tid == 0) {
     uint32_t nhuff = 0, pay_total = 0;
@@ -1188,13 +1227,13 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     }
 #pragma unroll
     for (int g = fast_nc; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
-    if (ok) fast = (T % (2u * nthr) == 0) ? 2 : ((T % (uint32_t)nthr == 0) ? 1 : 0);
+    if (ok) fast = (Tp % (2u * nthr) == 0) ? 2 : ((Tp % (uint32_t)nthr == 0) ? 1 : 0);
   }
   // exponent symbols are stored rotated for the fast loops' merge
   const bool rot0 = fast != 0 && DT != ZIPNN_U8;
   // the fast loop's first L2 prefetch window, in flight while the tables are
   // built (same raw groups and window as the loop computes)
-  if (fast != 0 && tid == 0 && T == (uint32_t)(fast * nthr)) {
+  if (fast != 0 && tid == 0 && Tp == (uint32_t)(fast * nthr)) {
     const uint8_t* rawp[G];
     uint32_t rawm = 0;
 #pragma unroll
@@ -1204,8 +1243,11 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     }
     const uint8_t* base8 = J.base ? J.base + c * J.chunk_bytes : nullptr;
     const uint32_t nper = (J.chunk_bytes / 16u) / T;
-    prefetch_steps<G>(rawp, rawm, base8, T, 0u,
-                      pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes));
+    // the window's steps cover every sub-stream of the chunk: a part of a
+    // split chunk requests its share of the steps (the parts run together)
+    const uint32_t D = pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes);
+    prefetch_steps<G>(rawp, rawm, base8, T, SPLIT && split ? part * D / parts : 0u,
+                      SPLIT && split ? (part + 1) * D / parts : D);
   }
   // 3c. pair tables, in two passes.  Pass 1: for window w (W bits) the first
   // code has length l1 = the least l <= W with w < lim_W[l] (W + 1 if none);
@@ -1316,11 +1358,11 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   if constexpr (W >= 11) {
     if (fast_nc == 1 && CI.mode[0] == kHuff) {
       if (fast == 2) {
-        decode_fast<DT, W, 2>(J, c, S, stg, err);
+        decode_fast<DT, W, 2, SPLIT>(J, c, S, stg, err, t_lo, t_hi);
         return true;
       }
       if (fast == 1) {
-        decode_fast<DT, W, 1>(J, c, S, stg, err);
+        decode_fast<DT, W, 1, SPLIT>(J, c, S, stg, err, t_lo, t_hi);
         return true;
       }
     }
@@ -1344,7 +1386,7 @@ template <int DTS, int W, int NT, bool GEN>
 __global__ void __launch_bounds__(NT, NT == 256 ? (GEN ? 2 : 3) : 1)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
          unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap,
-         uint32_t pf_bytes) {
+         uint32_t pf_bytes, uint32_t parts) {
   extern __shared__ __align__(128) uint8_t dsm[];  // [table slot 0] | stage
   __shared__ Smem S;
   __shared__ uint64_t bar;
@@ -1374,7 +1416,12 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     // items come in increasing order, so the job is found by scanning forward
     // from the previous item's job (a few steps; after eight, a search).
     if (tid == 0) {
-      const uint64_t ch = ticket ? atomicAdd(ticket, 1ull) : blockIdx.x + iter * gridDim.x;
+      // work item -> chunk (and, below, the part of a chunk split over
+      // `parts` items; parts = 1 but for launches with few chunks)
+      const uint64_t itm = ticket ? atomicAdd(ticket, 1ull) : blockIdx.x + iter * gridDim.x;
+      const uint32_t np = NT == kDecThreads ? parts : 1u;  // split launches use 128 threads
+      const uint64_t ch = np > 1 ? itm / np : itm;
+      S.part = np > 1 ? (uint32_t)(itm - ch * np) : 0u;
       int jj = 0;
       if (jr.table && ch < nchunks_total) {
         jj = S.job;
@@ -1394,15 +1441,22 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     const int j = S.job;
     const Job& J = jr.table ? jr.table[j] : jr.one;
     const uint64_t c = chunk - J.chunk_begin + J.chunk0;
+    const uint32_t part = S.part;
     bool ok;
     if (DTS >= 0) {
-      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN>(J, c, S, lut0, stg, err);
+      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
     } else {
       switch (J.dtype) {
-        case ZIPNN_BF16: ok = decode_chunk<ZIPNN_BF16, W, GEN>(J, c, S, lut0, stg, err); break;
-        case ZIPNN_FP16: ok = decode_chunk<ZIPNN_FP16, W, GEN>(J, c, S, lut0, stg, err); break;
-        case ZIPNN_FP32: ok = decode_chunk<ZIPNN_FP32, W, GEN>(J, c, S, lut0, stg, err); break;
-        default: ok = decode_chunk<ZIPNN_U8, W, GEN>(J, c, S, lut0, stg, err); break;
+        case ZIPNN_BF16:
+          ok = decode_chunk<ZIPNN_BF16, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          break;
+        case ZIPNN_FP16:
+          ok = decode_chunk<ZIPNN_FP16, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          break;
+        case ZIPNN_FP32:
+          ok = decode_chunk<ZIPNN_FP32, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          break;
+        default: ok = decode_chunk<ZIPNN_U8, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts); break;
       }
     }
     if (!ok) break;  // a bulk copy timed out: leave the stage alone
@@ -1423,7 +1477,7 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
 }
 
 using DecodeKernel = void (*)(JobRef, uint64_t, uint32_t*, unsigned long long*, uint32_t,
-                             uint32_t, uint32_t);
+                             uint32_t, uint32_t, uint32_t);
 
 // (Every translation unit instantiates the mixed-batch kernels its switch
 // names: they share the dtype-specialised out-of-line decode functions with

@@ -59,6 +59,31 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Shared-memory accesses through 32-bit shared-window addresses: the tables
+// and slots below are reached through pointers the compiler cannot always
+// place in shared memory, and would otherwise use generic loads and stores.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {  // read-only data (code tables)
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds32v(uint32_t saddr) {  // data written in this kernel
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t saddr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+// Code table entry (len << 16 | code) of byte k of w, table at shared address cb.
+__device__ __forceinline__ uint32_t code_of(uint32_t cb, uint32_t w, int k) {
+  return lds32(cb + 4u * __byte_perm(w, 0, 0x4440 + k));
+}
+
+
 __device__ __forceinline__ uint4 load_vec(const uint8_t* src, const uint8_t* base, uint64_t v,
                                           uint64_t nb) {
   uint4 a;
@@ -741,7 +766,7 @@ struct BitWriter {
 // Counts every bit; words past the slot are dropped (the unit then takes the
 // fallback path that re-reads its input).
 struct SlotWriter {
-  uint32_t* slot;
+  uint32_t slot;   // shared-window address of the unit's slot
   uint64_t acc;
   uint32_t nacc, wi, cap, bits;
   __device__ __forceinline__ void put(uint32_t x, uint32_t n) {  // n <= 32, x < 2^n
@@ -750,7 +775,7 @@ struct SlotWriter {
     bits += n;
     if (nacc >= 32) {
       nacc -= 32;
-      if (wi < cap) slot[wi] = (uint32_t)(acc >> nacc);
+      if (wi < cap) sts32(slot + 4u * wi, (uint32_t)(acc >> nacc));
       wi++;
       acc &= (1ull << nacc) - 1ull;
     }
@@ -764,7 +789,7 @@ struct SlotWriter {
     }
   }
   __device__ __forceinline__ void finish() {
-    if (nacc > 0 && wi < cap) slot[wi] = (uint32_t)(acc << (32 - nacc));
+    if (nacc > 0 && wi < cap) sts32(slot + 4u * wi, (uint32_t)(acc << (32 - nacc)));
   }
 };
 
@@ -773,7 +798,7 @@ struct SlotWriter {
 // shift and stores a word when 32 bits are complete.  Same bits, counts and
 // overflow rule as SlotWriter.
 struct SlotWriter32 {
-  uint32_t* slot;
+  uint32_t slot;   // shared-window address of the unit's slot
   uint32_t cur, nb, wi, cap, bits;
   __device__ __forceinline__ void put(uint32_t x, uint32_t n) {  // 1 <= n <= 32, x < 2^n
     const uint32_t total = nb + n;                                // <= 63
@@ -781,7 +806,7 @@ struct SlotWriter32 {
     const uint32_t hi = cur | (uint32_t)(X >> 32);
     bits += n;
     if (total >= 32) {
-      if (wi < cap) slot[wi] = hi;
+      if (wi < cap) sts32(slot + 4u * wi, hi);
       wi++;
       cur = (uint32_t)X;
       nb = total - 32;
@@ -799,14 +824,14 @@ struct SlotWriter32 {
     }
   }
   __device__ __forceinline__ void finish() {
-    if (nb > 0 && wi < cap) slot[wi] = cur;
+    if (nb > 0 && wi < cap) sts32(slot + 4u * wi, cur);
   }
 };
 
 // Codes of 4 consecutive symbols (bytes of w) joined MSB-first: <= 48 bits.
-__device__ __forceinline__ uint64_t join4(const uint32_t* codes, uint32_t w, uint32_t& len) {
-  uint32_t e0 = codes[__byte_perm(w, 0, 0x4440)], e1 = codes[__byte_perm(w, 0, 0x4441)];
-  uint32_t e2 = codes[__byte_perm(w, 0, 0x4442)], e3 = codes[__byte_perm(w, 0, 0x4443)];
+__device__ __forceinline__ uint64_t join4(uint32_t cb, uint32_t w, uint32_t& len) {
+  const uint32_t e0 = code_of(cb, w, 0), e1 = code_of(cb, w, 1);
+  const uint32_t e2 = code_of(cb, w, 2), e3 = code_of(cb, w, 3);
   const uint32_t l1 = e1 >> 16, l3 = e3 >> 16;
   const uint32_t p0 = ((e0 & 0xFFFFu) << l1) | (e1 & 0xFFFFu);   // <= 24 bits
   const uint32_t p1 = ((e2 & 0xFFFFu) << l3) | (e3 & 0xFFFFu);
@@ -816,9 +841,9 @@ __device__ __forceinline__ uint64_t join4(const uint32_t* codes, uint32_t w, uin
 }
 
 // Sum of the code lengths of the 4 bytes of w.
-__device__ __forceinline__ uint32_t len4(const uint32_t* codes, uint32_t w) {
-  return (codes[__byte_perm(w, 0, 0x4440)] >> 16) + (codes[__byte_perm(w, 0, 0x4441)] >> 16) +
-         (codes[__byte_perm(w, 0, 0x4442)] >> 16) + (codes[__byte_perm(w, 0, 0x4443)] >> 16);
+__device__ __forceinline__ uint32_t len4(uint32_t cb, uint32_t w) {
+  return (code_of(cb, w, 0) >> 16) + (code_of(cb, w, 1) >> 16) + (code_of(cb, w, 2) >> 16) +
+         (code_of(cb, w, 3) >> 16);
 }
 
 // Pass A for the dominant chunk layout: group 0 Huffman (slot-encoded), every
@@ -839,7 +864,7 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
   uint8_t* rawp[G];
 #pragma unroll
   for (int g = 0; g < G; g++) rawp[g] = out + P + S.off[g];
-  const uint32_t* codes0 = S.codes[0];
+  const uint32_t codes0 = smem_u32(S.codes[0]);
   auto ld = [&](uint64_t v) -> uint4 {
     uint4 a = __ldg(reinterpret_cast<const uint4*>(src) + v);
     if (base) {
@@ -851,7 +876,7 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T, ui = t * R + k;
     SlotWriter32 sw;
-    sw.slot = slots + (size_t)ui * slot_cap;
+    sw.slot = smem_u32(slots) + 4u * ui * slot_cap;
     sw.cur = 0;
     sw.nb = 0;
     sw.wi = 0;
@@ -1015,7 +1040,7 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 #pragma unroll
     for (int g = 0; g < G; g++) bits[g] = 0;
     SlotWriter sw;
-    sw.slot = slots + (size_t)(t * R + k) * slot_cap;
+    sw.slot = smem_u32(slots) + 4u * (t * R + k) * slot_cap;
     sw.acc = 0;
     sw.nacc = 0;
     sw.wi = 0;
@@ -1060,25 +1085,25 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 #pragma unroll
             for (int q = 0; q < V / 4; q++) {
               uint32_t len;
-              const uint64_t x = join4(S.codes[g], g4[g][q], len);
+              const uint64_t x = join4(smem_u32(S.codes[g]), g4[g][q], len);
               sw.put64(x, len);
             }
           } else {
 #pragma unroll
             for (int q = 0; q < V; q++)
               if (q < valid) {
-                const uint32_t cl = S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))];
+                const uint32_t cl = code_of(smem_u32(S.codes[g]), g4[g][q >> 2], q & 3);
                 sw.put(cl & 0xFFFFu, cl >> 16);
               }
           }
         } else if (huff >> g & 1) {
           if (full) {
 #pragma unroll
-            for (int q = 0; q < V / 4; q++) bits[g] += len4(S.codes[g], g4[g][q]);
+            for (int q = 0; q < V / 4; q++) bits[g] += len4(smem_u32(S.codes[g]), g4[g][q]);
           } else {
 #pragma unroll
             for (int q = 0; q < V; q++)
-              if (q < valid) bits[g] += S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))] >> 16;
+              if (q < valid) bits[g] += code_of(smem_u32(S.codes[g]), g4[g][q >> 2], q & 3) >> 16;
           }
         } else if (raw >> g & 1) {
           uint8_t* p = out + P + S.off[g] + v * V;
@@ -1151,14 +1176,14 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
         refill = true;  // slot overflowed: re-encode below from the input
       } else if (nbits) {
         uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[sg] + S.hsz[sg]);
-        const uint32_t* sl = slots + (size_t)ui * slot_cap;
+        const uint32_t sl = smem_u32(slots) + 4u * ui * slot_cap;
         const uint32_t o = S.part[sg][ui], sh = o & 31, w0 = o >> 5;
         const uint32_t end = o + nbits, wl = (end - 1) >> 5;
         const uint32_t nsw = (nbits + 31) >> 5;
         uint32_t prev = 0;
         for (uint32_t w = w0; w <= wl; w++) {
           const uint32_t i = w - w0;
-          const uint32_t cur = i < nsw ? sl[i] : 0u;
+          const uint32_t cur = i < nsw ? lds32v(sl + 4u * i) : 0u;
           const uint32_t word = __funnelshift_r(cur, prev, sh);
           prev = cur;
           if (w >= S.capw[sg]) break;  // never taken for a consistent input
@@ -1206,7 +1231,7 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 #pragma unroll
           for (int q = 0; q < V / 4; q++) {
             uint32_t len;
-            const uint64_t x = join4(S.codes[g], g4[g][q], len);
+            const uint64_t x = join4(smem_u32(S.codes[g]), g4[g][q], len);
             bw[g].put64(x, len);
           }
         } else {
@@ -1214,7 +1239,7 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 #pragma unroll
           for (int q = 0; q < V; q++)
             if (q < valid) {
-              const uint32_t cl = S.codes[g][__byte_perm(g4[g][q >> 2], 0, 0x4440 + (q & 3))];
+              const uint32_t cl = code_of(smem_u32(S.codes[g]), g4[g][q >> 2], q & 3);
               bw[g].put(cl & 0xFFFFu, cl >> 16);
             }
         }
@@ -1616,7 +1641,7 @@ cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64
   const bool skip = h_one ? h_one->skip != 0 : any_skip;
   // (a launch of empty tensors only has no chunk, hence no histogram area to
   // hold the single-pass kernel's ticket: the four-kernel path writes its headers)
-  if (encoder == 0 && nchunks_total > 0 && fused_encoder_applies(dt, skip))
+  if (encoder == 1 && nchunks_total > 0 && fused_encoder_applies(dt, skip))
     return launch_encode_fused(d_jobs, h_one, njobs, nchunks_total, s, d_err, st, dt,
                                debug_flags);
   cudaError_t e = launch_encode_analyse_ex(d_jobs, h_one, njobs, nchunks_total, ngc_total, s,

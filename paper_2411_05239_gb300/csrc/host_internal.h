@@ -34,10 +34,11 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
                                   cudaStream_t st, int uniform_dtype);
-// The whole encoder: the single-pass kernel (histogram, code build, offsets by
-// look-back, packing: one launch after a memset of its look-back words) when
-// every job is BF16, FP16 or U8 and none uses the skip-ahead probe and
-// encoder == 0, else the four kernels above.  Both write the same bytes.
+// The whole encoder: the four kernels above (encoder == 0), or the
+// single-pass kernel (histogram, code build, offsets by look-back, packing:
+// one launch after a memset of its look-back words) when encoder == 1 and
+// every job is BF16, FP16 or U8 and none uses the skip-ahead probe.  Both
+// write the same bytes.
 cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64_t nchunks_total,
                           uint64_t ngc_total, const EncodeScratch& s, uint32_t* d_err,
                           cudaStream_t st, int max_groups, int max_lanes, int uniform_dtype,
@@ -51,12 +52,14 @@ bool fused_encoder_applies(int dtype, bool any_skip);
 // the largest chunk (stage_frac64); has_delta: some job has a base; general:
 // use the general fast loops (two coded groups, SPARSE first groups) even
 // without a delta; stage_need: a stage size measured from the chunk maps (0 =
-// use frac64).
+// use frac64); common_lanes: the lanes of every job, or 0 if they differ (a
+// launch with few chunks may then split each chunk over several work items).
 cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
                              uint64_t nchunks_total, int max_groups, const zipnn_tuning* tuning,
                              uint32_t* d_err, unsigned long long* d_ticket, cudaStream_t st,
                              int uniform_dtype, uint64_t max_chunk, bool lanes256, int frac64,
-                             bool has_delta, bool general, uint32_t stage_need);
+                             bool has_delta, bool general, uint32_t stage_need,
+                             uint32_t common_lanes);
 
 // Sub-streams per group-chunk when a call gives none: chunk_bytes / 512 for
 // plain 16-bit containers (two sub-streams per thread of a 256-thread decoder

@@ -214,10 +214,13 @@ static zipnn_status plan_decode_range(const zipnn_stream* streams, const void* c
   memset(&tu, 0, sizeof(tu));
   if (tuning) tu = *tuning;
   const int uni = uniform < 0 ? -1 : uniform;
+  uint32_t common_lanes = jobs[0].lanes;
+  for (const Job& J : jobs)
+    if (J.lanes != common_lanes) common_lanes = 0;
   e = capture(p, [&](cudaStream_t cs) {
     return launch_decode_ex(d_jobs, nullptr, njobs, chunk, max_groups, &tu, err, ticket, cs, uni,
                             max_chunk, lanes256, frac64, has_delta, nd.general,
-                            planned_stage(nd));
+                            planned_stage(nd), common_lanes);
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
@@ -442,10 +445,13 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
       }
       if (r == cudaSuccess) r = cudaEventRecord(evs[(size_t)k], sc);
       if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);
+      uint32_t common_lanes = jobs[a].lanes;
+      for (int i = a; i < b; i++)
+        if (jobs[i].lanes != common_lanes) common_lanes = 0;
       if (r == cudaSuccess)
         r = launch_decode_ex(d_jobs + a, nullptr, b - a, nch, max_groups, &tu, err,
                              tickets + 2 * k, cs, uniform, max_chunk, lanes256, frac64,
-                             has_delta, nd.general, planned_stage(nd));
+                             has_delta, nd.general, planned_stage(nd), common_lanes);
     }
     // the last wait above joined the copy stream back into the capture stream
     return r;

@@ -219,11 +219,19 @@ void launch_batch(zipnn_server* s, int si, Batch* b) {
   int32_t rc = ZIPNN_OK;
   // the batch's kernels report into the slot's own error word
   set_thread_err_word(slot.d_err);
-  if (ncomp)
+  if (ncomp == 1 && dstr.empty()) {
+    // a batch of one request (the idle server's common case) takes the direct
+    // entry point: the job goes by value, no job table is uploaded
+    rc = zipnn_compress_into(csrc[0], cbase[0], cnb[0], cdt[0], chunk, 0, cout[0], ccap[0],
+                             s->arena_base + b->ws_off, b->ws_size, b->h_sizes, st);
+  } else if (ncomp) {
     rc = zipnn_batch_compress_into(csrc.data(), cbase.data(), cnb.data(), cdt.data(), (int)ncomp,
                                    chunk, 0, cout.data(), ccap.data(), s->arena_base + b->ws_off,
                                    b->ws_size, b->h_sizes, st);
-  if (rc == ZIPNN_OK && !dstr.empty())
+  }
+  if (rc == ZIPNN_OK && dstr.size() == 1 && ncomp == 0)
+    rc = zipnn_decompress(&dstr[0], dbase[0], ddst[0], dstr[0].orig_nbytes, st);
+  else if (rc == ZIPNN_OK && !dstr.empty())
     rc = zipnn_batch_decompress(dstr.data(), dbase.data(), ddst.data(), (int)dstr.size(), nullptr,
                                 st);
   set_thread_err_word(nullptr);

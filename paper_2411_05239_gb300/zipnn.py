@@ -59,7 +59,8 @@ class ZEncodeOptions(ctypes.Structure):
 
 class ZTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("lut_bits", ctypes.c_int32), ("debug_flags", ctypes.c_int32)]
+                ("lut_bits", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
+                ("parts", ctypes.c_int32)]
 
 
 _lib = None
@@ -308,8 +309,8 @@ def decompress(c: Compressed, out: torch.Tensor | None = None, base: torch.Tenso
 
 
 def tuning(threads: int = 0, ctas_per_sm: int = 0, lut_bits: int = 0,
-           debug_flags: int = 0) -> ZTuning:
-    return ZTuning(threads, ctas_per_sm, lut_bits, debug_flags)
+           debug_flags: int = 0, parts: int = 0) -> ZTuning:
+    return ZTuning(threads, ctas_per_sm, lut_bits, debug_flags, parts)
 
 
 def batch_decompress(cs: list[Compressed], outs: list[torch.Tensor],
@@ -345,8 +346,8 @@ class BatchCompressor:
     Arguments are marshalled once; each call() enqueues the four encoder
     kernels for all tensors (zipnn_batch_compress_into_ex).  probe_skip > 0
     applies the skip-ahead probe (Sec. 3.2): after a raw group-chunk the same
-    group of the next probe_skip chunks is stored raw.  encoder = 1 forces the
-    four-kernel encoder (0: the single-pass kernel where it applies)."""
+    group of the next probe_skip chunks is stored raw.  encoder = 1 selects
+    the single-pass encoder where it applies (0: the four kernels)."""
 
     def __init__(self, xs: list[torch.Tensor], chunk_bytes: int | None = None, lanes: int = 0,
                  bases: list[torch.Tensor | None] | None = None, probe_skip: int = 0,

@@ -1,7 +1,7 @@
 """The single-pass encoder (needs a GB300).
 
-Batches of one 16-bit dtype or U8 without the skip-ahead probe run one
-persistent kernel per launch: each chunk's histograms, codes, payload offset
+On request (encoder option 1), batches of one 16-bit dtype or U8 without the
+skip-ahead probe run one persistent kernel per launch: each chunk's histograms, codes, payload offset
 (decoupled look-back over the chunks before it in its tensor) and packing.
 Its containers must be byte-identical to the four-kernel encoder's and to the
 oracle's (ZipNN's container: Sec. 3.1, 3.2, 5.1), including across tensor
@@ -24,6 +24,9 @@ pytestmark = pytest.mark.gpu
 
 def u8(t: torch.Tensor) -> np.ndarray:
     return t.contiguous().view(-1).view(torch.uint8).cpu().numpy()
+
+
+FUSED, SPLIT = 1, 0   # encoder option values
 
 
 def _run(xs, chunk, encoder, bases=None, lanes=0):
@@ -51,8 +54,8 @@ def _batches():
 @pytest.mark.parametrize("chunk", [4096, 16384, 65536, 262144, 1 << 20])
 def test_single_pass_equals_four_kernels_and_oracle(chunk):
     for name, xs in _batches():
-        fused = _run(xs, chunk, 0)
-        split = _run(xs, chunk, 1)
+        fused = _run(xs, chunk, FUSED)
+        split = _run(xs, chunk, SPLIT)
         assert fused == split, name
         for x, got in zip(xs, fused):
             assert got == O.compress(u8(x), Z.dtype_code(x, None), chunk), (name, x.numel())
@@ -61,8 +64,8 @@ def test_single_pass_equals_four_kernels_and_oracle(chunk):
 @pytest.mark.parametrize("lanes", [1, 3, 100, 512, 1024])
 def test_single_pass_lane_counts(lanes):
     xs = [W.gaussian(n, 0.02, 300 + n, device="cuda") for n in (300_001, 131_072, 77)]
-    fused = _run(xs, 262144, 0, lanes=lanes)
-    assert fused == _run(xs, 262144, 1, lanes=lanes)
+    fused = _run(xs, 262144, FUSED, lanes=lanes)
+    assert fused == _run(xs, 262144, SPLIT, lanes=lanes)
     for x, got in zip(xs, fused):
         assert got == O.compress(u8(x), Z.BF16, 262144, lanes)
 
@@ -72,8 +75,8 @@ def test_single_pass_deltas_and_sparse_groups():
     other = W.gaussian(50_000, 0.02, 32, device="cuda")
     same = W.gaussian(70_000, 0.02, 33, device="cuda")
     xs, bases = [nxt, other, same], [base, None, same]
-    fused = _run(xs, 65536, 0, bases=bases)
-    assert fused == _run(xs, 65536, 1, bases=bases)
+    fused = _run(xs, 65536, FUSED, bases=bases)
+    assert fused == _run(xs, 65536, SPLIT, bases=bases)
     assert fused[0] == O.delta(u8(nxt), u8(base), Z.BF16, 65536)
     assert fused[1] == O.compress(u8(other), Z.BF16, 65536)
     assert fused[2] == O.delta(u8(same), u8(same), Z.BF16, 65536)   # all ZERO
@@ -85,8 +88,8 @@ def test_single_pass_many_tensors_one_launch():
     rng = np.random.default_rng(9)
     sizes = [int(v) for v in rng.integers(1, 200_000, size=300)]
     xs = [W.gaussian(n, 0.02, 400 + i, device="cuda") for i, n in enumerate(sizes)]
-    fused = _run(xs, 16384, 0)
-    split = _run(xs, 16384, 1)
+    fused = _run(xs, 16384, FUSED)
+    split = _run(xs, 16384, SPLIT)
     assert fused == split
     for i in list(range(0, 300, 37)) + [299]:
         assert fused[i] == O.compress(u8(xs[i]), Z.BF16, 16384)
@@ -103,12 +106,12 @@ def test_lookback_wait_gives_up_with_etimeout_and_context_survives():
     publishes its size, so its successors' bounded look-backs give up after
     100 ms (ETIMEOUT); the next call on the same buffers is exact."""
     xs = [W.gaussian(400_000, 0.02, 500, device="cuda"), W.gaussian(9000, 0.02, 501, device="cuda")]
-    bc = Z.BatchCompressor(xs, chunk_bytes=65536, debug_flags=1)
+    bc = Z.BatchCompressor(xs, chunk_bytes=65536, encoder=FUSED, debug_flags=1)
     bc()
     with pytest.raises(Z.ZipnnError) as e:
         Z.sync_status()
     assert e.value.status == -5
-    good = Z.BatchCompressor(xs, chunk_bytes=65536)
+    good = Z.BatchCompressor(xs, chunk_bytes=65536, encoder=FUSED)
     good()
     Z.sync_status()
     for x, c in zip(xs, good.containers()):

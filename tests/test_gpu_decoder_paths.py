@@ -253,3 +253,36 @@ def test_plans_size_their_stage_from_the_chunk_maps(which):
     p.close()
     for x, o in zip(xs, outs):
         assert np.array_equal(u8(o), u8(x))
+
+
+@pytest.mark.parametrize("parts", [0, 1, 2, 4])
+def test_chunks_split_over_work_items_decode_the_same(parts):
+    """Launches with few chunks split each model-weight chunk's sub-streams
+    over 2 or 4 work items (tuning.parts: 0 = automatic); chunks of other
+    layouts (ragged last chunk, FP32, lanes that do not split) are decoded
+    whole by their first part.  The decoded bytes never change."""
+    xs = [W.plain_bf16(device="cuda"),                                   # 32 full chunks
+          W.gaussian(300_001, 0.02, 81, device="cuda"),                  # ragged tail
+          W.gaussian(1 << 19, 0.02, 82, torch.float16, device="cuda"),
+          W.gaussian(700_000, 0.05, 83, torch.float32, device="cuda")]
+    for x in xs:
+        for lanes in (0, 256, 1024):
+            c = Z.compress(x, lanes=lanes)
+            out = torch.empty_like(x)
+            Z.batch_decompress([c], [out], tune=Z.tuning(parts=parts))
+            Z.sync_status()
+            assert torch.equal(out.view(torch.uint8), x.view(torch.uint8)), (x.dtype, lanes)
+            pd = Z.plan_decompress([c], [out], tune=Z.tuning(parts=parts))
+            for _ in range(2):
+                out.zero_()
+                pd.launch()
+                Z.sync_status()
+                assert torch.equal(out.view(torch.uint8), x.view(torch.uint8)), (x.dtype, lanes)
+            pd.close()
+    # a mixed-size batch: some chunks split, the ragged ones whole
+    cs = [Z.compress(x) for x in xs[:3]]
+    outs = [torch.empty_like(x) for x in xs[:3]]
+    Z.batch_decompress(cs, outs, tune=Z.tuning(parts=parts))
+    Z.sync_status()
+    for x, o in zip(xs, outs):
+        assert torch.equal(o.view(torch.uint8), x.view(torch.uint8))
