@@ -22,11 +22,9 @@
 //     sizing function as the workspace entry point, so the figure cannot
 //     drift from the layout);
 //   - all calls on a device share the array and it keeps the last call's
-//     contents.  The one part that must start at zero (the single-pass
-//     encoder's per-chunk offset words and work counter, at the front of the
-//     array) is cleared by each call itself, on its stream, before its
-//     kernel; every other scratch word a call reads was written earlier by
-//     the same call.  Two calls whose kernels
+//     contents.  Nothing in it has to start at zero: every scratch word a call
+//     reads was written earlier by the same call (it runs the four-kernel
+//     encoder).  Two calls whose kernels
 //     overlap on the GPU (e.g. on two streams without ordering) race on the
 //     array and produce garbage: order them on one stream or with events;
 //   - the first call on a device looks up the array's device address with
