@@ -51,7 +51,7 @@ def load_cache() -> dict:
 def save_cache(d: dict) -> None:
     p = cache_path()
     os.makedirs(os.path.dirname(p), exist_ok=True)
-    tmp = p + ".tmp"
+    tmp = f"{p}.{os.getpid()}.tmp"    # one writer per process (ranks may tune at once)
     with open(tmp, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)
     os.replace(tmp, p)
