@@ -25,6 +25,7 @@ import json
 import math
 import os
 import statistics
+import struct
 import subprocess
 import sys
 import threading
@@ -279,6 +280,8 @@ def run_gb300(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     hbm_peak, peak_kind = peaks()
+    if args.split:      # whole-tensor comparisons and the load path do not apply to a range
+        args.per_tensor, args.e2e_steps = 0, 0
 
     specs = W.llama8b_specs(n_layers=args.layers, vocab=args.vocab)
     ts = W.checkpoint_bf16(specs, seed=2, device=dev)
@@ -320,17 +323,54 @@ def run_gb300(args):
     tune = None if args.autotune else Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm,
                                                lut_bits=args.lut_bits)
     comp_plan = Z.plan_compress(bc)
-    dec_plan = Z.plan_decompress(cs, outs, tune=tune)
     if tune is None:
+        # the decode plan below takes the cached setting itself; this copy of it
+        # serves the other decoder launches (range plan, load plan)
         tune = Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm, lut_bits=args.lut_bits)
+    split = None
+    if args.split:
+        # sharded decode of ONE checkpoint (strong scaling): every rank holds the
+        # containers of all tensors (compressed identically on every rank) and
+        # decodes only its range of chunks, cut from the chunk maps by
+        # zipnn_partition_chunks into buffers of just its extents
+        zss = [c.zs for c in cs]
+        maps = [c.device_tensor()[:64 + 16 * c.zs.n_chunks * c.zs.n_groups].cpu() for c in cs]
+        bounds = Z.partition_chunks(zss, maps, world)
+        lo, hi = bounds[rank], bounds[rank + 1]
+        ext = Z.range_extents(zss, lo, hi)
+        outs = [torch.empty(e[2], dtype=torch.uint8, device=dev) if e else None for e in ext]
+        dec_plan = Z.plan_decompress_range(cs, outs, lo, hi, tune=tune)
+        orig_r = sum(e[2] for e in ext if e)
+        comp_r = 0                              # stored payload bytes of the range
+        for i, e in enumerate(ext):
+            if e is None:
+                continue
+            G = zss[i].n_groups
+            ent = maps[i].numpy().tobytes()
+            for ch in range(e[0], e[0] + -(-e[2] // zss[i].chunk_bytes)):
+                for g in range(G):
+                    size, mode = struct.unpack_from("<IB", ent, 64 + 16 * (ch * G + g) + 8)
+                    if mode in (0, 1, 4):       # raw, Huffman, sparse payloads
+                        comp_r += (size + 15) // 16 * 16
+        split = {"rank_bounds": bounds, "chunks": hi - lo, "orig_bytes": orig_r,
+                 "payload_bytes": comp_r}
+    elif args.autotune:
+        dec_plan = Z.plan_decompress(cs, outs)            # the cached decoder setting
+    else:
+        dec_plan = Z.plan_decompress(cs, outs, tune=tune)
 
     # correctness gate before timing (bit-exact round trip on the device)
     comp_plan.launch()
     dec_plan.launch()
     Z.sync_status()
-    for t, o in zip(ts, outs):
-        if not torch.equal(t.view(torch.int16), o.view(torch.int16)):
-            raise SystemExit("round trip mismatch: refusing to report a number")
+    if split is None:
+        for t, o in zip(ts, outs):
+            if not torch.equal(t.view(torch.int16), o.view(torch.int16)):
+                raise SystemExit("round trip mismatch: refusing to report a number")
+    else:
+        for t, o, e in zip(ts, outs, ext):
+            if e is not None and not torch.equal(t.view(torch.uint8)[e[1]:e[1] + e[2]], o):
+                raise SystemExit("range decode mismatch: refusing to report a number")
 
     stream = torch.cuda.current_stream()
     K, Wm = args.steps, args.warmup
@@ -474,15 +514,21 @@ def run_gb300(args):
                  "compress_gbs": rn["compress_gbs"], "sample": "the same sample, sliced"}
 
     dec_s, comp_s = md / 1e3, mc / 1e3
-    value = world * orig / dec_s / 1e9
+    # replicas: every rank decodes its own checkpoint (weak scaling); split: the
+    # ranks share one checkpoint, each decoding its range (strong scaling;
+    # md is already the slowest rank's time)
+    value = (orig if split else world * orig) / dec_s / 1e9
     alg_dec = comp_bytes + orig                 # compressed bytes read + original written
+    if split:
+        alg_dec = split["payload_bytes"] + split["orig_bytes"]   # this rank's range
     alg_comp = orig + comp_bytes                # original read + compressed written
-    traffic = traffic_from_profile(orig)
+    traffic = traffic_from_profile(split["orig_bytes"] if split else orig)
     srt = sorted(dec_ms)
     p = lambda q: srt[min(len(srt) - 1, int(math.ceil(q * len(srt))) - 1)]
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
-        "warmup": Wm, "ms_per_step": mspan / K, "higher_is_better": True, "scaling": "weak",
+        "warmup": Wm, "ms_per_step": mspan / K, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded N(0, 0.02/sqrt(2l+1)) BF16 weights, Llama-3.1-8B shapes)",
         "config": {"workload": ("llama8b_bf16_checkpoint" if (args.layers, args.vocab) == (32, 128256)
@@ -497,8 +543,11 @@ def run_gb300(args):
                                  "candidates": tuned.get("candidates"),
                                  "from_cache": tuned.get("from_cache"),
                                  "sample_decode_gbs": tuned.get("decode_gbs")}),
+                   "parallelism": (f"split{world}: one checkpoint, chunk ranges per rank"
+                                   if split else f"replicas{world}"),
                    "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
                    "form": "batched: 1 graph launch compress + 1 graph launch persistent decode"},
+        "split": split,
         "decompress_gbs": value, "compress_gbs": world * orig / comp_s / 1e9,
         "ratio": comp_bytes / orig,
         "decompress_ms": {"mean": md, "p50": p(0.5), "p99": p(0.99)},
@@ -1041,6 +1090,9 @@ def main(argv=None):
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="request arrivals per second (the served-stream workload: 200)")
     ap.add_argument("--ref-sample-mb", type=int, default=48)
+    ap.add_argument("--split", type=int, default=0,
+                    help="ranks decode disjoint chunk ranges of one checkpoint (strong scaling) "
+                         "instead of each its own checkpoint")
     ap.add_argument("--configs", type=int, default=1,
                     help="also measure the checkpoint delta and a shortened served stream")
     ap.add_argument("--configs-serve-requests", type=int, default=400,

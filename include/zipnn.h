@@ -96,9 +96,9 @@ typedef struct zipnn_tuning {
                              reports ZIPNN_ETIMEOUT via zipnn_sync_status */
     int32_t parts;        /* work items per chunk: 0 = automatic (launches whose
                              chunks would fill at most half the SMs split each
-                             model-weight chunk's sub-streams over 2 or 4 work
-                             items of 128-thread CTAs), 1 = never split, 2 or
-                             4 = split whenever the lanes allow */
+                             model-weight chunk's sub-streams over 2, 4 or 8
+                             work items of 128-thread CTAs), 1 = never split,
+                             2, 4 or 8 = split whenever the lanes allow */
 } zipnn_tuning;
 
 /* Library version (the container version is 1). */

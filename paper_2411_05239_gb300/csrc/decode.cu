@@ -80,12 +80,13 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   // Launches with few chunks (no more than half as many as SMs) split every
   // chunk of the model-weight layout over `parts` work items -- disjoint
   // sub-stream ranges, each a whole number of rounds of a 128-thread CTA --
-  // so that more SMs work on them (tuning->parts: 0 = this rule, 1 = never,
-  // 2 or 4 = whenever the lanes allow)
+  // so that more SMs work on them: the most parts (8, 4 or 2) that the lanes
+  // allow and that keep the work items within two per SM (tuning->parts: 0 =
+  // this rule, 1 = never, 2, 4 or 8 = whenever the lanes allow)
   uint32_t parts = 1;
   const int want_parts = tuning ? tuning->parts : 0;
   if (!gen && w >= 11 && uniform_dtype >= 0 && common_lanes && want_parts != 1) {
-    for (uint32_t p = 4; p >= 2; p /= 2) {
+    for (uint32_t p = 8; p >= 2; p /= 2) {
       if (common_lanes % (p * (uint32_t)kDecThreads) != 0) continue;
       if (want_parts == 0 && nchunks_total * 2 > (uint64_t)sms) break;
       if (want_parts == 0 && nchunks_total * p > 2ull * (uint64_t)sms) continue;

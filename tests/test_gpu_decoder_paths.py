@@ -255,10 +255,10 @@ def test_plans_size_their_stage_from_the_chunk_maps(which):
         assert np.array_equal(u8(o), u8(x))
 
 
-@pytest.mark.parametrize("parts", [0, 1, 2, 4])
+@pytest.mark.parametrize("parts", [0, 1, 2, 4, 8])
 def test_chunks_split_over_work_items_decode_the_same(parts):
     """Launches with few chunks split each model-weight chunk's sub-streams
-    over 2 or 4 work items (tuning.parts: 0 = automatic); chunks of other
+    over 2, 4 or 8 work items (tuning.parts: 0 = automatic); chunks of other
     layouts (ragged last chunk, FP32, lanes that do not split) are decoded
     whole by their first part.  The decoded bytes never change."""
     xs = [W.plain_bf16(device="cuda"),                                   # 32 full chunks
