@@ -865,10 +865,12 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
 #pragma unroll
   for (int g = 0; g < G; g++) rawp[g] = out + P + S.off[g];
   const uint32_t codes0 = smem_u32(S.codes[0]);
-  auto ld = [&](uint64_t v) -> uint4 {
-    uint4 a = __ldg(reinterpret_cast<const uint4*>(src) + v);
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  const uint4* b4 = reinterpret_cast<const uint4*>(base);
+  auto ld = [&](uint32_t v) -> uint4 {
+    uint4 a = __ldg(s4 + v);
     if (base) {
-      const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + v);
+      const uint4 b = __ldg(b4 + v);
       a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
     }
     return a;
@@ -882,28 +884,26 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
     sw.wi = 0;
     sw.cap = slot_cap;
     sw.bits = 0;
-    uint64_t v = t + (uint64_t)k * per * T;
-    constexpr uint32_t D = 2;  // vectors in flight per thread (L2 prefetches run further ahead)
-    // the unit's first vectors, up to where the in-loop prefetches start
+    uint32_t v = t + k * per * T;
+    constexpr uint32_t D = 2;
     for (uint32_t i = D; i < kPrefetchAhead && i < per; i++) {
-      prefetch_l2(reinterpret_cast<const uint4*>(src) + v + (uint64_t)i * T);
-      if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + v + (uint64_t)i * T);
+      prefetch_l2(s4 + v + i * T);
+      if (base) prefetch_l2(b4 + v + i * T);
     }
     uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
     auto one = [&](uint4& a, uint32_t i) {
       uint32_t g4[4][4];
       split_vec(DT, a, g4);
-      if (i + D < per) a = ld(v + (uint64_t)D * T);
+      if (i + D < per) a = ld(v + D * T);
       if (i + kPrefetchAhead < per) {
-        prefetch_l2(reinterpret_cast<const uint4*>(src) + v + (uint64_t)kPrefetchAhead * T);
-        if (base) prefetch_l2(reinterpret_cast<const uint4*>(base) + v + (uint64_t)kPrefetchAhead * T);
+        prefetch_l2(s4 + v + kPrefetchAhead * T);
+        if (base) prefetch_l2(b4 + v + kPrefetchAhead * T);
       }
       if constexpr (V / 4 == 1) {
         uint32_t len;
         const uint64_t x = join4(codes0, g4[0][0], len);
         sw.put48(x, len);
       } else {
-        // two joined quads at a time: one append when they fit in 32 bits
 #pragma unroll
         for (int q = 0; q < V / 4; q += 2) {
           uint32_t l0, l1;
@@ -920,9 +920,8 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
 #pragma unroll
       for (int g = 1; g < G; g++) {
         if (!(raw >> g & 1u)) continue;
-        uint8_t* p = rawp[g] + v * V;
-        if (V == 8) *reinterpret_cast<uint2*>(p) = make_uint2(g4[g][0], g4[g][1]);
-        else *reinterpret_cast<uint32_t*>(p) = g4[g][0];
+        if (V == 8) reinterpret_cast<uint2*>(rawp[g])[v] = make_uint2(g4[g][0], g4[g][1]);
+        else reinterpret_cast<uint32_t*>(rawp[g])[v] = g4[g][0];
       }
       v += T;
     };
