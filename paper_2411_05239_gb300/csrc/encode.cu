@@ -689,6 +689,8 @@ struct PackSmem {
   uint32_t capw[4];   // bitstream words available in the payload
   uint32_t hsz[4];    // table + start-offset bytes before the bitstream
   uint32_t sbits[kPackMaxUnits];  // bits of each unit of the slot-staged group
+  uint32_t ptab[1024];  // pair table of the 16-bit pass A (pack_pair_a)
+  uint32_t rsym[32];    // its symbol of each residue mod 32 (kNoSym: none, kClash: several)
 };
 
 // Exclusive scan of a[0..n) in place (block-wide); n <= kPackMaxUnits.
@@ -935,6 +937,162 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
   }
 }
 
+// Pass A for the same layout in 16-bit chunks whose exponent code gives its
+// symbols distinct residues mod 32 (nearly every chunk of a model: the
+// exponents of one chunk span fewer than 32 values).  Entry a + 32 b of the
+// pair table holds the codes of the symbols with residues a and b joined
+// MSB-first, as (joined code << 6) | joined length (<= 24 bits, <= 24).  An
+// element pair x (one 32-bit word, first element in the low half) finds its
+// entry without splitting bytes: the residues sit at bits 7-11 and 23-27, and
+// (x & 0x0F800F80) * 0x801 places them side by side at bits 18-27, so the
+// product's upper half is the entry's byte offset (plus the table's address,
+// added in the same multiply-add).  Two entries (four symbols, <= 32 bits in
+// all but rare cases) are joined in one register and appended to the unit's
+// slot through a 64-bit accumulator that emits at most one word per append.
+// Same slot words, bit counts and overflow rule as pack_fast_a.
+constexpr uint32_t kNoSym = 0x100, kClash = 0x200;
+
+// Builds S.ptab from S.codes[0] (all threads; ends past a barrier); false
+// when two symbols of the code share a residue (S.ptab unused).
+__device__ bool build_pair_table(PackSmem& S) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  bool ok = true;
+  if (tid < 32) {
+    uint32_t sym = kNoSym;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t s = (uint32_t)tid + 32u * k;
+      if (S.codes[0][s] >> 16) sym = sym == kNoSym ? s : kClash;
+    }
+    S.rsym[tid] = sym;
+    ok = sym != kClash;
+  }
+  if (!__syncthreads_and(ok)) return false;
+  for (int i = tid; i < 1024; i += nthr) {
+    const uint32_t sa = S.rsym[i & 31], sb = S.rsym[i >> 5];
+    uint32_t e = 0;
+    if (sa < 256 && sb < 256) {
+      const uint32_t ca = S.codes[0][sa], cb = S.codes[0][sb];
+      const uint32_t lb = cb >> 16;
+      e = ((((ca & 0xFFFFu) << lb) | (cb & 0xFFFFu)) << 6) | ((ca >> 16) + lb);
+    }
+    S.ptab[i] = e;
+  }
+  __syncthreads();
+  return true;
+}
+
+// One unit of pack_pair_a: vectors v, v + T, ... (per of them) from s4
+// (XOR b4 when XB), its fraction bytes to rawp when RW; bits into the slot
+// at shared address sa0 whose last word is at slast; returns the unit's bits.
+// Branch-free appends: every append stores a word at the slot's next free
+// word (the finished word when 32 bits are complete, else one that a later
+// store overwrites or that lies past the unit's bits); a unit that runs past
+// its slot is re-encoded from the input, so the clamped stores there are
+// never read.
+template <bool XB, bool RW>
+__device__ __forceinline__ uint32_t pair_unit(const uint4* __restrict__ s4,
+                                       const uint4* __restrict__ b4, uint2* rawp,
+                                       uint32_t v, uint32_t T, uint32_t per, uint32_t pb16,
+                                       uint32_t sa0, uint32_t slast) {
+  uint32_t sa = sa0, lo = 0, hi = 0, nb = 0;  // pending bits: the low nb of hi:lo
+  auto ld = [&](uint32_t w) -> uint4 {
+    uint4 a = __ldg(s4 + w);
+    if (XB) {
+      const uint4 b = __ldg(b4 + w);
+      a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+    }
+    return a;
+  };
+  auto pf = [&](uint32_t w) {
+    prefetch_l2(s4 + w);
+    if (XB) prefetch_l2(b4 + w);
+  };
+  auto entry = [&](uint32_t x) -> uint32_t {
+    return lds32(((x & 0x0F800F80u) * 0x801u + pb16) >> 16);
+  };
+  // sign + fraction bytes of the two elements of x at bytes 0 and 2
+  auto frac2 = [](uint32_t x) -> uint32_t {
+    return (x & 0x007F007Fu) | ((x >> 8) & 0x00800080u);
+  };
+  // append the L (0..32) bits of V
+  auto put = [&](uint32_t V, uint32_t L) {
+    hi = __funnelshift_lc(lo, hi, L);
+    lo = __funnelshift_lc(0u, lo, L) | V;
+    nb += L;
+    sts32(min(sa, slast), __funnelshift_r(lo, hi, nb - 32u));  // the word if nb >= 32
+    const bool full = nb >= 32;
+    sa += full ? 4u : 0u;
+    nb -= full ? 32u : 0u;
+  };
+  // four symbols: the entries of two element pairs
+  auto quad = [&](uint32_t E0, uint32_t E1) {
+    const uint32_t L = (E0 + E1) & 63u;
+    if (L <= 32) {
+      put(__funnelshift_l(0u, E0 >> 6, E1) | (E1 >> 6), L);
+    } else {
+      put(E0 >> 6, E0 & 63u);
+      put(E1 >> 6, E1 & 63u);
+    }
+  };
+  // one vector (a); then a <- the vector two ahead (LD) and an L2 prefetch of
+  // the one kPrefetchAhead ahead (PF)
+  auto one = [&](uint4& a, bool LD, bool PF) {
+    const uint4 x = a;
+    if (LD) a = ld(v + 2 * T);
+    if (PF) pf(v + kPrefetchAhead * T);
+    const uint32_t E0 = entry(x.x), E1 = entry(x.y), E2 = entry(x.z), E3 = entry(x.w);
+    if (RW)
+      rawp[v] = make_uint2(__byte_perm(frac2(x.x), frac2(x.y), 0x6420),
+                           __byte_perm(frac2(x.z), frac2(x.w), 0x6420));
+    quad(E0, E1);
+    quad(E2, E3);
+    v += T;
+  };
+  for (uint32_t i = 2; i < kPrefetchAhead && i < per; i++) pf(v + i * T);
+  uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
+  uint32_t i = 0;
+  for (; i + kPrefetchAhead + 1 < per; i += 2) {
+    one(a0, true, true);
+    one(a1, true, true);
+  }
+  for (; i < per; i += 2) {
+    one(a0, i + 2 < per, i + kPrefetchAhead < per);
+    if (i + 1 < per) one(a1, i + 3 < per, i + 1 + kPrefetchAhead < per);
+  }
+  if (nb) sts32(min(sa, slast), lo << (32 - nb));
+  return (sa - sa0) * 8u + nb;
+}
+
+template <int DT>
+__device__ __forceinline__ void pack_pair_a(const uint8_t* src, const uint8_t* base, uint32_t T,
+                                            uint32_t R, uint32_t per, uint32_t* slots,
+                                            uint32_t slot_cap, PackSmem& S, uint8_t* out,
+                                            uint64_t P, uint32_t raw) {
+  static_assert(DT == ZIPNN_BF16 || DT == ZIPNN_FP16, "16-bit chunks only");
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t units = T * R;
+  uint2* const rawp = reinterpret_cast<uint2*>(out + P + S.off[1]);
+  const bool rw = (raw >> 1 & 1u) != 0;
+  const uint32_t pb16 = smem_u32(S.ptab) << 16;  // table address < 61440 (checked by the caller)
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  const uint4* b4 = reinterpret_cast<const uint4*>(base);
+  for (uint32_t u = tid; u < units; u += nthr) {
+    const uint32_t t = u % T, k = u / T, ui = t * R + k;
+    const uint32_t sa0 = smem_u32(slots) + 4u * ui * slot_cap, slast = sa0 + 4u * (slot_cap - 1);
+    const uint32_t v = t + k * per * T;
+    uint32_t bits;
+    if (base)
+      bits = rw ? pair_unit<true, true>(s4, b4, rawp, v, T, per, pb16, sa0, slast)
+                : pair_unit<true, false>(s4, b4, rawp, v, T, per, pb16, sa0, slast);
+    else
+      bits = rw ? pair_unit<false, true>(s4, b4, rawp, v, T, per, pb16, sa0, slast)
+                : pair_unit<false, false>(s4, b4, rawp, v, T, per, pb16, sa0, slast);
+    S.sbits[ui] = bits;
+    S.part[0][ui] = bits;
+  }
+}
+
 // Map entries of chunk c (threads 0..G-1) from S.meta and S.off.
 template <int G>
 __device__ __forceinline__ void write_map_entries(const Job& J, uint64_t c, const PackSmem& S) {
@@ -1031,8 +1189,17 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   // pass A: unit bits (+ raw planes, + slot encoding of group sg)
   const bool fast_a = sg == 0 && huff == 1u && sparse == 0 && nb == J.chunk_bytes &&
                       nvec % T == 0 && nvt % R == 0 && T <= (uint32_t)nthr;
-  if (fast_a)
-    pack_fast_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+  if (fast_a) {
+    bool pairs = false;
+    if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16)
+      pairs = smem_u32(S.ptab) + 4096u <= 65536u && build_pair_table(S);
+    if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
+      if (pairs)
+        pack_pair_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+    }
+    if (!pairs)
+      pack_fast_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+  }
   for (uint32_t u = fast_a ? units : tid; u < units; u += nthr) {
     const uint32_t t = u % T, k = u / T;
     uint32_t bits[G];
@@ -1137,7 +1304,15 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     for (uint64_t q = m + tid; q < align_up(m, 16); q += nthr) p[q] = 0;
   }
   if (!huff) return;
-  __syncthreads();
+  // Pass B writes each output word of the slot-staged group whole (no zeroed
+  // words, no atomics) when that group is the only coded one and every unit
+  // holds 32 to slot_cap * 32 bits (so a word spans at most two units)
+  bool whole = sg == 0 && huff == 1u;
+  for (uint32_t u = tid; whole && u < units; u += nthr) {
+    const uint32_t b = S.sbits[(u % T) * R + u / T];
+    whole = b >= 32u && b <= slot_cap * 32u;
+  }
+  whole = __syncthreads_and(whole) != 0;
 
   // scan unit bits -> unit offsets; table bytes, sub-stream starts, zeroed words
 #pragma unroll
@@ -1155,13 +1330,41 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     uint32_t* words = po + (T - 1);
     const uint32_t capw =
         (uint32_t)(align_up(S.meta[g].size, 16) - h - 4ull * nbm - 4ull * (T - 1)) / 4;
-    for (uint32_t w = tid; w < capw; w += nthr) words[w] = 0;
+    if (!whole)
+      for (uint32_t w = tid; w < capw; w += nthr) words[w] = 0;
     if (tid == 0) {
       S.capw[g] = capw;
       S.hsz[g] = h + 4 * nbm + 4 * (T - 1);
     }
   }
   __syncthreads();
+
+  if (whole) {
+    // pass B, whole words: word w (bits 32w .. 32w + 31 of the group's
+    // bitstream) belongs to the unit holding bit 32w; a warp writes one
+    // unit's words at a time (contiguous stores), the last one completed by
+    // the next unit's first bits
+    uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[0] + S.hsz[0]);
+    const int lane = tid & 31, nwarps = nthr >> 5;
+    const uint32_t sl0 = smem_u32(slots);
+    for (uint32_t ui = (uint32_t)(tid >> 5); ui < units; ui += (uint32_t)nwarps) {
+      const uint32_t o = S.part[0][ui], nbits = S.sbits[ui], e = o + nbits;
+      const uint32_t nsw = (nbits + 31) >> 5, sl = sl0 + 4u * ui * slot_cap;
+      const uint32_t nxt = ui + 1 < units ? lds32v(sl0 + 4u * (ui + 1) * slot_cap) : 0u;
+      for (uint32_t w = ((o + 31) >> 5) + lane; w <= (e - 1) >> 5; w += 32) {
+        const uint32_t kb = 32u * w - o, i = kb >> 5, r = e - 32u * w;
+        const uint32_t a = lds32v(sl + 4u * i);
+        const uint32_t b = i + 1 < nsw ? lds32v(sl + 4u * (i + 1)) : 0u;
+        uint32_t x = __funnelshift_l(b, a, kb & 31);
+        if (r < 32) x |= nxt >> r;
+        words[w] = x;
+      }
+    }
+    // the payload's padding words after the bitstream
+    const uint32_t tot = S.part[0][units - 1] + S.sbits[units - 1];
+    for (uint32_t w = ((tot + 31) >> 5) + tid; w < S.capw[0]; w += nthr) words[w] = 0;
+    return;
+  }
 
   // pass B
   for (uint32_t u = tid; u < units; u += nthr) {
