@@ -311,9 +311,9 @@ def run_gb300(args):
         torch.cuda.synchronize()
     # compression plan (batched, graph-captured) and a first pass for the sizes
     if args.autotune:
-        bc = Z.BatchCompressor(ts)                        # the cached setting
+        bc = Z.BatchCompressor(ts, encoder=args.encoder)  # the cached setting
     else:
-        bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk, lanes=lanes)
+        bc = Z.BatchCompressor(ts, chunk_bytes=args.chunk, lanes=lanes, encoder=args.encoder)
     bc()
     Z.sync_status()
     cs = bc.containers()
@@ -322,7 +322,16 @@ def run_gb300(args):
     outs = [torch.empty_like(t) for t in ts]
     tune = None if args.autotune else Z.tuning(threads=args.threads, ctas_per_sm=args.ctas_per_sm,
                                                lut_bits=args.lut_bits)
-    comp_plan = Z.plan_compress(bc)
+    # plans capture the four-kernel encoder; the single-pass one (--encoder 1)
+    # runs as a direct batched call
+    comp_plan = Z.plan_compress(bc) if not args.encoder else None
+
+    def compress(s=None):
+        if comp_plan is not None:
+            comp_plan.launch(s)
+        else:
+            bc(s)
+
     if tune is None:
         # the decode plan below takes the cached setting itself; this copy of it
         # serves the other decoder launches (range plan, load plan)
@@ -360,7 +369,7 @@ def run_gb300(args):
         dec_plan = Z.plan_decompress(cs, outs, tune=tune)
 
     # correctness gate before timing (bit-exact round trip on the device)
-    comp_plan.launch()
+    compress()
     dec_plan.launch()
     Z.sync_status()
     if split is None:
@@ -379,7 +388,7 @@ def run_gb300(args):
     def step(e=None):
         if e:
             e[0].record(stream)
-        comp_plan.launch(stream)
+        compress(stream)
         if e:
             e[1].record(stream)
         dec_plan.launch(stream)
@@ -546,7 +555,10 @@ def run_gb300(args):
                    "parallelism": (f"split{world}: one checkpoint, chunk ranges per rank"
                                    if split else f"replicas{world}"),
                    "l2": f"inputs ({orig / 1e9:.2f} GB) larger than L2 (129 MB); no flush",
-                   "form": "batched: 1 graph launch compress + 1 graph launch persistent decode"},
+                   "form": ("batched: 1 graph launch compress + 1 graph launch persistent decode"
+                            if comp_plan is not None else
+                            "batched: 1 single-pass compress call + 1 graph launch persistent "
+                            "decode")},
         "split": split,
         "decompress_gbs": value, "compress_gbs": world * orig / comp_s / 1e9,
         "ratio": comp_bytes / orig,

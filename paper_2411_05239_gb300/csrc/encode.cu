@@ -690,7 +690,6 @@ struct PackSmem {
   uint32_t hsz[4];    // table + start-offset bytes before the bitstream
   uint32_t sbits[kPackMaxUnits];  // bits of each unit of the slot-staged group
   uint32_t ptab[1024];  // pair table of the 16-bit pass A (pack_pair_a)
-  uint32_t rsym[32];    // its symbol of each residue mod 32 (kNoSym: none, kClash: several)
 };
 
 // Exclusive scan of a[0..n) in place (block-wide); n <= kPackMaxUnits.
@@ -952,24 +951,23 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
 // Same slot words, bit counts and overflow rule as pack_fast_a.
 constexpr uint32_t kNoSym = 0x100, kClash = 0x200;
 
-// Builds S.ptab from S.codes[0] (all threads; ends past a barrier); false
-// when two symbols of the code share a residue (S.ptab unused).
+// Builds S.ptab from S.codes[0] (all threads, S.codes[0] visible; no
+// barrier: the caller's next one publishes the table); false when two
+// symbols of the code share a residue (S.ptab unused).  Every warp finds the
+// symbol of each residue itself (lane r: residue r), so the check needs no
+// shared state.
 __device__ bool build_pair_table(PackSmem& S) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  bool ok = true;
-  if (tid < 32) {
-    uint32_t sym = kNoSym;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  uint32_t sym = kNoSym;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const uint32_t s = (uint32_t)tid + 32u * k;
-      if (S.codes[0][s] >> 16) sym = sym == kNoSym ? s : kClash;
-    }
-    S.rsym[tid] = sym;
-    ok = sym != kClash;
+  for (int k = 0; k < 8; k++) {
+    const uint32_t sy = (uint32_t)lane + 32u * k;
+    if (S.codes[0][sy] >> 16) sym = sym == kNoSym ? sy : kClash;
   }
-  if (!__syncthreads_and(ok)) return false;
-  for (int i = tid; i < 1024; i += nthr) {
-    const uint32_t sa = S.rsym[i & 31], sb = S.rsym[i >> 5];
+  if (__any_sync(0xffffffffu, sym == kClash)) return false;
+  for (int i = tid; i < 1024; i += nthr) {  // warp-uniform trip count
+    const uint32_t sa = __shfl_sync(0xffffffffu, sym, i & 31);
+    const uint32_t sb = __shfl_sync(0xffffffffu, sym, i >> 5);
     uint32_t e = 0;
     if (sa < 256 && sb < 256) {
       const uint32_t ca = S.codes[0][sa], cb = S.codes[0][sb];
@@ -978,7 +976,6 @@ __device__ bool build_pair_table(PackSmem& S) {
     }
     S.ptab[i] = e;
   }
-  __syncthreads();
   return true;
 }
 
@@ -1126,16 +1123,46 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     S.meta[tid] = meta[gc0 + tid];
     S.off[tid] = offs[gc0 + tid];
   }
+  // group 0's code (coded in nearly every chunk) in the same round trip
+  for (int s = tid; s < 256; s += nthr) S.codes[0][s] = codes[gc0 * 256 + s];
   __syncthreads();
   write_map_entries<G>(J, c, S);
 #pragma unroll
-  for (int g = 0; g < G; g++)
+  for (int g = 1; g < G; g++)
     if (S.meta[g].mode == kHuff || S.meta[g].mode == kSparse)
       for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
   const uint8_t* tabp[4] = {nullptr, nullptr, nullptr, nullptr};
 #pragma unroll
   for (int g = 0; g < G; g++) tabp[g] = tabs + (gc0 + g) * kTabBytes;
   pack_chunk_core<DT>(J, c, S, slots, tabp);
+}
+
+// Pass B of a chunk whose group 0 is its only coded group and whose units
+// (offsets in S.part[0], bits in S.sbits) hold 32 to slot_cap * 32 bits
+// each: word w (bits 32w .. 32w + 31 of the bitstream, tot bits, capw words
+// of payload at words) belongs to the unit holding bit 32w, so each word is
+// written whole (no zeroed words, no atomics) from at most two units' slots;
+// a warp writes one unit's words at a time (contiguous stores), the last one
+// completed by the next unit's first bits.  Then the padding words.
+__device__ __forceinline__ void pass_b_whole(const PackSmem& S, const uint32_t* slots,
+                                             uint32_t slot_cap, uint32_t units, uint32_t* words,
+                                             uint32_t capw, uint32_t tot) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, nwarps = nthr >> 5;
+  const uint32_t sl0 = smem_u32(slots);
+  for (uint32_t ui = (uint32_t)(tid >> 5); ui < units; ui += (uint32_t)nwarps) {
+    const uint32_t o = S.part[0][ui], nbits = S.sbits[ui], e = o + nbits;
+    const uint32_t nsw = (nbits + 31) >> 5, sl = sl0 + 4u * ui * slot_cap;
+    const uint32_t nxt = ui + 1 < units ? lds32v(sl0 + 4u * (ui + 1) * slot_cap) : 0u;
+    for (uint32_t w = ((o + 31) >> 5) + lane; w <= (e - 1) >> 5; w += 32) {
+      const uint32_t kb = 32u * w - o, i = kb >> 5, r = e - 32u * w;
+      const uint32_t a = lds32v(sl + 4u * i);
+      const uint32_t b = i + 1 < nsw ? lds32v(sl + 4u * (i + 1)) : 0u;
+      uint32_t x = __funnelshift_l(b, a, kb & 31);
+      if (r < 32) x |= nxt >> r;
+      words[w] = x;
+    }
+  }
+  for (uint32_t w = ((tot + 31) >> 5) + tid; w < capw; w += nthr) words[w] = 0;
 }
 
 template <int DT>
@@ -1174,7 +1201,14 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
                                             align_up(12 + S.meta[g].nz, 4));
       for (uint32_t w = tid; w < bmw; w += nthr) bmap[g][w] = 0;
     }
-  __syncthreads();
+  // table bytes of the coded groups (counts per length, symbols)
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if (!(huff >> g & 1)) continue;
+    uint8_t* p = out + P + S.off[g];
+    const uint32_t nz = S.meta[g].nz, h = (uint32_t)align_up(12 + nz, 4);
+    for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tabp[g][i] : 0;
+  }
 
   // The first Huffman group is encoded once, in pass A, into per-unit slots in
   // shared memory (slot_cap words each, odd so that neighbouring slots fall in
@@ -1185,14 +1219,15 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     if (huff >> g & 1) sg = g;
   uint32_t slot_cap = (uint32_t)(kPackSlotWords / units);
   if (!(slot_cap & 1u)) slot_cap--;
-
-  // pass A: unit bits (+ raw planes, + slot encoding of group sg)
   const bool fast_a = sg == 0 && huff == 1u && sparse == 0 && nb == J.chunk_bytes &&
                       nvec % T == 0 && nvt % R == 0 && T <= (uint32_t)nthr;
+  bool pairs = false;
+  if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16)
+    pairs = fast_a && smem_u32(S.ptab) + 4096u <= 65536u && build_pair_table(S);
+  __syncthreads();
+
+  // pass A: unit bits (+ raw planes, + slot encoding of group sg)
   if (fast_a) {
-    bool pairs = false;
-    if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16)
-      pairs = smem_u32(S.ptab) + 4096u <= 65536u && build_pair_table(S);
     if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
       if (pairs)
         pack_pair_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
@@ -1308,11 +1343,50 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   // words, no atomics) when that group is the only coded one and every unit
   // holds 32 to slot_cap * 32 bits (so a word spans at most two units)
   bool whole = sg == 0 && huff == 1u;
-  for (uint32_t u = tid; whole && u < units; u += nthr) {
-    const uint32_t b = S.sbits[(u % T) * R + u / T];
-    whole = b >= 32u && b <= slot_cap * 32u;
+  // one unit per thread (unit tid): its exclusive bit offset from a warp scan
+  // before this barrier and a scan of the warp totals after it
+  const bool one = R == 1 && units == (uint32_t)nthr;
+  const int lane = tid & 31, wid = tid >> 5;
+  uint32_t ub = 0, uincl = 0;
+  if (one) {
+    ub = S.sbits[tid];
+    whole = whole && ub >= 32u && ub <= slot_cap * 32u;
+    uincl = ub;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, uincl, o);
+      if (lane >= o) uincl += t;
+    }
+    if (lane == 31) S.wsum[wid] = uincl;
+  } else {
+    for (uint32_t u = tid; whole && u < units; u += nthr) {
+      const uint32_t b = S.sbits[(u % T) * R + u / T];
+      whole = b >= 32u && b <= slot_cap * 32u;
+    }
   }
   whole = __syncthreads_and(whole) != 0;
+  if (whole && one) {
+    const int nw = nthr >> 5;
+    const uint32_t ws = lane < nw ? S.wsum[lane] : 0u;
+    uint32_t wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    const uint32_t uoff = __shfl_sync(0xffffffffu, wi - ws, wid) + uincl - ub;
+    const uint32_t tot = __shfl_sync(0xffffffffu, wi, nw - 1);
+    S.part[0][tid] = uoff;
+    uint8_t* p = out + P + S.off[0];
+    const uint32_t h = (uint32_t)align_up(12 + S.meta[0].nz, 4);
+    uint32_t* po = reinterpret_cast<uint32_t*>(p + h);
+    if (tid > 0) po[tid - 1] = uoff;  // sub-stream starts (sub-stream tid = unit tid)
+    uint32_t* words = po + (T - 1);
+    const uint32_t capw = (uint32_t)(align_up(S.meta[0].size, 16) - h - 4ull * (T - 1)) / 4;
+    __syncthreads();
+    pass_b_whole(S, slots, slot_cap, units, words, capw, tot);
+    return;
+  }
 
   // scan unit bits -> unit offsets; table bytes, sub-stream starts, zeroed words
 #pragma unroll
@@ -1322,8 +1396,6 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     uint8_t* p = out + P + S.off[g];
     const uint32_t nz = S.meta[g].nz;
     const uint32_t h = (uint32_t)align_up(12 + nz, 4);
-    const uint8_t* tab = tabp[g];
-    for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tab[i] : 0;
     const uint32_t nbm = (sparse >> g & 1u) ? bmw : 0u;  // bitmap words (written in pass A)
     uint32_t* po = reinterpret_cast<uint32_t*>(p + h + 4 * nbm);
     for (uint32_t t = 1 + tid; t < T; t += nthr) po[t - 1] = S.part[g][t * R];
@@ -1340,29 +1412,9 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   __syncthreads();
 
   if (whole) {
-    // pass B, whole words: word w (bits 32w .. 32w + 31 of the group's
-    // bitstream) belongs to the unit holding bit 32w; a warp writes one
-    // unit's words at a time (contiguous stores), the last one completed by
-    // the next unit's first bits
-    uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[0] + S.hsz[0]);
-    const int lane = tid & 31, nwarps = nthr >> 5;
-    const uint32_t sl0 = smem_u32(slots);
-    for (uint32_t ui = (uint32_t)(tid >> 5); ui < units; ui += (uint32_t)nwarps) {
-      const uint32_t o = S.part[0][ui], nbits = S.sbits[ui], e = o + nbits;
-      const uint32_t nsw = (nbits + 31) >> 5, sl = sl0 + 4u * ui * slot_cap;
-      const uint32_t nxt = ui + 1 < units ? lds32v(sl0 + 4u * (ui + 1) * slot_cap) : 0u;
-      for (uint32_t w = ((o + 31) >> 5) + lane; w <= (e - 1) >> 5; w += 32) {
-        const uint32_t kb = 32u * w - o, i = kb >> 5, r = e - 32u * w;
-        const uint32_t a = lds32v(sl + 4u * i);
-        const uint32_t b = i + 1 < nsw ? lds32v(sl + 4u * (i + 1)) : 0u;
-        uint32_t x = __funnelshift_l(b, a, kb & 31);
-        if (r < 32) x |= nxt >> r;
-        words[w] = x;
-      }
-    }
-    // the payload's padding words after the bitstream
-    const uint32_t tot = S.part[0][units - 1] + S.sbits[units - 1];
-    for (uint32_t w = ((tot + 31) >> 5) + tid; w < S.capw[0]; w += nthr) words[w] = 0;
+    pass_b_whole(S, slots, slot_cap, units,
+                 reinterpret_cast<uint32_t*>(out + P + S.off[0] + S.hsz[0]), S.capw[0],
+                 S.part[0][units - 1] + S.sbits[units - 1]);
     return;
   }
 
