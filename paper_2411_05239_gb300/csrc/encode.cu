@@ -1090,6 +1090,8 @@ __device__ __forceinline__ void pack_pair_a(const uint8_t* src, const uint8_t* b
   }
 }
 
+__device__ __forceinline__ bool coded_mode_pack(uint32_t m) { return m == kHuff || m == kSparse; }
+
 // Map entries of chunk c (threads 0..G-1) from S.meta and S.off.
 template <int G>
 __device__ __forceinline__ void write_map_entries(const Job& J, uint64_t c, const PackSmem& S) {
@@ -1123,17 +1125,26 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
     S.meta[tid] = meta[gc0 + tid];
     S.off[tid] = offs[gc0 + tid];
   }
-  // group 0's code (coded in nearly every chunk) in the same round trip
+  // group 0's code and table bytes (coded in nearly every chunk) in the same
+  // round trip; the table bytes go out below, the rest of it zero
   for (int s = tid; s < 256; s += nthr) S.codes[0][s] = codes[gc0 * 256 + s];
+  const uint32_t tw =
+      tid < kTabBytes / 4 ? reinterpret_cast<const uint32_t*>(tabs + gc0 * kTabBytes)[tid] : 0u;
   __syncthreads();
   write_map_entries<G>(J, c, S);
 #pragma unroll
   for (int g = 1; g < G; g++)
     if (S.meta[g].mode == kHuff || S.meta[g].mode == kSparse)
       for (int s = tid; s < 256; s += nthr) S.codes[g][s] = codes[(gc0 + g) * 256 + s];
-  const uint8_t* tabp[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (coded_mode_pack(S.meta[0].mode)) {
+    const uint32_t n = 12 + S.meta[0].nz, b = 4u * (uint32_t)tid;
+    if (b < n)
+      *reinterpret_cast<uint32_t*>(J.dst + kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes +
+                                   S.off[0] + b) = n - b >= 4 ? tw : tw & ((1u << 8 * (n - b)) - 1u);
+  }
+  const uint8_t* tabp[4] = {nullptr, nullptr, nullptr, nullptr};  // null: written
 #pragma unroll
-  for (int g = 0; g < G; g++) tabp[g] = tabs + (gc0 + g) * kTabBytes;
+  for (int g = 1; g < G; g++) tabp[g] = tabs + (gc0 + g) * kTabBytes;
   pack_chunk_core<DT>(J, c, S, slots, tabp);
 }
 
@@ -1201,10 +1212,11 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
                                             align_up(12 + S.meta[g].nz, 4));
       for (uint32_t w = tid; w < bmw; w += nthr) bmap[g][w] = 0;
     }
-  // table bytes of the coded groups (counts per length, symbols)
+  // table bytes of the coded groups (counts per length, symbols), unless the
+  // caller wrote them (null tabp)
 #pragma unroll
   for (int g = 0; g < G; g++) {
-    if (!(huff >> g & 1)) continue;
+    if (!(huff >> g & 1) || !tabp[g]) continue;
     uint8_t* p = out + P + S.off[g];
     const uint32_t nz = S.meta[g].nz, h = (uint32_t)align_up(12 + nz, 4);
     for (uint32_t i = tid; i < h; i += nthr) p[i] = (i < 12 + nz) ? tabp[g][i] : 0;
