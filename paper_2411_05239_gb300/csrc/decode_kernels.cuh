@@ -664,7 +664,12 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   const uint32_t D = pfl ? pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes) : 0u;
   const uint32_t t_begin = SPLIT ? t_lo : 0u, t_end = SPLIT ? t_hi : T;
   for (uint32_t t0 = t_begin + tid; t0 < t_end; t0 += NS * nthr) {
-    uint32_t w0[NS], w1[NS], pos[NS], idx[NS], vt[NS];
+    // window w1:w0 (bit pos of w0 first); in the 128-thread kernels (PRE) wn
+    // is the word after it, read one refill ahead so that a refill only moves
+    // registers (the 256-thread kernels cannot spare the registers: 2965 ->
+    // 2503 GB/s on the checkpoint, from spills)
+    constexpr bool PRE = SPLIT;
+    uint32_t w0[NS], w1[NS], wn[NS], pos[NS], idx[NS], vt[NS];
     uint32_t ra[NS][RW], rb[NS][RW];  // 16-bit: raw words of vectors k (even) and k + 1
     // FP32: raw words of step k into ring slot k mod RD (always one commit
     // group per step, empty past the end, so that step k has landed when at
@@ -696,7 +701,8 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
       pos[j] = start & 31u;
       w0[j] = words[min(idx[j], wlim)];
       w1[j] = words[min(idx[j] + 1u, wlim)];
-      idx[j] += 2;
+      if constexpr (PRE) wn[j] = words[min(idx[j] + 2u, wlim)];
+      idx[j] += PRE ? 3 : 2;
       if constexpr (!RING) {
         load_raw_vec<DT>(rawp, rawm, cw, t, ra[j]);
         if (nper > 1) load_raw_vec<DT>(rawp, rawm, cw, t + T, rb[j]);
@@ -722,7 +728,12 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
             if (pos[j] >= 32u) {
               pos[j] -= 32u;
               w0[j] = w1[j];
-              w1[j] = words[min(idx[j], wlim)];
+              if constexpr (PRE) {
+                w1[j] = wn[j];
+                wn[j] = words[min(idx[j], wlim)];
+              } else {
+                w1[j] = words[min(idx[j], wlim)];
+              }
               idx[j]++;
             }
             h[p][j] = e;
@@ -775,7 +786,7 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
     // every sub-stream ends where the next begins
 #pragma unroll
     for (int j = 0; j < NS; j++) {
-      const uint32_t end = (idx[j] - 2u) * 32u + pos[j];
+      const uint32_t end = (idx[j] - (PRE ? 3u : 2u)) * 32u + pos[j];
       if (vt[j] + 1u < T) bad |= end != starts[vt[j]];
       else bad |= end > nbits;
     }
@@ -1419,7 +1430,7 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
       // work item -> chunk (and, below, the part of a chunk split over
       // `parts` items; parts = 1 but for launches with few chunks)
       const uint64_t itm = ticket ? atomicAdd(ticket, 1ull) : blockIdx.x + iter * gridDim.x;
-      const uint32_t np = NT == kDecThreads ? parts : 1u;  // split launches use 128 threads
+      const uint32_t np = (NT == kDecThreads && DTS >= 0) ? parts : 1u;  // split: 128 threads, one dtype
       const uint64_t ch = np > 1 ? itm / np : itm;
       S.part = np > 1 ? (uint32_t)(itm - ch * np) : 0u;
       int jj = 0;
@@ -1442,21 +1453,24 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
     const Job& J = jr.table ? jr.table[j] : jr.one;
     const uint64_t c = chunk - J.chunk_begin + J.chunk0;
     const uint32_t part = S.part;
+    // split work items (and the fast loops' deeper lookahead): 128-thread
+    // kernels of one dtype (mixed launches are never split)
+    constexpr bool SP = NT == kDecThreads && DTS >= 0;
     bool ok;
     if (DTS >= 0) {
-      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+      ok = decode_chunk<(DTS < 0 ? 0 : DTS), W, GEN, SP>(J, c, S, lut0, stg, err, part, parts);
     } else {
       switch (J.dtype) {
         case ZIPNN_BF16:
-          ok = decode_chunk<ZIPNN_BF16, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          ok = decode_chunk<ZIPNN_BF16, W, GEN, SP>(J, c, S, lut0, stg, err, part, parts);
           break;
         case ZIPNN_FP16:
-          ok = decode_chunk<ZIPNN_FP16, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          ok = decode_chunk<ZIPNN_FP16, W, GEN, SP>(J, c, S, lut0, stg, err, part, parts);
           break;
         case ZIPNN_FP32:
-          ok = decode_chunk<ZIPNN_FP32, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts);
+          ok = decode_chunk<ZIPNN_FP32, W, GEN, SP>(J, c, S, lut0, stg, err, part, parts);
           break;
-        default: ok = decode_chunk<ZIPNN_U8, W, GEN, NT == kDecThreads>(J, c, S, lut0, stg, err, part, parts); break;
+        default: ok = decode_chunk<ZIPNN_U8, W, GEN, SP>(J, c, S, lut0, stg, err, part, parts); break;
       }
     }
     if (!ok) break;  // a bulk copy timed out: leave the stage alone
