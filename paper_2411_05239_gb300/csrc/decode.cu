@@ -126,14 +126,52 @@ cudaError_t launch_decode_ex(const Job* d_jobs, const Job* h_one, int njobs,
   if (per_sm == 0 || per_sm > occ) per_sm = occ;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > nchunks_total * parts) grid = nchunks_total * parts;
+  // a split launch runs as clusters of `parts` CTAs, one chunk per cluster
+  // (its CTAs build the chunk's table together), items by stride: the grid
+  // is a whole number of clusters
+  bool clustered = false;
+  if (parts > 1) {
+    grid -= grid % parts;
+    cudaLaunchConfig_t probe = {};
+    probe.gridDim = dim3((unsigned)grid);
+    probe.blockDim = dim3((unsigned)threads);
+    probe.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute ca;
+    ca.id = cudaLaunchAttributeClusterDimension;
+    ca.val.clusterDim.x = parts;
+    ca.val.clusterDim.y = 1;
+    ca.val.clusterDim.z = 1;
+    probe.attrs = &ca;
+    probe.numAttrs = 1;
+    int nclusters = 0;
+    clustered = grid >= parts &&
+                cudaOccupancyMaxActiveClusters(&nclusters, kern, &probe) == cudaSuccess &&
+                nclusters > 0;
+    if (!clustered) cudaGetLastError();  // clear a refused query; split without clusters
+  }
   uint32_t dbg = tuning ? (uint32_t)tuning->debug_flags : 0u;
   // the fast loops' L2 prefetch budget, shared by the CTAs that run at once
   uint64_t pf64 = kPfBudget / grid;
   uint32_t pf = (uint32_t)(pf64 > (64u << 20) ? (64u << 20) : pf64);
   // the kernel's parameters, in the order of k_decode's signature
-  void* args[] = {&r, &nchunks_total, &d_err, &d_ticket, &dbg, &stage, &pf, &parts};
-  e = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3((unsigned)threads), args, (size_t)smem, st);
-  return e;
+  unsigned long long* tk = clustered ? nullptr : d_ticket;  // clusters: items by stride
+  void* args[] = {&r, &nchunks_total, &d_err, &tk, &dbg, &stage, &pf, &parts};
+  if (!clustered)
+    return cudaLaunchKernel(kern, dim3((unsigned)grid), dim3((unsigned)threads), args,
+                            (size_t)smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute ca;
+  ca.id = cudaLaunchAttributeClusterDimension;
+  ca.val.clusterDim.x = parts;
+  ca.val.clusterDim.y = 1;
+  ca.val.clusterDim.z = 1;
+  cfg.attrs = &ca;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
 }  // namespace zipnn

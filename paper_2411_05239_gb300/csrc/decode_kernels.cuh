@@ -111,6 +111,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   return true;
 }
 
+// Thread-block clusters (split work items of one chunk): the CTA's rank and
+// the cluster's size, a shared address mapped into a peer CTA's shared
+// memory, a store there, and the cluster-wide barrier (release / acquire).
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_peer(uint32_t caddr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 template <int DT> struct Traits;
 template <> struct Traits<ZIPNN_BF16> { static constexpr int G = 2, V = 8; };
 template <> struct Traits<ZIPNN_FP16> { static constexpr int G = 2, V = 8; };
@@ -1271,9 +1297,37 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
   // zero-filled), kept when it fits in them.  Pass 2 reads entries that other
   // threads are turning into pairs; a pair keeps the first code's symbol and
   // length where pass 2 reads them, so either value serves.
+  // A chunk split over the CTAs of a cluster (one per part, launched as
+  // such) builds its table together: CTA r fills windows [r, r + 1) * 2^W /
+  // parts and stores every entry into all the cluster's tables (distributed
+  // shared memory, the same offset in each CTA), with a cluster barrier
+  // after each pass.  Every CTA of the cluster takes the same path here: the
+  // chunk's map and table bytes decide it.
+  uint32_t crank = 0, cn = 1;
+  if constexpr (SPLIT) {
+    if (split) {
+      cn = cluster_size();
+      crank = cluster_rank();
+      if (cn != parts || crank != part) {  // not launched as a cluster of the parts
+        cn = 1;
+        crank = 0;
+      }
+    }
+  }
+  // every CTA of the cluster has started (and finished any earlier chunk's
+  // loop, which reads its table) before the first store into a peer
+  if (cn > 1) cluster_sync();
   if (!bad_tab) {
-    const uint32_t per_w = (uint32_t)kLut / ((uint32_t)nthr >> 5);
-    const uint32_t wb = ((uint32_t)tid >> 5) * per_w;
+    const uint32_t span = (uint32_t)kLut / cn;  // windows of this CTA
+    const uint32_t per_w = span / ((uint32_t)nthr >> 5);
+    const uint32_t wb = crank * span + ((uint32_t)tid >> 5) * per_w;
+    // store e at window w of group g's table in every CTA of the cluster
+    auto put_all = [&](uint32_t L, uint32_t w, uint32_t e) {
+      sts32(L + 4u * w, e);
+      if constexpr (SPLIT) {
+        for (uint32_t r = 1; r < cn; r++) st_peer(map_peer(L + 4u * w, (crank + r) % cn), e);
+      }
+    };
 #pragma unroll
     for (int g = 0; g < G; g++) {
       if (!coded_mode(CI.mode[g])) continue;
@@ -1313,25 +1367,26 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
               ent |= kBadLong0 << nb;
           }
         }
-        sts32(L + 4u * w, ent);
+        put_all(L, w, ent);
       }
     }
-    __syncthreads();
+    if (cn > 1) cluster_sync();
+    else __syncthreads();
 #pragma unroll
     for (int g = 0; g < G; g++) {
       if (!coded_mode(CI.mode[g])) continue;
       const uint32_t L = smem_u32(S.lut_ptr[g]);
-      for (int w = tid; w < kLut; w += nthr) {
-        const uint32_t e = lds32(L + 4u * (uint32_t)w);
+      for (uint32_t w = crank * span + (uint32_t)tid; w < (crank + 1) * span; w += (uint32_t)nthr) {
+        const uint32_t e = lds32(L + 4u * w);
         const uint32_t l1 = (e >> 16) & 15u;
         if (l1 == 0 || l1 >= (uint32_t)W) continue;  // invalid, long, or no room left
-        const uint32_t e2 = lds32(L + 4u * (((uint32_t)w << l1) & (kLut - 1)));
+        const uint32_t e2 = lds32(L + 4u * ((w << l1) & (kLut - 1)));
         const uint32_t l2 = (e2 >> 16) & 15u;
         if (l2 == 0 || l1 + l2 > (uint32_t)W) continue;
-        sts32(L + 4u * (uint32_t)w,
-              (e & 0x000F00FFu) | ((e2 & 0xFFu) << 8) | ((l1 + l2) << 27) | kPair);
+        put_all(L, w, (e & 0x000F00FFu) | ((e2 & 0xFFu) << 8) | ((l1 + l2) << 27) | kPair);
       }
     }
+    if (cn > 1) cluster_sync();
   }
   // wait for the staged payloads (every thread; bounded)
   uint32_t timed_out = 0;
