@@ -690,11 +690,13 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   const uint32_t D = pfl ? pf_steps<G>(rawm, base8 != nullptr, T, nper, stg.pf_bytes) : 0u;
   const uint32_t t_begin = SPLIT ? t_lo : 0u, t_end = SPLIT ? t_hi : T;
   for (uint32_t t0 = t_begin + tid; t0 < t_end; t0 += NS * nthr) {
-    // window w1:w0 (bit pos of w0 first); in the 128-thread kernels (PRE) wn
-    // is the word after it, read one refill ahead so that a refill only moves
-    // registers (the 256-thread kernels cannot spare the registers: 2965 ->
-    // 2503 GB/s on the checkpoint, from spills)
-    constexpr bool PRE = SPLIT;
+    // window w1:w0 (bit pos of w0 first); with PRE, wn is the word after it,
+    // read one refill ahead so that a refill only moves registers: in the
+    // 128-thread kernels and the FP16 ones (two 256-thread CTAs per SM); the
+    // other 256-thread kernels cannot spare the registers at three CTAs per SM
+    // (2965 -> 2503 GB/s on the checkpoint, from spills) and lose more than
+    // PRE gains at two (2541)
+    constexpr bool PRE = SPLIT || DT == ZIPNN_FP16;
     uint32_t w0[NS], w1[NS], wn[NS], pos[NS], idx[NS], vt[NS];
     uint32_t ra[NS][RW], rb[NS][RW];  // 16-bit: raw words of vectors k (even) and k + 1
     // FP32: raw words of step k into ring slot k mod RD (always one commit
@@ -1447,9 +1449,11 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
 // DTS: the dtype of every job in the launch, or -1 for a mixed batch.
 // 256-thread CTAs: three per SM (80 registers) for the model-weight kernels;
 // two (128 registers) for the GEN kernels, whose delta loops decode two coded
-// groups and spill at 80.
+// groups and spill at 80, and for FP16, whose exponent codes are long (most
+// lookups take the two-step path) and which gains from the refill preload
+// (1408 -> 1523 GB/s on a 256 MiB tensor).
 template <int DTS, int W, int NT, bool GEN>
-__global__ void __launch_bounds__(NT, NT == 256 ? (GEN ? 2 : 3) : 1)
+__global__ void __launch_bounds__(NT, NT == 256 ? ((GEN || DTS == ZIPNN_FP16) ? 2 : 3) : 1)
 k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
          unsigned long long* __restrict__ ticket, uint32_t debug_flags, uint32_t stage_cap,
          uint32_t pf_bytes, uint32_t parts) {
