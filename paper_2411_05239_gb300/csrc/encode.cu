@@ -132,17 +132,23 @@ __device__ __forceinline__ void red_shared_inc(uint32_t saddr) {
 }
 
 // Histogram of a whole chunk of 16-bit elements (no ragged vector): the byte
-// offsets of an element h's counters follow from its bits directly.  Exponent
-// bin e = (h >> 7) & 0xFF sits at e * 128 = h & 0x7F80; the sign + low-fraction
-// bin r = (h >> 8 & 0x80) | (h & 0x7F) sits at 0x8000 + r * 128 =
-// 0x8000 | (h >> 1 & 0x4000) | (h << 7 & 0x3F80).  hl is the shared-window
-// address of lane 0's counter of exponent bin 0 plus 4 * lane.
-__device__ __forceinline__ void hist16_word(uint32_t hl, uint32_t w) {
-  red_shared_inc(hl + (w & 0x7F80u));
-  red_shared_inc(hl + (((w >> 1) & 0x4000u) | (((w << 7) & 0x3F80u) | 0x8000u)));
-  const uint32_t h = w >> 16;
-  red_shared_inc(hl + (h & 0x7F80u));
-  red_shared_inc(hl + (((h >> 1) & 0x4000u) | (((h << 7) & 0x3F80u) | 0x8000u)));
+// offsets of an element h's counters follow from its bits.  Exponent bin e =
+// (h >> 7) & 0xFF sits at e * 128 = h & 0x7F80 (one mask per element).  The
+// sign + low-fraction bins r = (h >> 8 & 0x80) | (h & 0x7F) of four elements
+// (two words) are gathered into one word with two byte permutes and a bit
+// select, as split16 does; bin r sits at 0x8000 + r * 128 (a byte permute
+// and a shift-add per element).  hl is the shared-window address of lane 0's
+// counter of exponent bin 0 plus 4 * lane.
+__device__ __forceinline__ void hist16_words(uint32_t hl, uint32_t w0, uint32_t w1) {
+  red_shared_inc(hl + (w0 & 0x7F80u));
+  red_shared_inc(hl + ((w0 >> 16) & 0x7F80u));
+  red_shared_inc(hl + (w1 & 0x7F80u));
+  red_shared_inc(hl + ((w1 >> 16) & 0x7F80u));
+  const uint32_t lo = __byte_perm(w0, w1, 0x6420), hi = __byte_perm(w0, w1, 0x7531);
+  const uint32_t r = (hi & 0x80808080u) | (lo & 0x7F7F7F7Fu);
+  const uint32_t hl8 = hl + 0x8000u;
+#pragma unroll
+  for (int k = 0; k < 4; k++) red_shared_inc(hl8 + (__byte_perm(r, 0, 0x4440 + k) << 7));
 }
 
 // Histograms of chunk c of job J by the NT threads of the CTA, with the
@@ -200,10 +206,8 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
       }
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        hist16_word(hls, a[u].x);
-        hist16_word(hls, a[u].y);
-        hist16_word(hls, a[u].z);
-        hist16_word(hls, a[u].w);
+        hist16_words(hls, a[u].x, a[u].y);
+        hist16_words(hls, a[u].z, a[u].w);
         const uint32_t any = a[u].x | a[u].y | a[u].z | a[u].w;
         if (!(any & 0x7F807F80u)) zc[0] += 8;       // 8 zero exponent bytes
         if (!(any & 0x807F807Fu)) zc[1 % G] += 8;   // 8 zero sign + fraction bytes
@@ -1152,24 +1156,34 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
 // (offsets in S.part[0], bits in S.sbits) hold 32 to slot_cap * 32 bits
 // each: word w (bits 32w .. 32w + 31 of the bitstream, tot bits, capw words
 // of payload at words) belongs to the unit holding bit 32w, so each word is
-// written whole (no zeroed words, no atomics) from at most two units' slots;
-// a warp writes one unit's words at a time (contiguous stores), the last one
-// completed by the next unit's first bits.  Then the padding words.
+// written whole (no zeroed words, no atomics) from at most two units' slots.
+// Warp k writes the words of its share of the units, 32 consecutive words at
+// a time (one 128-B store); each lane follows the unit of its word with a
+// cursor that only moves forward (units are consecutive in the stream: the
+// next one starts where the current one ends).  Then the padding words.
 __device__ __forceinline__ void pass_b_whole(const PackSmem& S, const uint32_t* slots,
                                              uint32_t slot_cap, uint32_t units, uint32_t* words,
                                              uint32_t capw, uint32_t tot) {
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, nwarps = nthr >> 5;
   const uint32_t sl0 = smem_u32(slots);
-  for (uint32_t ui = (uint32_t)(tid >> 5); ui < units; ui += (uint32_t)nwarps) {
-    const uint32_t o = S.part[0][ui], nbits = S.sbits[ui], e = o + nbits;
-    const uint32_t nsw = (nbits + 31) >> 5, sl = sl0 + 4u * ui * slot_cap;
-    const uint32_t nxt = ui + 1 < units ? lds32v(sl0 + 4u * (ui + 1) * slot_cap) : 0u;
-    for (uint32_t w = ((o + 31) >> 5) + lane; w <= (e - 1) >> 5; w += 32) {
-      const uint32_t kb = 32u * w - o, i = kb >> 5, r = e - 32u * w;
+  const uint32_t upw = (units + (uint32_t)nwarps - 1) / (uint32_t)nwarps;
+  const uint32_t u0 = min(units, (uint32_t)(tid >> 5) * upw), u1 = min(units, u0 + upw);
+  if (u0 < u1) {
+    const uint32_t wend = u1 < units ? (S.part[0][u1] + 31) >> 5 : (tot + 31) >> 5;
+    uint32_t cu = u0, o = S.part[0][u0], e = o + S.sbits[u0];
+    for (uint32_t w = ((o + 31) >> 5) + (uint32_t)lane; w < wend; w += 32) {
+      const uint32_t bit = 32u * w;
+      while (bit >= e) {  // at most a few units per step (each holds >= 32 bits)
+        cu++;
+        o = e;
+        e = o + S.sbits[cu];
+      }
+      const uint32_t k = bit - o, i = k >> 5, r = e - bit;
+      const uint32_t sl = sl0 + 4u * cu * slot_cap;
       const uint32_t a = lds32v(sl + 4u * i);
-      const uint32_t b = i + 1 < nsw ? lds32v(sl + 4u * (i + 1)) : 0u;
-      uint32_t x = __funnelshift_l(b, a, kb & 31);
-      if (r < 32) x |= nxt >> r;
+      const uint32_t b = 32u * (i + 1) < e - o ? lds32v(sl + 4u * (i + 1)) : 0u;
+      uint32_t x = __funnelshift_l(b, a, k & 31);
+      if (r < 32 && cu + 1 < units) x |= lds32v(sl + 4u * slot_cap) >> r;
       words[w] = x;
     }
   }
