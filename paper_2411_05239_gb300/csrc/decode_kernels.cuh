@@ -1266,7 +1266,11 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     }
 #pragma unroll
     for (int g = fast_nc; g < G; g++) ok = ok && !coded_mode(CI.mode[g]);
-    if (ok) fast = (Tp % (2u * nthr) == 0) ? 2 : ((Tp % (uint32_t)nthr == 0) ? 1 : 0);
+    // one sub-stream per thread for FP32 (its raw words come through the
+    // shared-memory ring: 1787 -> 1853 GB/s on a 256 MiB tensor), two for the
+    // 16-bit types (one: the checkpoint 2965 -> 2575 GB/s)
+    if (ok)
+      fast = (DT != ZIPNN_FP32 && Tp % (2u * nthr) == 0) ? 2 : ((Tp % (uint32_t)nthr == 0) ? 1 : 0);
   }
   // exponent symbols are stored rotated for the fast loops' merge
   const bool rot0 = fast != 0 && DT != ZIPNN_U8;
