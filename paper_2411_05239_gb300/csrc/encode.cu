@@ -1202,8 +1202,9 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   const uint32_t T = J.lanes;
   const uint32_t R = T <= (uint32_t)nthr ? (uint32_t)nthr / T : 1u;  // parts per sub-stream
   const uint32_t units = T * R;                                        // <= max(nthr, T)
-  const uint64_t nvt = (nvec + T - 1) / T;                             // vectors of sub-stream 0
-  const uint64_t per = (nvt + R - 1) / R;                              // vectors per part
+  // (32-bit divisions: a chunk holds fewer than 2^32 vectors)
+  const uint64_t nvt = ((uint32_t)nvec + T - 1) / T;                   // vectors of sub-stream 0
+  const uint64_t per = ((uint32_t)nvt + R - 1) / R;                    // vectors per part
   const uint8_t* src = J.src + off0;
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
   const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
