@@ -678,6 +678,15 @@ __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v) {
   for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
 }
 
+// a / b and a % b for the sub-stream geometry: a shift and a mask when b is a
+// power of two (the lane counts and unit counts in use), else the division.
+__device__ __forceinline__ uint32_t gdiv(uint32_t a, uint32_t b) {
+  return (b & (b - 1u)) == 0 ? a >> (__ffs(b) - 1) : a / b;
+}
+__device__ __forceinline__ uint32_t gmod(uint32_t a, uint32_t b) {
+  return (b & (b - 1u)) == 0 ? a & (b - 1u) : a % b;
+}
+
 template <int DT> struct PTraits;
 template <> struct PTraits<ZIPNN_BF16> { static constexpr int G = 2, V = 8; };
 template <> struct PTraits<ZIPNN_FP16> { static constexpr int G = 2, V = 8; };
@@ -881,7 +890,7 @@ __device__ __forceinline__ void pack_fast_a(const uint8_t* src, const uint8_t* b
     return a;
   };
   for (uint32_t u = tid; u < units; u += nthr) {
-    const uint32_t t = u % T, k = u / T, ui = t * R + k;
+    const uint32_t t = gmod(u, T), k = gdiv(u, T), ui = t * R + k;
     SlotWriter32 sw;
     sw.slot = smem_u32(slots) + 4u * ui * slot_cap;
     sw.cur = 0;
@@ -1079,7 +1088,7 @@ __device__ __forceinline__ void pack_pair_a(const uint8_t* src, const uint8_t* b
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   const uint4* b4 = reinterpret_cast<const uint4*>(base);
   for (uint32_t u = tid; u < units; u += nthr) {
-    const uint32_t t = u % T, k = u / T, ui = t * R + k;
+    const uint32_t t = gmod(u, T), k = gdiv(u, T), ui = t * R + k;
     const uint32_t sa0 = smem_u32(slots) + 4u * ui * slot_cap, slast = sa0 + 4u * (slot_cap - 1);
     const uint32_t v = t + k * per * T;
     uint32_t bits;
@@ -1200,11 +1209,11 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   const uint64_t m = nb / ES;
   const uint64_t nvec = (nb + 15) / 16;
   const uint32_t T = J.lanes;
-  const uint32_t R = T <= (uint32_t)nthr ? (uint32_t)nthr / T : 1u;  // parts per sub-stream
+  const uint32_t R = T <= (uint32_t)nthr ? gdiv((uint32_t)nthr, T) : 1u;  // parts per sub-stream
   const uint32_t units = T * R;                                        // <= max(nthr, T)
   // (32-bit divisions: a chunk holds fewer than 2^32 vectors)
-  const uint64_t nvt = ((uint32_t)nvec + T - 1) / T;                   // vectors of sub-stream 0
-  const uint64_t per = ((uint32_t)nvt + R - 1) / R;                    // vectors per part
+  const uint64_t nvt = gdiv((uint32_t)nvec + T - 1, T);                // vectors of sub-stream 0
+  const uint64_t per = gdiv((uint32_t)nvt + R - 1, R);                 // vectors per part
   const uint8_t* src = J.src + off0;
   const uint8_t* base = J.base ? J.base + off0 : nullptr;
   const uint64_t P = kHdrBytes + (uint64_t)J.n_chunks * G * kEntryBytes;
@@ -1244,10 +1253,11 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 #pragma unroll
   for (int g = G - 1; g >= 0; g--)
     if (huff >> g & 1) sg = g;
-  uint32_t slot_cap = (uint32_t)(kPackSlotWords / units);
+  uint32_t slot_cap = gdiv(kPackSlotWords, units);
   if (!(slot_cap & 1u)) slot_cap--;
   const bool fast_a = sg == 0 && huff == 1u && sparse == 0 && nb == J.chunk_bytes &&
-                      nvec % T == 0 && nvt % R == 0 && T <= (uint32_t)nthr;
+                      gmod((uint32_t)nvec, T) == 0 && gmod((uint32_t)nvt, R) == 0 &&
+                      T <= (uint32_t)nthr;
   bool pairs = false;
   if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16)
     pairs = fast_a && smem_u32(S.ptab) + 4096u <= 65536u && build_pair_table(S);
@@ -1257,13 +1267,13 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   if (fast_a) {
     if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
       if (pairs)
-        pack_pair_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+        pack_pair_a<DT>(src, base, T, R, gdiv((uint32_t)nvt, R), slots, slot_cap, S, out, P, raw);
     }
     if (!pairs)
-      pack_fast_a<DT>(src, base, T, R, (uint32_t)(nvt / R), slots, slot_cap, S, out, P, raw);
+      pack_fast_a<DT>(src, base, T, R, gdiv((uint32_t)nvt, R), slots, slot_cap, S, out, P, raw);
   }
   for (uint32_t u = fast_a ? units : tid; u < units; u += nthr) {
-    const uint32_t t = u % T, k = u / T;
+    const uint32_t t = gmod(u, T), k = gdiv(u, T);
     uint32_t bits[G];
 #pragma unroll
     for (int g = 0; g < G; g++) bits[g] = 0;
@@ -1387,7 +1397,7 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     if (lane == 31) S.wsum[wid] = uincl;
   } else {
     for (uint32_t u = tid; whole && u < units; u += nthr) {
-      const uint32_t b = S.sbits[(u % T) * R + u / T];
+      const uint32_t b = S.sbits[gmod(u, T) * R + gdiv(u, T)];
       whole = b >= 32u && b <= slot_cap * 32u;
     }
   }
@@ -1447,7 +1457,7 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 
   // pass B
   for (uint32_t u = tid; u < units; u += nthr) {
-    const uint32_t t = u % T, k = u / T;
+    const uint32_t t = gmod(u, T), k = gdiv(u, T);
     const uint32_t ui = t * R + k;
     // (1) slot-staged group: shift the unit's slot words to its bit offset
     bool refill = false;
@@ -1567,7 +1577,10 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
     return;
   }
   const uint64_t chunk = blockIdx.x;
-  const int j = find_job_chunk(jr, chunk);
+  __shared__ int job;  // found by thread 0, read by all after the barrier
+  if (tid == 0) job = find_job_chunk(jr, chunk);
+  __syncthreads();
+  const int j = job;
   const Job& J = job_at(jr, j);
   if (totals[j] > J.out_capacity) return;
   const uint64_t c = chunk - J.chunk_begin;
