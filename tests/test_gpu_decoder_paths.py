@@ -286,3 +286,26 @@ def test_chunks_split_over_work_items_decode_the_same(parts):
     Z.sync_status()
     for x, o in zip(xs, outs):
         assert torch.equal(o.view(torch.uint8), x.view(torch.uint8))
+
+
+@pytest.mark.parametrize("parts,nchunks", [(4, 76), (2, 150), (8, 40)])
+def test_cluster_split_with_several_items_per_cta(parts, nchunks):
+    """Split launches run as clusters of the chunk's parts that build its table
+    together; with one CTA per SM (ctas_per_sm = 1) a cluster takes several
+    chunks in turn, and each chunk's table build starts only when every CTA
+    of the cluster has finished the previous chunk.  Exact bytes."""
+    lanes = 1024 if parts == 8 else 512
+    x = W.gaussian(nchunks * 262144 // 2, 0.02, 90 + parts, device="cuda")
+    c = Z.compress(x, lanes=lanes)
+    out = torch.empty_like(x)
+    for tune in (Z.tuning(parts=parts, ctas_per_sm=1), Z.tuning(parts=parts)):
+        out.fill_(0)
+        Z.batch_decompress([c], [out], tune=tune)
+        Z.sync_status()
+        assert torch.equal(out.view(torch.int16), x.view(torch.int16))
+        pd = Z.plan_decompress([c], [out], tune=tune)
+        out.fill_(0)
+        pd.launch()
+        Z.sync_status()
+        pd.close()
+        assert torch.equal(out.view(torch.int16), x.view(torch.int16))
