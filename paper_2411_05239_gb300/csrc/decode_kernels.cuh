@@ -692,11 +692,11 @@ __device__ __forceinline__ void decode_fast(const Job& J, uint64_t c, const Smem
   for (uint32_t t0 = t_begin + tid; t0 < t_end; t0 += NS * nthr) {
     // window w1:w0 (bit pos of w0 first); with PRE, wn is the word after it,
     // read one refill ahead so that a refill only moves registers: in the
-    // 128-thread kernels and the FP16 ones (two 256-thread CTAs per SM); the
-    // other 256-thread kernels cannot spare the registers at three CTAs per SM
-    // (2965 -> 2503 GB/s on the checkpoint, from spills) and lose more than
-    // PRE gains at two (2541)
-    constexpr bool PRE = SPLIT || DT == ZIPNN_FP16;
+    // 128-thread kernels, the FP16 ones (two 256-thread CTAs per SM) and FP32
+    // (one sub-stream per thread); the BF16 256-thread kernel cannot spare the
+    // registers at three CTAs per SM (2965 -> 2503 GB/s on the checkpoint,
+    // from spills) and loses more than PRE gains at two (2541)
+    constexpr bool PRE = SPLIT || DT == ZIPNN_FP16 || DT == ZIPNN_FP32;
     uint32_t w0[NS], w1[NS], wn[NS], pos[NS], idx[NS], vt[NS];
     uint32_t ra[NS][RW], rb[NS][RW];  // 16-bit: raw words of vectors k (even) and k + 1
     // FP32: raw words of step k into ring slot k mod RD (always one commit
