@@ -1074,14 +1074,109 @@ __device__ __forceinline__ uint32_t pair_unit(const uint4* __restrict__ s4,
   return (sa - sa0) * 8u + nb;
 }
 
+// The FP32 unit of pack_pair_a: a vector holds four elements, whose exponent
+// bytes (bits 23-30) a byte permute gathers into the 16-bit pair layout (two
+// entries, one four-symbol append per vector); the three other byte groups are
+// stored through rawp[0..2] (groups 1-3; null: not raw).
+template <bool XB>
+__device__ __forceinline__ uint32_t pair_unit32(const uint4* __restrict__ s4,
+                                                const uint4* __restrict__ b4,
+                                                uint32_t* const (&rawp)[3], uint32_t v, uint32_t T,
+                                                uint32_t per, uint32_t pb16, uint32_t sa0,
+                                                uint32_t slast) {
+  uint32_t sa = sa0, lo = 0, hi = 0, nb = 0;  // pending bits: the low nb of hi:lo
+  auto ld = [&](uint32_t w) -> uint4 {
+    uint4 a = __ldg(s4 + w);
+    if (XB) {
+      const uint4 b = __ldg(b4 + w);
+      a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+    }
+    return a;
+  };
+  auto pf = [&](uint32_t w) {
+    prefetch_l2(s4 + w);
+    if (XB) prefetch_l2(b4 + w);
+  };
+  auto entry = [&](uint32_t x) -> uint32_t {
+    return lds32(((x & 0x0F800F80u) * 0x801u + pb16) >> 16);
+  };
+  auto put = [&](uint32_t V, uint32_t L) {
+    hi = __funnelshift_lc(lo, hi, L);
+    lo = __funnelshift_lc(0u, lo, L) | V;
+    nb += L;
+    sts32(min(sa, slast), __funnelshift_r(lo, hi, nb - 32u));  // the word if nb >= 32
+    const bool full = nb >= 32;
+    sa += full ? 4u : 0u;
+    nb -= full ? 32u : 0u;
+  };
+  const bool anyraw = rawp[0] || rawp[1] || rawp[2];
+  auto one = [&](uint4& a, bool LD, bool PF) {
+    const uint4 x = a;
+    if (LD) a = ld(v + 2 * T);
+    if (PF) pf(v + kPrefetchAhead * T);
+    // high halves of elements 0,1 and 2,3: exponents at bits 7-14 and 23-30
+    const uint32_t E0 = entry(__byte_perm(x.x, x.y, 0x7632));
+    const uint32_t E1 = entry(__byte_perm(x.z, x.w, 0x7632));
+    if (anyraw) {
+      const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+      uint32_t g[4];
+      split32(xs, g);
+#pragma unroll
+      for (int q = 0; q < 3; q++)
+        if (rawp[q]) rawp[q][v] = g[q + 1];
+    }
+    const uint32_t L = (E0 + E1) & 63u;
+    if (L <= 32) {
+      put(__funnelshift_l(0u, E0 >> 6, E1) | (E1 >> 6), L);
+    } else {
+      put(E0 >> 6, E0 & 63u);
+      put(E1 >> 6, E1 & 63u);
+    }
+    v += T;
+  };
+  for (uint32_t i = 2; i < kPrefetchAhead && i < per; i++) pf(v + i * T);
+  uint4 a0 = ld(v), a1 = per > 1 ? ld(v + T) : make_uint4(0, 0, 0, 0);
+  uint32_t i = 0;
+  for (; i + kPrefetchAhead + 1 < per; i += 2) {
+    one(a0, true, true);
+    one(a1, true, true);
+  }
+  for (; i < per; i += 2) {
+    one(a0, i + 2 < per, i + kPrefetchAhead < per);
+    if (i + 1 < per) one(a1, i + 3 < per, i + 1 + kPrefetchAhead < per);
+  }
+  if (nb) sts32(min(sa, slast), lo << (32 - nb));
+  return (sa - sa0) * 8u + nb;
+}
+
 template <int DT>
 __device__ __forceinline__ void pack_pair_a(const uint8_t* src, const uint8_t* base, uint32_t T,
                                             uint32_t R, uint32_t per, uint32_t* slots,
                                             uint32_t slot_cap, PackSmem& S, uint8_t* out,
                                             uint64_t P, uint32_t raw) {
-  static_assert(DT == ZIPNN_BF16 || DT == ZIPNN_FP16, "16-bit chunks only");
+  static_assert(DT == ZIPNN_BF16 || DT == ZIPNN_FP16 || DT == ZIPNN_FP32,
+                "16-bit or FP32 chunks");
   const int tid = threadIdx.x, nthr = blockDim.x;
   const uint32_t units = T * R;
+  if constexpr (DT == ZIPNN_FP32) {
+    uint32_t* const rawp[3] = {
+        (raw >> 1 & 1u) ? reinterpret_cast<uint32_t*>(out + P + S.off[1]) : nullptr,
+        (raw >> 2 & 1u) ? reinterpret_cast<uint32_t*>(out + P + S.off[2]) : nullptr,
+        (raw >> 3 & 1u) ? reinterpret_cast<uint32_t*>(out + P + S.off[3]) : nullptr};
+    const uint32_t pb16 = smem_u32(S.ptab) << 16;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    const uint4* b4 = reinterpret_cast<const uint4*>(base);
+    for (uint32_t u = tid; u < units; u += nthr) {
+      const uint32_t t = gmod(u, T), k = gdiv(u, T), ui = t * R + k;
+      const uint32_t sa0 = smem_u32(slots) + 4u * ui * slot_cap, slast = sa0 + 4u * (slot_cap - 1);
+      const uint32_t v = t + k * per * T;
+      const uint32_t bits = base ? pair_unit32<true>(s4, b4, rawp, v, T, per, pb16, sa0, slast)
+                                 : pair_unit32<false>(s4, b4, rawp, v, T, per, pb16, sa0, slast);
+      S.sbits[ui] = bits;
+      S.part[0][ui] = bits;
+    }
+    return;
+  }
   uint2* const rawp = reinterpret_cast<uint2*>(out + P + S.off[1]);
   const bool rw = (raw >> 1 & 1u) != 0;
   const uint32_t pb16 = smem_u32(S.ptab) << 16;  // table address < 61440 (checked by the caller)
@@ -1259,13 +1354,13 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
                       gmod((uint32_t)nvec, T) == 0 && gmod((uint32_t)nvt, R) == 0 &&
                       T <= (uint32_t)nthr;
   bool pairs = false;
-  if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16)
+  if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16 || DT == ZIPNN_FP32)
     pairs = fast_a && smem_u32(S.ptab) + 4096u <= 65536u && build_pair_table(S);
   __syncthreads();
 
   // pass A: unit bits (+ raw planes, + slot encoding of group sg)
   if (fast_a) {
-    if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
+    if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16 || DT == ZIPNN_FP32) {
       if (pairs)
         pack_pair_a<DT>(src, base, T, R, gdiv((uint32_t)nvt, R), slots, slot_cap, S, out, P, raw);
     }

@@ -1,13 +1,14 @@
 """The packer's pass-A variants against the oracle (needs a GB300).
 
 Chunks of 16-bit elements whose exponent group is Huffman coded and whose
-sign + fraction group is stored raw take one of two specialised encoders:
+sign + fraction group is stored raw (and FP32 chunks with a coded exponent
+group and raw other groups) take one of two specialised encoders:
 pair lookups when the code's symbols have distinct residues mod 32, single
 lookups otherwise; both stage each unit's bits in a shared-memory slot and
 re-encode a unit whose slot overflows.  Every variant must write the oracle's
 container byte for byte (ZipNN Sec. 3.1, 3.2, 5.1): here with symbol sets that
 clash mod 32, four-symbol runs longer than 32 bits, overflowing slots, exact
-zeros, deltas, FP16, every lane split and several chunk sizes.
+zeros, deltas, FP16, FP32, every lane split and several chunk sizes.
 """
 from __future__ import annotations
 
@@ -67,6 +68,15 @@ def _cases():
     out["fp16"] = (W.gaussian(N, 0.02, 73, torch.float16), None)
     # a delta whose exponent XOR is coded and whose fraction XOR is raw
     out["delta"] = (W.gaussian(N, 0.02, 74), W.gaussian(N, 0.02, 75))
+    # FP32: exponent pairs gathered from two elements, three raw byte groups
+    out["fp32"] = (W.gaussian(N // 2, 0.05, 76, torch.float32), None)
+    out["fp32_delta"] = (W.gaussian(N // 2, 0.05, 77, torch.float32),
+                         W.gaussian(N // 2, 0.05, 78, torch.float32))
+    f = W.gaussian(N // 2, 0.05, 79, torch.float32).view(torch.int32).numpy().copy()
+    pick = g.random(N // 2)
+    f[pick < 0.01] = (f[pick < 0.01] & ~(0xFF << 23)) | (100 << 23)   # exponents 100 and 132
+    f[(pick >= 0.01) & (pick < 0.02)] = (f[(pick >= 0.01) & (pick < 0.02)] & ~(0xFF << 23)) | (132 << 23)
+    out["fp32_clash"] = (torch.from_numpy(f).view(torch.float32), None)
     return out
 
 
