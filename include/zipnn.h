@@ -301,6 +301,9 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
  *   about segment_bytes (0 = 512 MiB); each segment's persistent decode starts
  *   as soon as its copies have landed, while the copies of the next segments
  *   proceed on another stream: one graph, copies and decoding overlapped.
+ *   Containers of a segment that sit back to back in both host and device
+ *   memory (h_containers[i] + nbytes == h_containers[i+1] and likewise for
+ *   data) travel in one copy; no byte outside a container is written.
  *   Pageable host memory cannot be captured and returns ECUDA.  Creation
  *   reads the host containers' chunk maps to size each segment's stage. */
 zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_containers,

@@ -431,17 +431,24 @@ zipnn_status zipnn_plan_load(const zipnn_stream* streams, const void* const* h_c
         add_map_need(static_cast<const uint8_t*>(h_containers[i]) + kHdrBytes, s->n_chunks,
                      s->n_groups, plan_lut_bits(&tu), dflt, &nd);
       }
-      for (int i = a; i < b && r == cudaSuccess; i++) {
+      for (int i = a; i < b; i++) {
         if (jobs[i].flags & ZIPNN_FLAG_DELTA) has_delta = true;
-        if (stage_frac64(jobs[i].dtype, jobs[i].flags) > frac64)
-          frac64 = stage_frac64(jobs[i].dtype, jobs[i].flags);
-        r = cudaMemcpyAsync(streams[i].data, h_containers[i], streams[i].nbytes,
-                            cudaMemcpyHostToDevice, sc);
         nch += jobs[i].n_chunks;
         if (jobs[i].dtype != uniform) uniform = -1;
-        if (jobs[i].chunk_bytes > max_chunk) max_chunk = jobs[i].chunk_bytes;
         if ((int)streams[i].n_groups > max_groups) max_groups = (int)streams[i].n_groups;
         if (jobs[i].lanes % 256) lanes256 = false;
+      }
+      // one copy per run of containers that sit back to back in both host and
+      // device memory (each copy costs the copy engine a few microseconds of
+      // setup); exact adjacency only, so no byte outside a container is written
+      for (int i = a; i < b && r == cudaSuccess; i++) {
+        const uint8_t* hs = static_cast<const uint8_t*>(h_containers[i]);
+        uint8_t* ds = static_cast<uint8_t*>(streams[i].data);
+        size_t run = streams[i].nbytes;
+        while (i + 1 < b && static_cast<const uint8_t*>(h_containers[i + 1]) == hs + run &&
+               static_cast<uint8_t*>(streams[i + 1].data) == ds + run)
+          run += streams[++i].nbytes;
+        r = cudaMemcpyAsync(ds, hs, run, cudaMemcpyHostToDevice, sc);
       }
       if (r == cudaSuccess) r = cudaEventRecord(evs[(size_t)k], sc);
       if (r == cudaSuccess) r = cudaStreamWaitEvent(cs, evs[(size_t)k], 0);

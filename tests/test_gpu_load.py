@@ -54,3 +54,48 @@ def test_load_plan_rejects_pageable_host_memory():
     h = [torch.empty(c.nbytes, dtype=torch.uint8) for c in cs]
     with pytest.raises(ValueError):
         Z.plan_load(cs, h, [torch.empty_like(y) for y in ys], bases=bases)
+
+
+@pytest.mark.parametrize("segment_bytes", [0, 300_000])
+def test_load_plan_coalesces_adjacent_containers_only(segment_bytes):
+    """Containers back to back in both a pinned host arena and a device arena
+    go over in one copy per run; a gap on either side splits the run, and the
+    device bytes in a gap are never written."""
+    cs, ys, bases = _setup()
+    n = len(cs)
+    gap = 32
+    # device gap after container 1, host gap after container 3
+    dgap = [gap if i == 1 else 0 for i in range(n)]
+    hgap = [gap if i == 3 else 0 for i in range(n)]
+    hoff, doff, ho, do = [], [], 0, 0
+    for i, c in enumerate(cs):
+        assert c.nbytes % 16 == 0
+        hoff.append(ho)
+        doff.append(do)
+        ho += c.nbytes + hgap[i]
+        do += c.nbytes + dgap[i]
+    harena = torch.full((ho,), 0xA5, dtype=torch.uint8, pin_memory=True)
+    darena = torch.full((do,), 0x3C, dtype=torch.uint8, device="cuda")
+    for i, c in enumerate(cs):
+        harena[hoff[i]:hoff[i] + c.nbytes].copy_(c.device_tensor())
+    torch.cuda.synchronize()
+    lcs = []
+    for i, c in enumerate(cs):
+        dv = darena[doff[i]:doff[i] + c.nbytes]
+        dv.copy_(c.device_tensor())
+        lcs.append(Z.wrap(dv, c.nbytes))
+    for i, c in enumerate(cs):   # the load must bring every container byte
+        darena[doff[i]:doff[i] + c.nbytes].zero_()
+    hs = [harena[hoff[i]:hoff[i] + c.nbytes] for i, c in enumerate(cs)]
+    outs = [torch.empty_like(y) for y in ys]
+    plan = Z.plan_load(lcs, hs, outs, bases=bases, segment_bytes=segment_bytes)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        plan.launch()
+        Z.sync_status()
+        for y, o in zip(ys, outs):
+            assert torch.equal(o.view(torch.uint8), y.view(torch.uint8))
+        g0 = doff[1] + cs[1].nbytes
+        assert torch.all(darena[g0:g0 + gap] == 0x3C)
+    plan.close()
