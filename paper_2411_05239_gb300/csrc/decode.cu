@@ -21,8 +21,11 @@ namespace {
 // two CTAs share an SM.  With one (a plan that read its containers' chunk
 // maps): exactly that many bytes, up to the whole SM when only one CTA per SM
 // can stage the payloads.  Always room for the tables of every Huffman group
-// after the first.  Multiples of 128 B, as the decoder's table placement
-// assumes.
+// after the first: in the stage for a 16-bit chunk's second group; in the
+// stage and the raw-word rings behind it together for an FP32 chunk's
+// groups 1-3 (such a chunk takes no fast loop, which leaves the rings free),
+// so that the three spare tables do not cost FP32 launches a CTA per SM.
+// Multiples of 128 B, as the decoder's table placement assumes.
 uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int w, uint32_t ring,
                             uint32_t stage_need) {
   const uint64_t fixed = (4u << w) + kStaticReserve + ring;
@@ -35,7 +38,10 @@ uint32_t decode_stage_bytes(uint64_t max_chunk, int frac64, int max_groups, int 
     want = (max_chunk * (uint64_t)frac64 / 64 + 1024 + 127) & ~127ull;
   }
   uint32_t st = (uint32_t)(want < kStageMin ? kStageMin : (want > cap ? cap : want));
-  const uint32_t tabs = (uint32_t)(max_groups - 1) * (4u << w) + 256u;
+  const uint32_t lut = 4u << w;
+  uint32_t tabs = max_groups > 1 ? lut + 256u : 0u;
+  const uint32_t all = (uint32_t)(max_groups - 1) * lut + 256u;
+  if (max_groups > 2 && all > tabs + ring) tabs = all - ring;
   return st > tabs ? st : tabs;
 }
 

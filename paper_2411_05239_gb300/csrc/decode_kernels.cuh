@@ -342,6 +342,7 @@ struct Staging {
   uint32_t cap;        // its size in bytes
   uint32_t pf_bytes;   // L2 prefetch window of the fast loops per CTA (bytes)
   uint32_t ring;       // shared-memory address of the raw-word rings (kRingBytes per thread)
+  uint32_t ring_bytes; // their size (0: the launch has none); they follow the stage
   uint64_t* bar;       // its mbarrier
   uint32_t parity;     // phase to wait for next
   uint32_t extra_tx;   // fault injection: bytes expected but never sent (0 normally)
@@ -1176,7 +1177,12 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
         pay_total += (uint32_t)align_up(CI.size[g], 16);
       }
     const uint32_t extra = nhuff > 1 ? (nhuff - 1) * kLutBytes : 0u;
-    const bool stage_payloads = nhuff && pay_total + extra + 32 <= stg.cap;
+    // an FP32 chunk with several coded groups takes no fast loop, so the
+    // raw-word rings after the stage are free for its tables (the launch
+    // sizes stage + rings for three more tables, the stage alone for one)
+    const uint32_t tcap = stg.cap + ((G == 4 && nhuff > 1) ? stg.ring_bytes : 0u);
+    // (the tables start at the first 128-B boundary after the payloads + 32 B)
+    const bool stage_payloads = nhuff && ((pay_total + 32u + 127u) & ~127u) + extra <= tcap;
     uint32_t used = 0, k = 0;
     for (int g = 0; g < G; g++) {
       CI.staged[g] = 0xFFFFFFFFu;
@@ -1192,7 +1198,7 @@ __device__ bool decode_chunk(const Job& J, uint64_t c, Smem& S, uint32_t* lut0, 
     uint32_t lo = (used + 32 + 127) & ~127u;
     for (int g = 0; g < G; g++)
       if (coded_mode(CI.mode[g]) && S.lut_ptr[g] == nullptr) {
-        if (lo + kLutBytes > stg.cap) {  // cannot happen with the launch's sizing; fail closed
+        if (lo + kLutBytes > tcap) {  // cannot happen with the launch's sizing; fail closed
           CI.bad = 1;
           lo = 0;
         }
@@ -1470,6 +1476,11 @@ k_decode(JobRef jr, uint64_t nchunks_total, uint32_t* __restrict__ err,
   stg.cap = stage_cap;
   stg.pf_bytes = pf_bytes;
   stg.ring = smem_u32(dsm + (4u << W) + stage_cap);
+  {
+    uint32_t dyn;  // the launch's dynamic shared memory: table slot | stage | rings
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    stg.ring_bytes = dyn - (4u << W) - stage_cap;
+  }
   stg.bar = &bar;
   stg.parity = 0;
   // debug flag 1 (tests only): expect 16 bytes more than the bulk copies send,

@@ -309,3 +309,67 @@ def test_cluster_split_with_several_items_per_cta(parts, nchunks):
         Z.sync_status()
         pd.close()
         assert torch.equal(out.view(torch.int16), x.view(torch.int16))
+
+
+def fp32_few_values(n: int, seed: int, random_low_bytes: int) -> torch.Tensor:
+    """FP32 values drawn from 37 distinct floats: every byte group has at most
+    37 symbols and is Huffman coded; the lowest `random_low_bytes` bytes of
+    each element are then replaced by uniform bytes (those groups stay raw)."""
+    g = np.random.default_rng(seed)
+    vals = g.standard_normal(37).astype(np.float32).view(np.uint32)
+    b = vals[g.integers(0, 37, size=n)]
+    if random_low_bytes:
+        mask = np.uint32((1 << (8 * random_low_bytes)) - 1)
+        b = (b & ~mask) | (g.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32) & mask)
+    return torch.from_numpy(b.view(np.int32)).view(torch.float32)
+
+
+@pytest.mark.parametrize("coded", [4, 3, 2])
+def test_fp32_chunks_with_several_coded_groups(coded):
+    """An FP32 chunk with more than one Huffman group takes the general loop,
+    with a table per coded group: the spare tables sit in the stage and the
+    raw-word rings behind it, which only the single-coded-group FP32 loop
+    uses, so a launch reserves stage + rings (not the stage alone) for three
+    of them.  Two, three and four coded groups, three full 256 KiB chunks and
+    a ragged one, both CTA sizes and table widths, direct calls and plans,
+    alone and in a batch with BF16 and single-coded-group FP32 tensors."""
+    x = fp32_few_values(3 * 65536 + 1001, 120 + coded, 4 - coded)
+    xs = u8(x)
+    c = Z.compress(x.cuda())
+    s = c.to_bytes()
+    assert s == O.compress(xs, Z.FP32, Z.DEFAULT_CHUNK)
+    for ch in range(3):  # the full chunks (the 4 KB tail is too short to code)
+        m = _modes(s, ch)
+        assert [mode for mode, _ in m] == [1] * coded + [0] * (4 - coded), (ch, m)
+    out = torch.empty_like(x, device="cuda")
+    for nt in (128, 256):
+        for w in (11, 12):
+            out.zero_()
+            Z.batch_decompress([c], [out], tune=Z.tuning(threads=nt, lut_bits=w))
+            Z.sync_status()
+            assert np.array_equal(u8(out), xs), (nt, w)
+            out.zero_()
+            p = Z.plan_decompress([c], [out], tune=Z.tuning(threads=nt, lut_bits=w))
+            p.launch()
+            Z.sync_status()
+            p.close()
+            assert np.array_equal(u8(out), xs), ("plan", nt, w)
+    ys = [x, W.gaussian(2 * 131072 + 3, 0.02, 124), W.gaussian(65536 + 7, 0.05, 125, torch.float32)]
+    cs = [c] + [Z.compress(y.cuda()) for y in ys[1:]]
+    outs = [torch.empty_like(y, device="cuda") for y in ys]
+    for nt in (128, 256):
+        for o in outs:
+            o.zero_()
+        Z.batch_decompress(cs, outs, tune=Z.tuning(threads=nt))
+        Z.sync_status()
+        for y, o in zip(ys, outs):
+            assert np.array_equal(u8(o), u8(y)), nt
+    # FP32 alone, with a single-coded-group tensor first in the batch
+    cs2, ys2 = [cs[2], c], [ys[2], x]
+    outs2 = [torch.empty_like(y, device="cuda") for y in ys2]
+    p = Z.plan_decompress(cs2, outs2)
+    p.launch()
+    Z.sync_status()
+    p.close()
+    for y, o in zip(ys2, outs2):
+        assert np.array_equal(u8(o), u8(y))
