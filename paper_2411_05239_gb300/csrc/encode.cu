@@ -152,23 +152,38 @@ __device__ __forceinline__ void hist16_words(uint32_t hl, uint32_t w0, uint32_t 
 }
 
 // Histograms of chunk c of job J by the NT threads of the CTA, with the
-// lane-indexed counters in sh (G * 256 * 32 + G words); the bin totals go to
-// hist_out[g * 256 + b] and the symbols inside all-zero vectors to zs_out[g]
-// (global or shared memory).  Ends with every thread past a barrier.
+// lane-indexed counters in sh (hist_counter_words(DT) + G words); the bin
+// totals go to hist_out[g * 256 + b] and the symbols inside all-zero vectors
+// to zs_out[g] (global or shared memory).  Ends with every thread past a
+// barrier.  FP32 keeps two 16-bit counters per word (bins b and b + 128 of a
+// group and lane, low and high half): its four groups then take the 64 KiB
+// that two 16-bit groups take, three CTAs per SM instead of one.  A word
+// counts at most kPkRound / 8 symbols per half in a round of kPkRound vectors
+// (lane l of every warp adds into it: NT / 32 threads of kPkRound / NT
+// vectors each, 4 symbols per vector and group), so chunks of more than
+// kPkRound vectors are counted in rounds, each round's halves added into
+// per-thread totals before the next.
+constexpr uint32_t kPkRound = 1u << 18;  // vectors (4 MiB) per round: <= 32768 per half
+template <int DT>
+__host__ __device__ constexpr int hist_counter_words() {
+  return DT == ZIPNN_FP32 ? 4 * 128 * 32 : (DT == ZIPNN_U8 ? 1 : 2) * 256 * 32;
+}
 template <int DT, int NT = kHistThreads>
 __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* hist_out,
                            uint32_t* zs_out) {
   constexpr int G = DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2);
   constexpr int V = 16 / (DT == ZIPNN_FP32 ? 4 : (DT == ZIPNN_U8 ? 1 : 2));
   constexpr int ES = 16 / V;
+  constexpr bool PK = DT == ZIPNN_FP32;
+  constexpr int CW = hist_counter_words<DT>();
   const int tid = threadIdx.x, lane = tid & 31;
   const uint64_t off = c * J.chunk_bytes;
   const uint64_t nb = min((uint64_t)J.chunk_bytes, J.nbytes - off);
   const uint8_t* src = J.src + off;
   const uint8_t* base = J.base ? J.base + off : nullptr;
 
-  uint32_t* zcnt = sh + G * 256 * 32;  // per group: symbols inside all-zero vectors
-  for (int i = tid; i < G * 256 * 32 + G; i += NT) sh[i] = 0;
+  uint32_t* zcnt = sh + CW;  // per group: symbols inside all-zero vectors
+  for (int i = tid; i < CW + G; i += NT) sh[i] = 0;
   __syncthreads();
   uint32_t zc[G];
 #pragma unroll
@@ -215,40 +230,82 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
     }
     vstart = nfast + tid;
   }
-  for (uint64_t v0 = vstart; v0 < nvec; v0 += (uint64_t)NT * U) {
-    uint4 a[U];
+  // packed counters: running totals of this thread's words (bins b, b + 128)
+  constexpr int PKW = PK ? (G * 128 + NT - 1) / NT : 1;
+  uint32_t tot_lo[PKW], tot_hi[PKW];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const uint64_t v = v0 + (uint64_t)u * NT;
-      a[u] = v < nvec ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
-    }
+  for (int i = 0; i < PKW; i++) tot_lo[i] = tot_hi[i] = 0;
+  auto add_packed = [&]() {
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const uint64_t v = v0 + (uint64_t)u * NT;
-      if (v >= nvec) break;
-      uint32_t g[4][4];
-      split_vec(DT, a[u], g);
-      const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
-#pragma unroll
-      for (int gg = 0; gg < G; gg++) {
-        uint32_t any = 0;
-#pragma unroll
-        for (int q = 0; q < V / 4; q++) any |= g[gg][q];
-        if (!any) zc[gg] += (uint32_t)valid;   // bytes past the tail were loaded as zero
+    for (int i = 0; i < PKW; i++) {
+      const int bw = tid + i * NT;
+      if (bw < G * 128) {
+#pragma unroll 8
+        for (int l = 0; l < 32; l++) {
+          const uint32_t w = sh[bw * 32 + ((l + bw) & 31)];
+          tot_lo[i] += w & 0xFFFFu;
+          tot_hi[i] += w >> 16;
+        }
       }
-      if (valid == V) {
+    }
+  };
+  // rounds of kPkRound vectors with packed counters, else one round; the
+  // round bounds are the same in every thread, so all of them meet the
+  // barriers between rounds
+  const uint64_t vb = vstart - (uint64_t)tid;
+  const uint64_t rlen = PK ? (uint64_t)kPkRound : (nvec > vb ? nvec - vb : 1u);
+  for (uint64_t r0 = vb; r0 < nvec; r0 += rlen) {
+    if (PK && r0 != vb) {
+      // a round is complete: fold the halves into the totals, clear the words
+      __syncthreads();
+      add_packed();
+      __syncthreads();
+      for (int i = tid; i < CW; i += NT) sh[i] = 0;
+      __syncthreads();
+    }
+    const uint64_t rend = min(nvec, r0 + rlen);
+    for (uint64_t v0 = r0 + (uint64_t)tid; v0 < rend; v0 += (uint64_t)NT * U) {
+      uint4 a[U];
 #pragma unroll
-        for (int gg = 0; gg < G; gg++)
+      for (int u = 0; u < U; u++) {
+        const uint64_t v = v0 + (uint64_t)u * NT;
+        a[u] = v < rend ? load_vec(src, base, v, nb) : make_uint4(0, 0, 0, 0);
+      }
 #pragma unroll
-          for (int k = 0; k < V; k++)
-            atomicAdd(&hl[(gg * 256 + __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3))) * 32], 1u);
-      } else {
+      for (int u = 0; u < U; u++) {
+        const uint64_t v = v0 + (uint64_t)u * NT;
+        if (v >= rend) break;
+        uint32_t g[4][4];
+        split_vec(DT, a[u], g);
+        const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
 #pragma unroll
-        for (int gg = 0; gg < G; gg++)
+        for (int gg = 0; gg < G; gg++) {
+          uint32_t any = 0;
 #pragma unroll
-          for (int k = 0; k < V; k++)
-            if (k < valid)
-              atomicAdd(&hl[(gg * 256 + __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3))) * 32], 1u);
+          for (int q = 0; q < V / 4; q++) any |= g[gg][q];
+          if (!any) zc[gg] += (uint32_t)valid;   // bytes past the tail were loaded as zero
+        }
+        // symbol b of group gg: word (gg * 256 + b) * 32 + lane, or with packed
+        // counters word (gg * 128 + b % 128) * 32 + lane, half b / 128
+        auto count = [&](int gg, uint32_t b) {
+          if constexpr (PK)
+            atomicAdd(&hl[(gg * 128 + (b & 127u)) * 32], (b & 128u) ? 0x10000u : 1u);
+          else
+            atomicAdd(&hl[(gg * 256 + b) * 32], 1u);
+        };
+        if (valid == V) {
+#pragma unroll
+          for (int gg = 0; gg < G; gg++)
+#pragma unroll
+            for (int k = 0; k < V; k++)
+              count(gg, __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3)));
+        } else {
+#pragma unroll
+          for (int gg = 0; gg < G; gg++)
+#pragma unroll
+            for (int k = 0; k < V; k++)
+              if (k < valid) count(gg, __byte_perm(g[gg][k >> 2], 0, 0x4440 + (k & 3)));
+        }
       }
     }
   }
@@ -262,11 +319,23 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
   if (tid < G) zs_out[tid] = zcnt[tid];
   // bin totals: thread b sums the 32 lane counters of bin b (rotated start so
   // the 32 threads of a warp read 32 different banks)
-  for (int b = tid; b < G * 256; b += NT) {
-    uint32_t s = 0;
+  if constexpr (PK) {
+    add_packed();
+#pragma unroll
+    for (int i = 0; i < PKW; i++) {
+      const int bw = tid + i * NT;
+      if (bw < G * 128) {
+        hist_out[(bw >> 7) * 256 + (bw & 127)] = tot_lo[i];
+        hist_out[(bw >> 7) * 256 + (bw & 127) + 128] = tot_hi[i];
+      }
+    }
+  } else {
+    for (int b = tid; b < G * 256; b += NT) {
+      uint32_t s = 0;
 #pragma unroll 8
-    for (int i = 0; i < 32; i++) s += sh[b * 32 + ((i + b) & 31)];
-    hist_out[b] = s;
+      for (int i = 0; i < 32; i++) s += sh[b * 32 + ((i + b) & 31)];
+      hist_out[b] = s;
+    }
   }
   __syncthreads();
 }
@@ -294,7 +363,12 @@ k_hist(JobRef jr, uint32_t* __restrict__ hist, uint32_t* __restrict__ zsyms) {
   }
 }
 
-static int hist_smem_bytes(int max_groups) { return max_groups * (256 * 32 + 1) * 4; }
+// counters + zero-symbol words: a launch that may hold FP32 chunks (packed
+// counters) needs as much as one of 16-bit chunks
+static int hist_smem_bytes(int max_groups) {
+  const int g = max_groups > 2 ? 2 : max_groups;
+  return (g * 256 * 32 + max_groups) * 4;
+}
 
 // ---------------------------------------------------------------------------
 // k_build: one warp per group-chunk.
