@@ -151,6 +151,25 @@ __device__ __forceinline__ void hist16_words(uint32_t hl, uint32_t w0, uint32_t 
   for (int k = 0; k < 4; k++) red_shared_inc(hl8 + (__byte_perm(r, 0, 0x4440 + k) << 7));
 }
 
+// Shared-memory add of v without a result, on a 32-bit shared-window address.
+__device__ __forceinline__ void red_shared_add(uint32_t saddr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+
+// Histogram of one FP32 element x with packed counters: group g's counter of
+// bin b for this lane is the half b / 128 of the word at byte g * 16384 +
+// (b % 128) * 128 from hl (the shared-window address of lane 0's word of
+// group 0, bin 0, plus 4 * lane).  With g0 = x >> 23 & 0xFF, g1 = (x >> 24 &
+// 0x80) | (x >> 16 & 0x7F), g2 = x >> 8 & 0xFF and g3 = x & 0xFF, each word
+// offset is a shift and a mask of x and each half the bit 30, 31, 15 or 7
+// of x: no byte is extracted.
+__device__ __forceinline__ void hist32_elem(uint32_t hl, uint32_t x) {
+  red_shared_add(hl + ((x >> 16) & 0x3F80u), (x & 0x40000000u) ? 0x10000u : 1u);
+  red_shared_add(hl + 0x4000u + ((x >> 9) & 0x3F80u), (x & 0x80000000u) ? 0x10000u : 1u);
+  red_shared_add(hl + 0x8000u + ((x >> 1) & 0x3F80u), (x & 0x8000u) ? 0x10000u : 1u);
+  red_shared_add(hl + 0xC000u + ((x << 7) & 0x3F80u), (x & 0x80u) ? 0x10000u : 1u);
+}
+
 // Histograms of chunk c of job J by the NT threads of the CTA, with the
 // lane-indexed counters in sh (hist_counter_words(DT) + G words); the bin
 // totals go to hist_out[g * 256 + b] and the symbols inside all-zero vectors
@@ -189,6 +208,7 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
 #pragma unroll
   for (int g = 0; g < G; g++) zc[g] = 0;
   uint32_t* hl = sh + lane;
+  const uint32_t hls = (uint32_t)__cvta_generic_to_shared(hl);
   const uint64_t nvec = (nb + 15) / 16;
   const uint64_t m = nb / ES;
   constexpr int U = 4;  // vectors in flight per thread
@@ -196,7 +216,6 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
   if constexpr (DT == ZIPNN_BF16 || DT == ZIPNN_FP16) {
     // whole rounds of NT * U vectors of whole 16-bit elements
     const uint64_t nfast = nb % 16 ? 0 : nvec / ((uint64_t)NT * U) * (NT * U);
-    const uint32_t hls = (uint32_t)__cvta_generic_to_shared(hl);
     // the second round, up to where the in-loop prefetches start
     for (uint64_t vp = tid + (uint64_t)NT * U; vp < nfast && vp < 2ull * NT * U;
          vp += NT) {
@@ -275,9 +294,23 @@ __device__ void hist_chunk(const Job& J, uint64_t c, uint32_t* sh, uint32_t* his
       for (int u = 0; u < U; u++) {
         const uint64_t v = v0 + (uint64_t)u * NT;
         if (v >= rend) break;
+        const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
+        if constexpr (PK) {
+          if (valid == V) {  // four whole elements
+            hist32_elem(hls, a[u].x);
+            hist32_elem(hls, a[u].y);
+            hist32_elem(hls, a[u].z);
+            hist32_elem(hls, a[u].w);
+            const uint32_t any = a[u].x | a[u].y | a[u].z | a[u].w;
+            if (!(any & 0x7F800000u)) zc[0] += 4;
+            if (!(any & 0x807F0000u)) zc[1 % G] += 4;
+            if (!(any & 0x0000FF00u)) zc[2 % G] += 4;
+            if (!(any & 0x000000FFu)) zc[3 % G] += 4;
+            continue;
+          }
+        }
         uint32_t g[4][4];
         split_vec(DT, a[u], g);
-        const int valid = (v + 1) * V <= m ? V : (int)(m - v * V);
 #pragma unroll
         for (int gg = 0; gg < G; gg++) {
           uint32_t any = 0;
