@@ -347,7 +347,8 @@ extern "C" zipnn_status zipnn_batch_compress_into_ex(
   cudaError_t e = g_ring.h2d(d_jobs, bp.jobs.data(), sizeof(Job) * bp.jobs.size(), st);
   if (e == cudaSuccess)
     e = launch_encode(d_jobs, nullptr, count, bp.nchunks, bp.ngc, s, err, st, bp.max_groups,
-                      bp.max_lanes, bp.uniform, skip != 0, (int)encoder, dbg);
+                      bp.max_lanes, bp.uniform, skip != 0, (int)encoder, dbg,
+                      any_base(d_bases, count));
   return cuda_status(e);
 }
 

@@ -812,7 +812,8 @@ struct PackSmem {
   uint32_t ptab[1024];  // pair table of the 16-bit pass A (pack_pair_a)
 };
 
-// Exclusive scan of a[0..n) in place (block-wide); n <= kPackMaxUnits.
+// Exclusive scan of a[0..n) in place (block-wide), the total into a[n];
+// n <= kPackMaxUnits.
 __device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* wsum) {
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t per = (n + nthr - 1) / nthr;
@@ -844,6 +845,7 @@ __device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* wsum) {
     a[i] = run;
     run += b;
   }
+  if (b0 < b1 && b1 == n) a[n] = run;  // the total, after the last offset
   __syncthreads();
 }
 
@@ -1325,11 +1327,11 @@ __device__ __forceinline__ void write_map_entries(const Job& J, uint64_t c, cons
 // Packing of chunk c whose mode records (S.meta), payload offsets (S.off) and
 // codes of its coded groups (S.codes) are in shared memory and whose map
 // entries have been written; tabp[g] points to group g's table bytes.
-template <int DT>
+template <int DT, bool S2 = false>
 __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
                                 const uint8_t* const* tabp);
 
-template <int DT>
+template <int DT, bool S2 = false>
 __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
                            const uint32_t* codes, const uint8_t* tabs, const GcMeta* meta,
                            const uint64_t* offs) {
@@ -1360,7 +1362,7 @@ __device__ void pack_chunk(const Job& J, uint64_t c, PackSmem& S, uint32_t* slot
   const uint8_t* tabp[4] = {nullptr, nullptr, nullptr, nullptr};  // null: written
 #pragma unroll
   for (int g = 1; g < G; g++) tabp[g] = tabs + (gc0 + g) * kTabBytes;
-  pack_chunk_core<DT>(J, c, S, slots, tabp);
+  pack_chunk_core<DT, S2>(J, c, S, slots, tabp);
 }
 
 // Pass B of a chunk whose group 0 is its only coded group and whose units
@@ -1401,7 +1403,7 @@ __device__ __forceinline__ void pass_b_whole(const PackSmem& S, const uint32_t* 
   for (uint32_t w = ((tot + 31) >> 5) + tid; w < capw; w += nthr) words[w] = 0;
 }
 
-template <int DT>
+template <int DT, bool S2>
 __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t* slots,
                                 const uint8_t* const* tabp) {
   constexpr int G = PTraits<DT>::G, V = PTraits<DT>::V, ES = 16 / V;
@@ -1450,13 +1452,37 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
 
   // The first Huffman group is encoded once, in pass A, into per-unit slots in
   // shared memory (slot_cap words each, odd so that neighbouring slots fall in
-  // different banks); pass B only shifts the slot words into place.
-  int sg = -1;
+  // different banks); pass B only shifts the slot words into place.  With S2
+  // (the packer of launches that hold deltas, whose chunks often code both
+  // 16-bit groups) the second Huffman group is staged as well, into slots of
+  // slot_cap1 words after the first group's, when the two groups' average
+  // words per unit (from their payload sizes) leave at least 4 of a unit's
+  // share of the slot area; the rest is split evenly between them.  Pass B
+  // encodes from the input again only the groups not staged and the units
+  // whose slot overflowed.
+  int sg = -1, sg1 = -1;
 #pragma unroll
-  for (int g = G - 1; g >= 0; g--)
-    if (huff >> g & 1) sg = g;
-  uint32_t slot_cap = gdiv(kPackSlotWords, units);
+  for (int g = 0; g < G; g++)
+    if (huff >> g & 1) {
+      if (sg < 0) sg = g;
+      else if (S2 && sg1 < 0) sg1 = g;
+    }
+  uint32_t slot_cap = gdiv(kPackSlotWords, units), slot_cap1 = 0;
+  if (S2 && sg1 >= 0) {
+    const uint64_t uw = 32ull * units;
+    const uint32_t n0 = (uint32_t)((8ull * S.meta[sg].size + uw - 1) / uw);
+    const uint32_t n1 = (uint32_t)((8ull * S.meta[sg1].size + uw - 1) / uw);
+    if (n0 + n1 + 4u <= slot_cap) {
+      const uint32_t left = (slot_cap - n0 - n1) / 2u;
+      slot_cap1 = n1 + left;
+      slot_cap = n0 + left;
+      if (!(slot_cap1 & 1u)) slot_cap1--;
+    } else {
+      sg1 = -1;  // encoded from the input in pass B, as a third group would be
+    }
+  }
   if (!(slot_cap & 1u)) slot_cap--;
+  const uint32_t slots1 = smem_u32(slots) + 4u * units * slot_cap;  // second group's slots
   const bool fast_a = sg == 0 && huff == 1u && sparse == 0 && nb == J.chunk_bytes &&
                       gmod((uint32_t)nvec, T) == 0 && gmod((uint32_t)nvt, R) == 0 &&
                       T <= (uint32_t)nthr;
@@ -1479,13 +1505,15 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
     uint32_t bits[G];
 #pragma unroll
     for (int g = 0; g < G; g++) bits[g] = 0;
-    SlotWriter sw;
+    SlotWriter sw, sw1;
     sw.slot = smem_u32(slots) + 4u * (t * R + k) * slot_cap;
-    sw.acc = 0;
-    sw.nacc = 0;
-    sw.wi = 0;
+    sw1.slot = slots1 + 4u * (t * R + k) * slot_cap1;
+    sw.acc = sw1.acc = 0;
+    sw.nacc = sw1.nacc = 0;
+    sw.wi = sw1.wi = 0;
     sw.cap = slot_cap;
-    sw.bits = 0;
+    sw1.cap = slot_cap1;
+    sw.bits = sw1.bits = 0;
     const uint64_t i1 = min(nvt, (uint64_t)(k + 1) * per);
     constexpr int U = 2;  // vectors in flight per thread
     for (uint64_t i0 = (uint64_t)k * per; i0 < i1; i0 += U) {
@@ -1520,22 +1548,28 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
           }
           if (!any) continue;
         }
-        if (g == sg) {
+        // this vector's symbols of group g into slot writer w
+        auto stage = [&](SlotWriter& w) {
           if (full) {
 #pragma unroll
             for (int q = 0; q < V / 4; q++) {
               uint32_t len;
               const uint64_t x = join4(smem_u32(S.codes[g]), g4[g][q], len);
-              sw.put64(x, len);
+              w.put64(x, len);
             }
           } else {
 #pragma unroll
             for (int q = 0; q < V; q++)
               if (q < valid) {
                 const uint32_t cl = code_of(smem_u32(S.codes[g]), g4[g][q >> 2], q & 3);
-                sw.put(cl & 0xFFFFu, cl >> 16);
+                w.put(cl & 0xFFFFu, cl >> 16);
               }
           }
+        };
+        if (g == sg) {
+          stage(sw);
+        } else if (S2 && g == sg1) {
+          stage(sw1);
         } else if (huff >> g & 1) {
           if (full) {
 #pragma unroll
@@ -1566,6 +1600,12 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
       for (int g = 0; g < G; g++)
         if (g == sg) bits[g] = sw.bits;
       S.sbits[t * R + k] = sw.bits;
+    }
+    if (S2 && sg1 >= 0) {
+      sw1.finish();
+#pragma unroll
+      for (int g = 0; g < G; g++)
+        if (g == sg1) bits[g] = sw1.bits;
     }
 #pragma unroll
     for (int g = 0; g < G; g++) S.part[g][t * R + k] = bits[g];
@@ -1661,16 +1701,22 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
   for (uint32_t u = tid; u < units; u += nthr) {
     const uint32_t t = gmod(u, T), k = gdiv(u, T);
     const uint32_t ui = t * R + k;
-    // (1) slot-staged group: shift the unit's slot words to its bit offset
-    bool refill = false;
-    if (sg >= 0) {
-      const uint32_t nbits = S.sbits[ui];
-      if (nbits > slot_cap * 32u) {
-        refill = true;  // slot overflowed: re-encode below from the input
+    // (1) slot-staged groups: shift the unit's slot words to its bit offset
+    // (its bits: the staged count, or the next unit's offset minus its own)
+    bool refill = false, refill1 = false;
+#pragma unroll
+    for (int s1 = 0; s1 < (S2 ? 2 : 1); s1++) {
+      const int gs = s1 ? sg1 : sg;
+      if (gs < 0) continue;
+      const uint32_t o = S.part[gs][ui];
+      const uint32_t nbits = s1 ? S.part[gs][ui + 1] - o : S.sbits[ui];
+      const uint32_t cap = s1 ? slot_cap1 : slot_cap;
+      if (nbits > cap * 32u) {
+        (s1 ? refill1 : refill) = true;  // slot overflowed: re-encode below from the input
       } else if (nbits) {
-        uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[sg] + S.hsz[sg]);
-        const uint32_t sl = smem_u32(slots) + 4u * ui * slot_cap;
-        const uint32_t o = S.part[sg][ui], sh = o & 31, w0 = o >> 5;
+        uint32_t* words = reinterpret_cast<uint32_t*>(out + P + S.off[gs] + S.hsz[gs]);
+        const uint32_t sl = (s1 ? slots1 : smem_u32(slots)) + 4u * ui * cap;
+        const uint32_t sh = o & 31, w0 = o >> 5;
         const uint32_t end = o + nbits, wl = (end - 1) >> 5;
         const uint32_t nsw = (nbits + 31) >> 5;
         uint32_t prev = 0;
@@ -1679,23 +1725,24 @@ __device__ void pack_chunk_core(const Job& J, uint64_t c, PackSmem& S, uint32_t*
           const uint32_t cur = i < nsw ? lds32v(sl + 4u * i) : 0u;
           const uint32_t word = __funnelshift_r(cur, prev, sh);
           prev = cur;
-          if (w >= S.capw[sg]) break;  // never taken for a consistent input
+          if (w >= S.capw[gs]) break;  // never taken for a consistent input
           if ((w == w0 && sh) || (w == wl && (end & 31))) atomicOr(&words[w], word);
           else words[w] = word;
         }
       }
     }
     // (2) other Huffman groups (and overflowed units): encode from the input
-    bool any = refill;
+    bool any = refill || refill1;
 #pragma unroll
     for (int g = 0; g < G; g++)
-      if ((huff >> g & 1) && g != sg) any = true;
+      if ((huff >> g & 1) && g != sg && g != sg1) any = true;
     if (!any) continue;
     BitWriter bw[G];
     bool emit[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      emit[g] = (huff >> g & 1) && (g != sg || refill);
+      emit[g] = (huff >> g & 1) &&
+                ((g != sg && g != sg1) || (g == sg && refill) || (g == sg1 && refill1));
       bw[g].words = reinterpret_cast<uint32_t*>(out + P + S.off[g] + S.hsz[g]);
       const uint32_t st = emit[g] ? S.part[g][ui] : 0u;
       bw[g].acc = 0;
@@ -1763,7 +1810,7 @@ __device__ void write_header(const Job& J, uint64_t total) {
   for (int k = 48; k < 64; k++) h[k] = 0;
 }
 
-template <int DTS>
+template <int DTS, bool S2>
 __global__ void __launch_bounds__(kPackThreads, 2)
 k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
        const uint8_t* __restrict__ tabs, const GcMeta* __restrict__ meta,
@@ -1787,14 +1834,14 @@ k_pack(JobRef jr, uint64_t nchunks_total, const uint32_t* __restrict__ codes,
   if (totals[j] > J.out_capacity) return;
   const uint64_t c = chunk - J.chunk_begin;
   if (DTS >= 0) {
-    pack_chunk<(DTS < 0 ? 0 : DTS)>(J, c, S, slots, codes, tabs, meta, offs);
+    pack_chunk<(DTS < 0 ? 0 : DTS), S2>(J, c, S, slots, codes, tabs, meta, offs);
     return;
   }
   switch (J.dtype) {
-    case ZIPNN_BF16: pack_chunk<ZIPNN_BF16>(J, c, S, slots, codes, tabs, meta, offs); break;
-    case ZIPNN_FP16: pack_chunk<ZIPNN_FP16>(J, c, S, slots, codes, tabs, meta, offs); break;
-    case ZIPNN_FP32: pack_chunk<ZIPNN_FP32>(J, c, S, slots, codes, tabs, meta, offs); break;
-    default: pack_chunk<ZIPNN_U8>(J, c, S, slots, codes, tabs, meta, offs); break;
+    case ZIPNN_BF16: pack_chunk<ZIPNN_BF16, S2>(J, c, S, slots, codes, tabs, meta, offs); break;
+    case ZIPNN_FP16: pack_chunk<ZIPNN_FP16, S2>(J, c, S, slots, codes, tabs, meta, offs); break;
+    case ZIPNN_FP32: pack_chunk<ZIPNN_FP32, S2>(J, c, S, slots, codes, tabs, meta, offs); break;
+    default: pack_chunk<ZIPNN_U8, S2>(J, c, S, slots, codes, tabs, meta, offs); break;
   }
 }
 
@@ -2072,12 +2119,19 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
 
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st, int uniform_dtype) {
+                                  cudaStream_t st, int uniform_dtype, bool any_delta) {
   JobRef r = make_ref(d_jobs, njobs, h_one);
   (void)max_lanes;
-  if (h_one) uniform_dtype = h_one->dtype;
-  auto kp = pick(uniform_dtype, k_pack<ZIPNN_BF16>, k_pack<ZIPNN_FP16>, k_pack<ZIPNN_FP32>,
-                 k_pack<ZIPNN_U8>, k_pack<-1>);
+  if (h_one) {
+    uniform_dtype = h_one->dtype;
+    any_delta = h_one->base != nullptr;
+  }
+  // launches that hold deltas stage two coded groups in pass A (S2)
+  auto kp = any_delta ? pick(uniform_dtype, k_pack<ZIPNN_BF16, true>, k_pack<ZIPNN_FP16, true>,
+                             k_pack<ZIPNN_FP32, true>, k_pack<ZIPNN_U8, true>, k_pack<-1, true>)
+                      : pick(uniform_dtype, k_pack<ZIPNN_BF16, false>, k_pack<ZIPNN_FP16, false>,
+                             k_pack<ZIPNN_FP32, false>, k_pack<ZIPNN_U8, false>,
+                             k_pack<-1, false>);
   const int ps = (int)(kPackSlotWords * 4);
   cudaError_t ea = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
   if (ea == cudaSuccess)
@@ -2132,7 +2186,7 @@ cudaError_t launch_encode_fused(const Job* d_jobs, const Job* h_one, int njobs,
 cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64_t nchunks_total,
                           uint64_t ngc_total, const EncodeScratch& s, uint32_t* d_err,
                           cudaStream_t st, int max_groups, int max_lanes, int uniform_dtype,
-                          bool any_skip, int encoder, uint32_t debug_flags) {
+                          bool any_skip, int encoder, uint32_t debug_flags, bool any_delta) {
   const int dt = h_one ? h_one->dtype : uniform_dtype;
   const bool skip = h_one ? h_one->skip != 0 : any_skip;
   // (a launch of empty tensors only has no chunk, hence no histogram area to
@@ -2144,7 +2198,7 @@ cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64
                                            d_err, st, max_groups, uniform_dtype);
   if (e == cudaSuccess)
     e = launch_encode_pack_ex(d_jobs, h_one, njobs, nchunks_total, max_lanes, s, st,
-                              uniform_dtype);
+                              uniform_dtype, any_delta);
   return e;
 }
 

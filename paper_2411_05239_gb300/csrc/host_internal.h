@@ -31,9 +31,18 @@ cudaError_t launch_encode_analyse_ex(const Job* d_jobs, const Job* h_one, int nj
                                      uint64_t nchunks_total, uint64_t ngc_total,
                                      const EncodeScratch& s, uint32_t* d_err, cudaStream_t st,
                                      int max_groups, int uniform_dtype);
+// True when some of the count bases is given (a batch that holds deltas).
+inline bool any_base(const void* const* d_bases, int count) {
+  if (!d_bases) return false;
+  for (int i = 0; i < count; i++)
+    if (d_bases[i]) return true;
+  return false;
+}
+// any_delta: some job has a base (its packer stages two coded groups per
+// chunk in pass A); taken from the job itself when h_one is given.
 cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs,
                                   uint64_t nchunks_total, int max_lanes, const EncodeScratch& s,
-                                  cudaStream_t st, int uniform_dtype);
+                                  cudaStream_t st, int uniform_dtype, bool any_delta = false);
 // The whole encoder: the four kernels above (encoder == 0), or the
 // single-pass kernel (histogram, code build, offsets by look-back, packing:
 // one launch after a memset of its look-back words) when encoder == 1 and
@@ -42,7 +51,8 @@ cudaError_t launch_encode_pack_ex(const Job* d_jobs, const Job* h_one, int njobs
 cudaError_t launch_encode(const Job* d_jobs, const Job* h_one, int njobs, uint64_t nchunks_total,
                           uint64_t ngc_total, const EncodeScratch& s, uint32_t* d_err,
                           cudaStream_t st, int max_groups, int max_lanes, int uniform_dtype,
-                          bool any_skip, int encoder, uint32_t debug_flags = 0);
+                          bool any_skip, int encoder, uint32_t debug_flags = 0,
+                          bool any_delta = false);
 bool fused_encoder_applies(int dtype, bool any_skip);
 
 // Decoder (decode.cu): one persistent launch over all chunks of the jobs.

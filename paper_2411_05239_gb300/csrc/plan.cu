@@ -323,7 +323,7 @@ zipnn_status zipnn_plan_compress(const void* const* d_srcs, const void* const* d
   if (e != cudaSuccess) return fail(p, e);
   e = capture(p, [&](cudaStream_t cs) {
     return launch_encode(d_jobs, nullptr, count, nch, ngc, s, err, cs, max_groups, max_lanes,
-                         uniform, false, 0);
+                         uniform, false, 0, 0, any_base(d_bases, count));
   });
   if (e != cudaSuccess) return fail(p, e);
   *out = p;
