@@ -469,12 +469,58 @@ __device__ void pm_lengths(BuildSmem& S, const uint32_t cnt[8], uint32_t nz, int
     }
   }
   __syncwarp();
-  for (uint32_t i = lane; i < nz; i += 32) {
-    const uint32_t key = S.keys[i];
-    uint32_t r = 0;
-    for (uint32_t q = 0; q < nz; q++) r += (S.keys[q] < key);
-    S.leafw[r] = key >> 8;
-    S.leafsym[r] = (uint8_t)(255 - (key & 0xFFu));
+  if (nz <= 96) {
+    for (uint32_t i = lane; i < nz; i += 32) {
+      const uint32_t key = S.keys[i];
+      uint32_t r = 0;
+      for (uint32_t q = 0; q < nz; q++) r += (S.keys[q] < key);
+      S.leafw[r] = key >> 8;
+      S.leafsym[r] = (uint8_t)(255 - (key & 0xFFu));
+    }
+  } else {
+    // many leaves: a bitonic sort of the keys padded to 256 with the largest
+    // key (element i = 8 * lane + r in register r of the lane; partners 8 or
+    // more apart are exchanged by shuffles), instead of nz compares per key
+    uint32_t v[8];
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      const uint32_t i = 8u * lane + r;
+      v[r] = i < nz ? S.keys[i] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        if (stride >= 8) {
+          const int ls = stride >> 3;  // partner lane distance
+#pragma unroll
+          for (int r = 0; r < 8; r++) {
+            const uint32_t i = 8u * lane + r;
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v[r], ls);
+            const bool up = (i & (uint32_t)size) == 0, lower = (lane & ls) == 0;
+            v[r] = (lower == up) ? min(v[r], o) : max(v[r], o);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 8; r++) {
+            if (r & stride) continue;
+            const int q = r | stride;
+            const bool up = ((8u * lane + r) & (uint32_t)size) == 0;
+            const uint32_t a = v[r], b = v[q];
+            v[r] = up ? min(a, b) : max(a, b);
+            v[q] = up ? max(a, b) : min(a, b);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      const uint32_t i = 8u * lane + r;
+      if (i < nz) {
+        S.leafw[i] = v[r] >> 8;
+        S.leafsym[i] = (uint8_t)(255 - (v[r] & 0xFFu));
+      }
+    }
   }
   for (int i = lane; i < kMaxLen * 16; i += 32) (&S.leafbits[0][0])[i] = 0;
   __syncwarp();
@@ -491,18 +537,49 @@ __device__ void pm_lengths(BuildSmem& S, const uint32_t cnt[8], uint32_t nz, int
     const int np = sp >> 1;
     for (int k = lane; k < np; k += 32) S.pk[k] = prev[2 * k] + prev[2 * k + 1];
     __syncwarp();
-    for (int k = lane; k < np; k += 32) {
-      uint32_t w = S.pk[k];
-      cur[k + upper_bound_u32(S.leafw, n, w)] = w;      // after leaves of equal weight
-    }
-    for (int k = lane; k < n; k += 32) {
-      uint32_t w = S.leafw[k];
-      int pos = k + lower_bound_u32(S.pk, np, w);
-      cur[pos] = w;
-      atomicOr(&S.leafbits[lvl][pos >> 5], 1u << (pos & 31));
+    // the merged list, a leaf before a package of equal weight.  Few leaves:
+    // each package and leaf finds its position by a binary search in the
+    // other list.  Many (more than 96): merge path, lane l writes outputs
+    // [l * seg, (l + 1) * seg), one binary search finding how many leaves
+    // precede its first output, then a sequential merge that marks its
+    // leaves' positions (at most two bitmap words)
+    const int total = n + np, seg = (total + 31) >> 5;
+    const int d0 = min(total, lane * seg), d1 = min(total, d0 + seg);
+    if (n <= 96) {
+      for (int k = lane; k < np; k += 32) {
+        uint32_t w = S.pk[k];
+        cur[k + upper_bound_u32(S.leafw, n, w)] = w;      // after leaves of equal weight
+      }
+      for (int k = lane; k < n; k += 32) {
+        uint32_t w = S.leafw[k];
+        int pos = k + lower_bound_u32(S.pk, np, w);
+        cur[pos] = w;
+        atomicOr(&S.leafbits[lvl][pos >> 5], 1u << (pos & 31));
+      }
+    } else if (d0 < d1) {
+      int lo = max(0, d0 - np), hi = min(d0, n);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (S.leafw[mid] <= S.pk[d0 - mid - 1]) lo = mid + 1; else hi = mid;
+      }
+      int li = lo, pi = d0 - lo;
+      uint64_t mask = 0;  // leaf positions from word d0 / 32
+      const int off = d0 & 31;
+      for (int d = d0; d < d1; d++) {
+        const bool leaf = pi >= np || (li < n && S.leafw[li] <= S.pk[pi]);
+        cur[d] = leaf ? S.leafw[li] : S.pk[pi];
+        if (leaf) {
+          mask |= 1ull << (off + d - d0);
+          li++;
+        } else {
+          pi++;
+        }
+      }
+      if ((uint32_t)mask) atomicOr(&S.leafbits[lvl][d0 >> 5], (uint32_t)mask);
+      if (mask >> 32) atomicOr(&S.leafbits[lvl][(d0 >> 5) + 1], (uint32_t)(mask >> 32));
     }
     __syncwarp();
-    sp = n + np;
+    sp = total;
     prev = cur;
     cur_buf ^= 1;
   }
