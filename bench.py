@@ -498,6 +498,8 @@ def run_gb300(args):
                "copies_alone_ms": min(conts_ms),
                "h2d_bound_gbs": world * bound,
                "frac_of_h2d_bound": orig / e2e_s / 1e9 / bound,
+               "frac_of_h2d_bound_median_step": orig / (steps_ms[len(steps_ms) // 2] / 1e3) / 1e9
+               / bound,
                "steps": args.e2e_steps, "ms_per_step": e2e_s * 1e3,
                "step_ms_min": steps_ms[0], "step_ms_median": steps_ms[len(steps_ms) // 2],
                "step_ms_max": steps_ms[-1],
