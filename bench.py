@@ -1109,7 +1109,7 @@ def main(argv=None):
                     help="0 = four-kernel encoder, 1 = single-pass encoder where it applies")
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick chunk size, lanes, table width, CTAs/SM on a sample first")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-segment-mb", type=int, default=512,
                     help="container bytes per decode launch in the load plan")
     ap.add_argument("--per-tensor", type=int, default=1)
