@@ -131,3 +131,51 @@ def test_single_pass_encoder_takes_the_same_paths():
     Z.sync_status()
     for x, c in zip(xs, a.containers()):
         assert c.to_bytes() == O.compress(u8(x.cpu()), Z.BF16, 262144, 512)
+
+
+def _few_values_fp32(n: int, seed: int) -> np.ndarray:
+    g = np.random.default_rng(seed)
+    vals = g.standard_normal(29).astype(np.float32).view(np.uint32)
+    return vals[g.integers(0, 29, size=n)]
+
+
+@pytest.mark.parametrize("chunk", [262144, 65536])
+def test_delta_packer_stages_two_groups(chunk):
+    """Launches that hold deltas take the packer instance that stages two coded
+    groups in pass A (and encodes any further coded group, and any unit whose
+    slot overflows, from the inputs again).  FP32 deltas of few-valued tensors
+    code all four XOR groups, BF16 deltas code both; a batch mixing them with
+    plain tensors, against the oracle byte for byte, and decoded back."""
+    g = np.random.default_rng(140)
+    n32 = 3 * 65536 + 777
+    b32 = _few_values_fp32(n32, 141)
+    x32 = b32.copy()
+    pick = g.random(n32) < 0.3
+    x32[pick] = _few_values_fp32(int(pick.sum()), 142)
+    base32 = torch.from_numpy(b32.view(np.int32)).view(torch.float32)
+    next32 = torch.from_numpy(x32.view(np.int32)).view(torch.float32)
+    next16, base16 = W.delta_pair(400_003, seed=143)
+    plain = W.gaussian(200_001, 0.02, 144)
+    xs = [next32, next16, plain]
+    bases = [base32, base16, None]
+    bc = Z.BatchCompressor([x.cuda() for x in xs], chunk_bytes=chunk,
+                           bases=[b.cuda() if b is not None else None for b in bases])
+    for o in bc.outs:
+        o.fill_(0x5A)
+    bc()
+    Z.sync_status()
+    cs = bc.containers()
+    want = [O.delta(u8(next32), u8(base32), Z.FP32, chunk),
+            O.delta(u8(next16), u8(base16), Z.BF16, chunk),
+            O.compress(u8(plain), Z.BF16, chunk)]
+    modes32 = [m for ch in range(2) for m, _ in
+               [tuple(want[0][64 + 16 * (ch * 4 + gg) + 12: 64 + 16 * (ch * 4 + gg) + 14])
+                for gg in range(4)]]
+    assert modes32.count(1) + modes32.count(4) >= 6  # most FP32 XOR groups coded
+    for c, w in zip(cs, want):
+        assert c.to_bytes() == w
+    outs = [torch.empty_like(x, device="cuda") for x in xs]
+    Z.batch_decompress(cs, outs, bases=[b.cuda() if b is not None else None for b in bases])
+    Z.sync_status()
+    for x, o in zip(xs, outs):
+        assert torch.equal(o.cpu().view(torch.uint8), x.view(torch.uint8))
